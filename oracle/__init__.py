@@ -1,0 +1,194 @@
+"""FP64 CPU oracle of the PINOCCHIO collapse-time step (Sec. 2.1.1).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and
+by bench.py's cpu_baseline / reference leg.  The product path never imports
+it.  Everything here is argument marshalling around oracle/pin_oracle.c.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def _p(a, ct=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None else None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if _build.needs_build():
+            p = _build.build()
+            if p is not None:
+                out, _ = p.communicate()
+                if p.returncode != 0:
+                    raise RuntimeError("oracle build failed:\n" + out.decode())
+        L = ctypes.CDLL(_build.LIB)
+        L.or_dft1d.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp]
+        L.or_idft3d.argtypes = [_dp, ctypes.c_int]
+        L.or_hessian.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
+        L.or_hessian_point.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.or_hessian_point.restype = ctypes.c_double
+        L.or_eig3.argtypes = [_dp, _dp]
+        L.or_axis_coeffs.argtypes = [_dp, ctypes.c_int, _dp]
+        L.or_first_root.argtypes = [_dp]
+        L.or_first_root.restype = ctypes.c_double
+        L.or_delta_c.restype = ctypes.c_double
+        L.or_x3.restype = ctypes.c_double
+        L.or_collapse_F.argtypes = [_dp, ctypes.c_int]
+        L.or_collapse_F.restype = ctypes.c_double
+        L.or_collapse_point.argtypes = [_dp, ctypes.c_int, _dp]
+        L.or_collapse_point.restype = ctypes.c_double
+        L.or_collapse_slope.argtypes = [_dp]
+        L.or_collapse_slope.restype = ctypes.c_double
+        L.or_collapse_times.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
+                                        ctypes.c_int, _dp, _ip, _dp, _dp, _ip, _dp]
+        L.or_collapse_times_sampled.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                _dp, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_longlong), _dp, _ip, _dp,
+                                                _ip]
+        L.or_collapse_from_hessians.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                _dp, _ip, _dp, _ip]
+        _lib = L
+    return _lib
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def dft1d(x, sign=+1):
+    """Unnormalised 1D DFT with exp(sign 2 pi i jk/n)."""
+    x = _c128(x)
+    out = np.empty_like(x)
+    lib().or_dft1d(_p(x.view(np.float64)), x.size, sign, _p(out.view(np.float64)))
+    return out
+
+
+def idft3d(a):
+    """Normalised inverse 3D DFT of a full complex cube (copy)."""
+    a = _c128(a).copy()
+    lib().or_idft3d(_p(a.view(np.float64)), a.shape[0])
+    return a
+
+
+def hessian(delta_half, box, radius):
+    """(6, n, n, n) FP64 deformation tensor xx, yy, zz, xy, xz, yz, and the
+    largest imaginary residue of the inverse transforms."""
+    d = _c128(delta_half)
+    n = d.shape[0]
+    out = np.empty((6, n, n, n), dtype=np.float64)
+    mi = ctypes.c_double()
+    rc = lib().or_hessian(_p(d.view(np.float64)), n, box, radius, _p(out), ctypes.byref(mi))
+    if rc:
+        raise ValueError("or_hessian failed: %d" % rc)
+    return out, mi.value
+
+
+def hessian_point(delta_half, box, radius, comp, q):
+    d = _c128(delta_half)
+    return lib().or_hessian_point(_p(d.view(np.float64)), d.shape[0], box, radius, comp,
+                                  int(q[0]), int(q[1]), int(q[2]))
+
+
+def eig3(h6):
+    h = np.ascontiguousarray(h6, dtype=np.float64)
+    lam = np.empty(3)
+    lib().or_eig3(_p(h), _p(lam))
+    return lam
+
+
+def axis_coeffs(lam, i):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    c = np.empty(3)
+    lib().or_axis_coeffs(_p(lam), i, _p(c))
+    return c
+
+
+def first_root(c):
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    return lib().or_first_root(_p(c))
+
+
+def delta_c():
+    return lib().or_delta_c()
+
+
+def x3():
+    return lib().or_x3()
+
+
+def collapse_F(lam, correction=1):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    return lib().or_collapse_F(_p(lam), correction)
+
+
+def collapse_point(h6, correction=1):
+    h = np.ascontiguousarray(h6, dtype=np.float64)
+    lam = np.empty(3)
+    F = lib().or_collapse_point(_p(h), correction, _p(lam))
+    return F, lam
+
+
+def collapse_slope(lam):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    return lib().or_collapse_slope(_p(lam))
+
+
+def collapse_times(delta_half, box, radii, correction=1, keep_all=False):
+    """Returns dict with fmax, idx (n^3), f2/idx2 (runner-up), slope, and
+    f_all (S, n^3) when keep_all."""
+    d = _c128(delta_half)
+    n = d.shape[0]
+    r = np.ascontiguousarray(radii, dtype=np.float64)
+    S = r.size
+    n3 = n ** 3
+    fmax = np.empty(n3)
+    idx = np.empty(n3, dtype=np.int32)
+    f2 = np.empty(n3)
+    idx2 = np.empty(n3, dtype=np.int32)
+    slope = np.empty(n3)
+    f_all = np.empty((S, n3)) if keep_all else None
+    rc = lib().or_collapse_times(_p(d.view(np.float64)), n, box, S, _p(r), correction,
+                                 _p(fmax), _p(idx, ctypes.c_int), _p(f_all), _p(f2),
+                                 _p(idx2, ctypes.c_int), _p(slope))
+    if rc:
+        raise ValueError("or_collapse_times failed: %d" % rc)
+    out = dict(fmax=fmax, idx=idx, f2=f2, idx2=idx2, slope=slope)
+    if keep_all:
+        out["f_all"] = f_all
+    return out
+
+
+def collapse_times_sampled(delta_half, box, radii, q_list, correction=1):
+    d = _c128(delta_half)
+    n = d.shape[0]
+    r = np.ascontiguousarray(radii, dtype=np.float64)
+    q = np.ascontiguousarray(q_list, dtype=np.int64)
+    m = q.size
+    fmax, f2 = np.empty(m), np.empty(m)
+    idx, idx2 = np.empty(m, dtype=np.int32), np.empty(m, dtype=np.int32)
+    rc = lib().or_collapse_times_sampled(_p(d.view(np.float64)), n, box, r.size, _p(r),
+                                         correction, m, _p(q, ctypes.c_longlong), _p(fmax),
+                                         _p(idx, ctypes.c_int), _p(f2), _p(idx2, ctypes.c_int))
+    if rc:
+        raise ValueError("or_collapse_times_sampled failed: %d" % rc)
+    return dict(fmax=fmax, idx=idx, f2=f2, idx2=idx2)
+
+
+def collapse_from_hessians(h6s, correction=1):
+    """h6s: (S, npts, 6) Hessians -> running max over S by the oracle."""
+    h = np.ascontiguousarray(h6s, dtype=np.float64)
+    S, m, _ = h.shape
+    fmax, f2 = np.empty(m), np.empty(m)
+    idx, idx2 = np.empty(m, dtype=np.int32), np.empty(m, dtype=np.int32)
+    lib().or_collapse_from_hessians(_p(h), S, m, correction, _p(fmax), _p(idx, ctypes.c_int),
+                                    _p(f2), _p(idx2, ctypes.c_int))
+    return dict(fmax=fmax, idx=idx, f2=f2, idx2=idx2)

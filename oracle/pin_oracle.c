@@ -1,0 +1,497 @@
+/*
+ * FP64 CPU oracle for the PINOCCHIO collapse-time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg load this file's library.  It shares no code,
+ * header, table or constant with the CUDA path; it is slow and plain on
+ * purpose, so that each step can be checked against the paper by eye.
+ *
+ * What it computes (Sec. 2.1.1 of Monaco et al. 2013, "Collapse times"):
+ *   for every smoothing radius R (processed in the order given):
+ *     1. T_ij(k) = (k_i k_j / k^2) W(kR) delta(k), W Gaussian (Sec. 2.1.1:
+ *        smoothing with a Gaussian filter; the deformation tensor is the
+ *        Hessian of the peculiar potential, with del^2 phi = delta).
+ *     2. phi_ij(q) = inverse 3D DFT of T_ij ("a series of FFTs").
+ *     3. per grid point, eigenvalues lambda1 >= lambda2 >= lambda3 of phi_ij
+ *        (principal axes of the ellipsoid).
+ *     4. collapse of the first axis (orbit crossing) under the ellipsoidal
+ *        truncation of third-order LPT with the growing mode D as the clock,
+ *        plus the quasi-spherical correction; F = 1 / D(t_coll) (Eq. F).
+ *     5. running maximum of F along the trajectory, F_max, and the index of
+ *        the radius at which it was reached (R_max).
+ *
+ * The paper defers the formulas of steps 4 to earlier papers that are not
+ * available, so steps 1 and 4 follow a written reading:
+ *   - filter: W = exp(-k^2 R^2 / 2), R the Gaussian sigma; signed wavenumber
+ *     index in [-N/2, N/2); for i != j every mode whose k_i or k_j sits on the
+ *     Nyquist index is zeroed (otherwise the off-diagonal spectra are not
+ *     Hermitian);
+ *   - axis displacement in the eigenframe, with mu1 = sum lambda,
+ *     mu2 = sum_{i<j} lambda_i lambda_j, mu3 = prod lambda and
+ *     e_i = lambda_i (mu1 - lambda_i) / 2:
+ *       a_i(D) = D lambda_i + (3/7) D^2 e_i
+ *              + D^3 [ (10/21)(1/4)(lambda_i (e_j + e_k) + e_i (lambda_j + lambda_k))
+ *                      - mu3 / 9 ]
+ *     (each invariant's terms shared equally between the axes that carry its
+ *     index; a sphere gives 1 - x/3 - x^2/21 - 23 x^3/1701, the textbook
+ *     spherical series, and lambda2 = lambda3 = 0 gives Zel'dovich);
+ *   - D_c = smallest positive root of a_i(D) = 1 over the three axes;
+ *     F_C6 = 1 / D_c, or 0 when no axis collapses;
+ *   - quasi-spherical correction (mode 1): for mu1 > 0,
+ *       F = F_C6 + mu1 (1/delta_c - 1/x3) exp(-(eps / 0.1)^2),
+ *       eps = (lambda1 - lambda3) / |mu1|,
+ *     delta_c = (3/20)(12 pi)^(2/3) and x3 the root of
+ *     x/3 + x^2/21 + 23 x^3 / 1701 = 1, so that a sphere gives exactly
+ *     F = delta / delta_c (Sec. 2.1.1, spherical limit);
+ *   - F_max starts at 0 with index -1; an update needs F > F_max strictly.
+ *
+ * Parity against the real PINOCCHIO code is unpinned (no code or data of it
+ * exists here); the tests pin this oracle to closed forms and limits.
+ */
+#include "pin_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ DFT -- */
+
+static int is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+/* Unnormalised 1D DFT X_k = sum_j x_j exp(sign 2 pi i j k / n), by recursive
+ * radix-2 decimation in time.  x is read with the given stride; out is
+ * contiguous. */
+static void fft_radix2(const double complex* x, int n, int stride, int sign,
+                       double complex* out) {
+  if (n == 1) { out[0] = x[0]; return; }
+  int h = n / 2;
+  double complex* even = malloc(sizeof(double complex) * h);
+  double complex* odd = malloc(sizeof(double complex) * h);
+  fft_radix2(x, h, 2 * stride, sign, even);
+  fft_radix2(x + stride, h, 2 * stride, sign, odd);
+  for (int k = 0; k < h; ++k) {
+    double ang = sign * 2.0 * M_PI * k / n;
+    double complex t = (cos(ang) + I * sin(ang)) * odd[k];
+    out[k] = even[k] + t;
+    out[k + h] = even[k] - t;
+  }
+  free(even);
+  free(odd);
+}
+
+/* Unnormalised 1D DFT by the defining sum, O(n^2). */
+static void dft_direct(const double complex* x, int n, int sign, double complex* out) {
+  for (int k = 0; k < n; ++k) {
+    double complex s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      long long jk = ((long long)j * k) % n;
+      double ang = sign * 2.0 * M_PI * (double)jk / n;
+      s += x[j] * (cos(ang) + I * sin(ang));
+    }
+    out[k] = s;
+  }
+}
+
+void or_dft1d(const double* in_ri, int n, int sign, double* out_ri) {
+  const double complex* in = (const double complex*)in_ri;
+  double complex* out = (double complex*)out_ri;
+  if (is_pow2(n)) fft_radix2(in, n, 1, sign, out);
+  else dft_direct(in, n, sign, out);
+}
+
+/* In-place 3D inverse DFT of a full complex cube a[n][n][n] (row major,
+ * last index fastest), normalised by n^-3: one 1D transform per line along
+ * each axis in turn. */
+static void idft3d(double complex* a, int n) {
+  const size_t n2 = (size_t)n * n;
+  for (int axis = 0; axis < 3; ++axis) {
+    size_t stride = axis == 0 ? n2 : (axis == 1 ? (size_t)n : 1);
+#pragma omp parallel
+    {
+      double complex* line = malloc(sizeof(double complex) * n);
+      double complex* res = malloc(sizeof(double complex) * n);
+#pragma omp for schedule(static)
+      for (long long l = 0; l < (long long)n2; ++l) {
+        /* enumerate the n^2 lines orthogonal to this axis */
+        size_t u = (size_t)l / n, v = (size_t)l % n, base;
+        if (axis == 0) base = u * n + v;
+        else if (axis == 1) base = u * n2 + v;
+        else base = u * n2 + v * n;
+        for (int j = 0; j < n; ++j) line[j] = a[base + j * stride];
+        or_dft1d((const double*)line, n, +1, (double*)res);
+        for (int j = 0; j < n; ++j) a[base + j * stride] = res[j];
+      }
+      free(line);
+      free(res);
+    }
+  }
+  const double norm = 1.0 / ((double)n * n * n);
+#pragma omp parallel for schedule(static)
+  for (long long i = 0; i < (long long)(n2 * n); ++i) a[i] *= norm;
+}
+
+void or_idft3d(double* a_ri, int n) { idft3d((double complex*)a_ri, n); }
+
+/* ------------------------------------------------------------- filter -- */
+
+static int signed_index(int i, int n) { return i < n / 2 ? i : i - n; }
+
+/* Component c of the symmetric tensor, in the order xx, yy, zz, xy, xz, yz. */
+static const int COMP_I[6] = {0, 1, 2, 0, 0, 1};
+static const int COMP_J[6] = {0, 1, 2, 1, 2, 2};
+
+/* Filtered spectrum T_c(k) on the full cube, from the half-spectrum delta(k)
+ * ([n][n][n/2+1]).  Modes with kz > n/2 come from Hermitian symmetry,
+ * T(-k) = conj T(k), which the filter preserves (it is an even real function
+ * of k once the off-diagonal Nyquist modes are zeroed). */
+static void filtered_full(const double complex* half, int n, double box, double radius,
+                          int comp, double complex* full) {
+  const int nh = n / 2 + 1;
+  const int ci = COMP_I[comp], cj = COMP_J[comp];
+  const double kf = 2.0 * M_PI / box;
+#pragma omp parallel for schedule(static)
+  for (int ix = 0; ix < n; ++ix) {
+    for (int iy = 0; iy < n; ++iy) {
+      for (int iz = 0; iz < n; ++iz) {
+        /* the stored mode that holds this one, conjugated if mirrored */
+        int sx, sy, sz, mirrored = iz > n / 2;
+        size_t src;
+        if (!mirrored) {
+          src = ((size_t)ix * n + iy) * nh + iz;
+        } else {
+          src = ((size_t)((n - ix) % n) * n + (n - iy) % n) * nh + (n - iz);
+        }
+        /* signed index of THIS mode (iz = n/2 maps to -n/2) */
+        sx = signed_index(ix, n);
+        sy = signed_index(iy, n);
+        sz = signed_index(iz, n);
+        int s[3] = {sx, sy, sz};
+        double k[3] = {kf * sx, kf * sy, kf * sz};
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        double complex d = mirrored ? conj(half[src]) : half[src];
+        double complex t = 0.0;
+        if (k2 > 0.0) {
+          int nyq = (ci != cj) && (s[ci] == -n / 2 || s[cj] == -n / 2);
+          if (!nyq) {
+            double w = exp(-0.5 * k2 * radius * radius);
+            t = k[ci] * k[cj] / k2 * w * d;
+          }
+        }
+        full[((size_t)ix * n + iy) * n + iz] = t;
+      }
+    }
+  }
+}
+
+int or_hessian(const double* delta_half_ri, int n, double box, double radius,
+               double* out6, double* max_imag) {
+  if (n < 2 || (n & 1)) return -1;
+  const size_t n3 = (size_t)n * n * n;
+  double complex* full = malloc(sizeof(double complex) * n3);
+  if (!full) return -2;
+  double worst = 0.0;
+  for (int c = 0; c < 6; ++c) {
+    filtered_full((const double complex*)delta_half_ri, n, box, radius, c, full);
+    idft3d(full, n);
+    for (size_t q = 0; q < n3; ++q) {
+      out6[c * n3 + q] = creal(full[q]);
+      double a = fabs(cimag(full[q]));
+      if (a > worst) worst = a;
+    }
+  }
+  if (max_imag) *max_imag = worst;
+  free(full);
+  return 0;
+}
+
+/* Direct evaluation of phi_c(q) at one grid point from the half-spectrum:
+ * N^-3 sum over all k of T_c(k) e^{+i k.q}, the half-spectrum modes with
+ * 0 < kz < n/2 counted twice (their mirrors are the conjugates). */
+double or_hessian_point(const double* delta_half_ri, int n, double box, double radius,
+                        int comp, int qx, int qy, int qz) {
+  const double complex* half = (const double complex*)delta_half_ri;
+  const int nh = n / 2 + 1;
+  const int ci = COMP_I[comp], cj = COMP_J[comp];
+  const double kf = 2.0 * M_PI / box;
+  double total = 0.0;
+#pragma omp parallel for reduction(+ : total) schedule(static)
+  for (int ix = 0; ix < n; ++ix) {
+    double acc = 0.0;
+    for (int iy = 0; iy < n; ++iy) {
+      for (int iz = 0; iz < nh; ++iz) {
+        int s[3] = {signed_index(ix, n), signed_index(iy, n), iz < n / 2 ? iz : -(n / 2)};
+        double k[3] = {kf * s[0], kf * s[1], kf * s[2]};
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        if (k2 == 0.0) continue;
+        if (ci != cj && (s[ci] == -n / 2 || s[cj] == -n / 2)) continue;
+        double mult = k[ci] * k[cj] / k2 * exp(-0.5 * k2 * radius * radius);
+        double complex d = half[((size_t)ix * n + iy) * nh + iz];
+        long long ph = ((long long)ix * qx + (long long)iy * qy + (long long)iz * qz) % n;
+        double ang = 2.0 * M_PI * (double)ph / n;
+        double term = mult * creal(d * (cos(ang) + I * sin(ang)));
+        acc += (iz == 0 || iz == n / 2) ? term : 2.0 * term;
+      }
+    }
+    total += acc;
+  }
+  return total / ((double)n * n * n);
+}
+
+/* ------------------------------------------------------- eigenvalues -- */
+
+/* Cyclic Jacobi on a symmetric 3x3 matrix; eigenvalues sorted descending. */
+void or_eig3(const double* h6, double* lam) {
+  double a[3][3] = {{h6[0], h6[3], h6[4]}, {h6[3], h6[1], h6[5]}, {h6[4], h6[5], h6[2]}};
+  double norm2 = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) norm2 += a[i][j] * a[i][j];
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off2 = 2.0 * (a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2]);
+    if (off2 <= 1e-30 * norm2 || off2 == 0.0) break;
+    for (int p = 0; p < 2; ++p) {
+      for (int q = p + 1; q < 3; ++q) {
+        if (a[p][q] == 0.0) continue;
+        /* rotation angle that annihilates a[p][q]: tan(2 theta) = 2 a_pq / (a_qq - a_pp) */
+        double theta = 0.5 * atan2(2.0 * a[p][q], a[q][q] - a[p][p]);
+        double c = cos(theta), s = sin(theta);
+        double j[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        j[p][p] = c; j[q][q] = c; j[p][q] = s; j[q][p] = -s;
+        /* a <- J^T a J */
+        double t[3][3], r[3][3];
+        for (int u = 0; u < 3; ++u)
+          for (int v = 0; v < 3; ++v) {
+            t[u][v] = 0.0;
+            for (int w = 0; w < 3; ++w) t[u][v] += a[u][w] * j[w][v];
+          }
+        for (int u = 0; u < 3; ++u)
+          for (int v = 0; v < 3; ++v) {
+            r[u][v] = 0.0;
+            for (int w = 0; w < 3; ++w) r[u][v] += j[w][u] * t[w][v];
+          }
+        memcpy(a, r, sizeof(a));
+        a[p][q] = a[q][p] = 0.0;
+      }
+    }
+  }
+  double e[3] = {a[0][0], a[1][1], a[2][2]};
+  /* sort descending */
+  for (int i = 0; i < 3; ++i)
+    for (int k = i + 1; k < 3; ++k)
+      if (e[k] > e[i]) { double tmp = e[i]; e[i] = e[k]; e[k] = tmp; }
+  lam[0] = e[0]; lam[1] = e[1]; lam[2] = e[2];
+}
+
+/* ------------------------------------------------------------ collapse -- */
+
+/* Coefficients (c1, c2, c3) of a_i(D) = c1 D + c2 D^2 + c3 D^3 for axis i. */
+void or_axis_coeffs(const double* lam, int i, double* c) {
+  int j = (i + 1) % 3, k = (i + 2) % 3;
+  double mu1 = lam[0] + lam[1] + lam[2];
+  double mu3 = lam[0] * lam[1] * lam[2];
+  double e[3];
+  for (int a = 0; a < 3; ++a) e[a] = lam[a] * (mu1 - lam[a]) / 2.0;
+  c[0] = lam[i];
+  c[1] = 3.0 / 7.0 * e[i];
+  c[2] = 10.0 / 21.0 * 0.25 * (lam[i] * (e[j] + e[k]) + e[i] * (lam[j] + lam[k])) - mu3 / 9.0;
+}
+
+static double cubic_p(const double* c, double d) {
+  return ((c[2] * d + c[1]) * d + c[0]) * d - 1.0;
+}
+
+/* Smallest positive root of p(D) = c3 D^3 + c2 D^2 + c1 D - 1, or +inf.
+ * The positive critical points of p cut (0, B] (B = Cauchy bound) into
+ * intervals on which p is monotone; p(0) = -1, so the root is in the first
+ * interval whose right end has p >= 0, found there by bisection. */
+double or_first_root(const double* c) {
+  double c1 = c[0], c2 = c[1], c3 = c[2];
+  double lead, bound;
+  if (c3 != 0.0) {
+    lead = fabs(c3);
+    double m = fmax(fmax(fabs(c2), fabs(c1)), 1.0);
+    bound = 1.0 + m / lead;
+  } else if (c2 != 0.0) {
+    lead = fabs(c2);
+    bound = 1.0 + fmax(fabs(c1), 1.0) / lead;
+  } else if (c1 != 0.0) {
+    bound = 1.0 + 1.0 / fabs(c1);
+  } else {
+    return INFINITY;
+  }
+  /* positive roots of p'(D) = 3 c3 D^2 + 2 c2 D + c1 */
+  double crit[2];
+  int ncrit = 0;
+  if (c3 != 0.0) {
+    double A = 3.0 * c3, B = 2.0 * c2, C = c1;
+    double disc = B * B - 4.0 * A * C;
+    if (disc >= 0.0) {
+      double sq = sqrt(disc);
+      double r1 = (-B - sq) / (2.0 * A), r2 = (-B + sq) / (2.0 * A);
+      if (r1 > r2) { double t = r1; r1 = r2; r2 = t; }
+      if (r1 > 0.0 && r1 < bound) crit[ncrit++] = r1;
+      if (r2 > 0.0 && r2 < bound && r2 != r1) crit[ncrit++] = r2;
+    }
+  } else if (c2 != 0.0) {
+    double r = -c1 / (2.0 * c2);
+    if (r > 0.0 && r < bound) crit[ncrit++] = r;
+  }
+  double pts[4];
+  int np = 0;
+  pts[np++] = 0.0;
+  for (int i = 0; i < ncrit; ++i) pts[np++] = crit[i];
+  pts[np++] = bound;
+  for (int i = 0; i + 1 < np; ++i) {
+    double lo = pts[i], hi = pts[i + 1];
+    if (cubic_p(c, hi) < 0.0) continue;
+    /* p(lo) < 0 <= p(hi) and p is monotone on [lo, hi] */
+    for (int it = 0; it < 400 && hi - lo > 1e-15 * hi; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (cubic_p(c, mid) < 0.0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+  }
+  return INFINITY;
+}
+
+double or_delta_c(void) { return 3.0 / 20.0 * pow(12.0 * M_PI, 2.0 / 3.0); }
+
+double or_x3(void) {
+  /* root of x/3 + x^2/21 + 23 x^3 / 1701 = 1 on [0, 3] by bisection */
+  double lo = 0.0, hi = 3.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    double v = mid / 3.0 + mid * mid / 21.0 + 23.0 * mid * mid * mid / 1701.0 - 1.0;
+    if (v < 0.0) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+double or_collapse_F(const double* lam, int correction) {
+  double dmin = INFINITY;
+  for (int i = 0; i < 3; ++i) {
+    double c[3];
+    or_axis_coeffs(lam, i, c);
+    double d = or_first_root(c);
+    if (d < dmin) dmin = d;
+  }
+  double F = isinf(dmin) ? 0.0 : 1.0 / dmin;
+  double mu1 = lam[0] + lam[1] + lam[2];
+  if (correction == 1 && mu1 > 0.0) {
+    double eps = (lam[0] - lam[2]) / fabs(mu1);
+    double w = exp(-(eps / 0.1) * (eps / 0.1));
+    F += mu1 * (1.0 / or_delta_c() - 1.0 / or_x3()) * w;
+  }
+  return F;
+}
+
+double or_collapse_point(const double* h6, int correction, double* lam_out) {
+  double lam[3];
+  or_eig3(h6, lam);
+  if (lam_out) { lam_out[0] = lam[0]; lam_out[1] = lam[1]; lam_out[2] = lam[2]; }
+  return or_collapse_F(lam, correction);
+}
+
+/* Sensitivity of the collapse root: D_c * a'(D_c) for the axis that sets D_c
+ * (0 when nothing collapses).  Small values flag a near-tangent crossing, where
+ * F jumps under tiny changes of the Hessian. */
+double or_collapse_slope(const double* lam) {
+  double dmin = INFINITY, slope = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    double c[3];
+    or_axis_coeffs(lam, i, c);
+    double d = or_first_root(c);
+    if (d < dmin) {
+      dmin = d;
+      slope = d * (c[0] + 2.0 * c[1] * d + 3.0 * c[2] * d * d);
+    }
+  }
+  return isinf(dmin) ? 0.0 : slope;
+}
+
+/* --------------------------------------------------------- trajectory -- */
+
+int or_collapse_times(const double* delta_half_ri, int n, double box, int nscales,
+                      const double* radii, int correction, double* fmax, int* idx,
+                      double* f_all, double* f2, int* idx2, double* slope) {
+  if (n < 2 || (n & 1) || nscales < 1) return -1;
+  const size_t n3 = (size_t)n * n * n;
+  double* h = malloc(sizeof(double) * 6 * n3);
+  if (!h) return -2;
+  for (size_t q = 0; q < n3; ++q) {
+    fmax[q] = 0.0;
+    idx[q] = -1;
+    if (f2) { f2[q] = 0.0; idx2[q] = -1; }
+    if (slope) slope[q] = 0.0;
+  }
+  for (int s = 0; s < nscales; ++s) {
+    int rc = or_hessian(delta_half_ri, n, box, radii[s], h, NULL);
+    if (rc) { free(h); return rc; }
+#pragma omp parallel for schedule(static)
+    for (long long q = 0; q < (long long)n3; ++q) {
+      double h6[6];
+      for (int c = 0; c < 6; ++c) h6[c] = h[c * n3 + q];
+      double lam[3];
+      double F = or_collapse_point(h6, correction, lam);
+      if (f_all) f_all[(size_t)s * n3 + q] = F;
+      if (F > fmax[q]) {
+        if (f2) { f2[q] = fmax[q]; idx2[q] = idx[q]; }
+        fmax[q] = F;
+        idx[q] = s;
+        if (slope) slope[q] = or_collapse_slope(lam);
+      } else if (f2 && F > f2[q]) {
+        f2[q] = F;
+        idx2[q] = s;
+      }
+    }
+  }
+  free(h);
+  return 0;
+}
+
+int or_collapse_times_sampled(const double* delta_half_ri, int n, double box, int nscales,
+                              const double* radii, int correction, int npts,
+                              const long long* q_list, double* fmax, int* idx, double* f2,
+                              int* idx2) {
+  if (n < 2 || (n & 1) || nscales < 1) return -1;
+  const size_t n3 = (size_t)n * n * n;
+  double* h = malloc(sizeof(double) * 6 * n3);
+  if (!h) return -2;
+  for (int p = 0; p < npts; ++p) { fmax[p] = 0.0; idx[p] = -1; f2[p] = 0.0; idx2[p] = -1; }
+  for (int s = 0; s < nscales; ++s) {
+    int rc = or_hessian(delta_half_ri, n, box, radii[s], h, NULL);
+    if (rc) { free(h); return rc; }
+#pragma omp parallel for schedule(static)
+    for (int p = 0; p < npts; ++p) {
+      double h6[6];
+      for (int c = 0; c < 6; ++c) h6[c] = h[c * n3 + (size_t)q_list[p]];
+      double F = or_collapse_point(h6, correction, NULL);
+      if (F > fmax[p]) {
+        f2[p] = fmax[p]; idx2[p] = idx[p];
+        fmax[p] = F; idx[p] = s;
+      } else if (F > f2[p]) {
+        f2[p] = F; idx2[p] = s;
+      }
+    }
+  }
+  free(h);
+  return 0;
+}
+
+/* Running maximum over per-scale Hessians supplied by the caller (h6s is
+ * [nscales][npts][6]); the oracle's own eigenvalues and collapse times. */
+void or_collapse_from_hessians(const double* h6s, int nscales, int npts, int correction,
+                               double* fmax, int* idx, double* f2, int* idx2) {
+#pragma omp parallel for schedule(static)
+  for (int p = 0; p < npts; ++p) {
+    double best = 0.0, second = 0.0;
+    int bi = -1, si = -1;
+    for (int s = 0; s < nscales; ++s) {
+      double F = or_collapse_point(h6s + ((size_t)s * npts + p) * 6, correction, NULL);
+      if (F > best) { second = best; si = bi; best = F; bi = s; }
+      else if (F > second) { second = F; si = s; }
+    }
+    fmax[p] = best; idx[p] = bi;
+    if (f2) { f2[p] = second; idx2[p] = si; }
+  }
+}

@@ -1,0 +1,93 @@
+"""In-tree build of the native libraries.
+
+  _build/libpin.so     CUDA path for sm_103a (nvcc), C-ABI in include/pin.h
+  _build/libpin_ic.so  seeded input generator (gcc), C-ABI in include/pin_ic.h
+
+Both are compiled in parallel; nothing is installed outside the tree.
+"""
+import glob
+import os
+import subprocess
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+INC = os.path.join(ROOT, "include")
+OUT_DIR = os.path.join(PKG, "_build")
+LIBPIN = os.path.join(OUT_DIR, "libpin.so")
+LIBIC = os.path.join(OUT_DIR, "libpin_ic.so")
+
+CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _sources_pin():
+    return sorted(glob.glob(os.path.join(PKG, "csrc", "*.cu")))
+
+
+def _deps_pin():
+    return (_sources_pin() + glob.glob(os.path.join(PKG, "csrc", "*.cuh"))
+            + glob.glob(os.path.join(PKG, "csrc", "*.h")) + [os.path.join(INC, "pin.h")])
+
+
+def _stale(target, deps):
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+def cmd_pin(extra=()):
+    return ([NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared",
+                             "-Xcompiler", "-fPIC", "-I", INC, "-I", os.path.join(PKG, "csrc"),
+                             "-o", LIBPIN] + list(extra) + _sources_pin() + ["-lcuda"])
+
+
+def cmd_ic():
+    src = os.path.join(PKG, "ic", "pin_ic.c")
+    return ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+            "-ffp-contract=off", "-I", INC, "-o", LIBIC, src, "-lm"]
+
+
+def _run(procs):
+    errs = []
+    for name, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            errs.append("%s build failed:\n%s" % (name, out.decode(errors="replace")))
+    if errs:
+        raise RuntimeError("\n".join(errs))
+
+
+def start(force=False, which=("pin", "ic")):
+    os.makedirs(OUT_DIR, exist_ok=True)
+    procs = []
+    if "ic" in which and (force or _stale(LIBIC, [os.path.join(PKG, "ic", "pin_ic.c"),
+                                                  os.path.join(INC, "pin_ic.h")])):
+        procs.append(("libpin_ic", subprocess.Popen(cmd_ic(), stdout=subprocess.PIPE,
+                                                    stderr=subprocess.STDOUT)))
+    if "pin" in which and _sources_pin() and (force or _stale(LIBPIN, _deps_pin())):
+        procs.append(("libpin", subprocess.Popen(cmd_pin(), stdout=subprocess.PIPE,
+                                                 stderr=subprocess.STDOUT)))
+    return procs
+
+
+def build_all(force=False):
+    _run(start(force=force))
+
+
+def ensure_ic():
+    if _stale(LIBIC, [os.path.join(PKG, "ic", "pin_ic.c"), os.path.join(INC, "pin_ic.h")]):
+        _run(start(which=("ic",)))
+    return LIBIC
+
+
+def ensure_pin():
+    if _stale(LIBPIN, _deps_pin()):
+        _run(start(which=("pin",)))
+    return LIBPIN
+
+
+if __name__ == "__main__":
+    build_all(force=True)
+    print("built", LIBPIN, LIBIC)

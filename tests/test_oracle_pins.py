@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test checks the oracle against a closed form, a brute-force sum, a
+library routine in a special case, or a textbook value, chosen so that a
+dropped term, a wrong sign or index, or a transposed axis fails one of them.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_1505_gb300 import ic
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split(None, 1)
+            vals[k] = v
+    return vals
+
+
+# ---------------------------------------------------------------- DFT pins --
+
+def _dft_matrix(n, sign):
+    j = np.arange(n)
+    return np.exp(sign * 2j * np.pi * np.outer(j, j) / n)
+
+
+@pytest.mark.parametrize("n", [1, 2, 8, 16, 12, 6, 9])
+def test_dft1d_matches_brute_force(n):
+    rng = np.random.default_rng(n)
+    x = rng.normal(size=n) + 1j * rng.normal(size=n)
+    for sign in (+1, -1):
+        ref = _dft_matrix(n, sign) @ x
+        got = oracle.dft1d(x, sign)
+        assert np.allclose(got, ref, rtol=0, atol=1e-12 * max(1, np.abs(ref).max()))
+    # library special case: the unnormalised inverse DFT is n * numpy.fft.ifft
+    assert np.allclose(oracle.dft1d(x, +1), n * np.fft.ifft(x), atol=1e-12 * n)
+
+
+@pytest.mark.parametrize("n", [8, 6])
+def test_idft3d_matches_brute_force(n):
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=(n, n, n)) + 1j * rng.normal(size=(n, n, n))
+    E = _dft_matrix(n, +1)
+    ref = np.einsum("ai,bj,ck,ijk->abc", E, E, E, a) / n ** 3
+    got = oracle.idft3d(a)
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [16, 12])
+def test_parseval(n):
+    rng = np.random.default_rng(5)
+    a = rng.normal(size=(n, n, n)) + 1j * rng.normal(size=(n, n, n))
+    f = oracle.idft3d(a)
+    lhs = np.sum(np.abs(f) ** 2)
+    rhs = np.sum(np.abs(a) ** 2) / n ** 3
+    assert abs(lhs - rhs) < 1e-12 * rhs
+
+
+# ------------------------------------------------------------- filter pins --
+
+def _field(n, box, seed):
+    return ic.delta_k(n, box, seed, dtype=np.complex128)
+
+
+def test_hessian_is_real_for_hermitian_input():
+    d = _field(16, 100.0, 11)
+    h, max_imag = oracle.hessian(d, 100.0, 4.0)
+    assert max_imag < 1e-13 * np.abs(h).max()
+
+
+@pytest.mark.parametrize("n,box,radius", [(16, 100.0, 4.0), (12, 60.0, 3.0), (8, 50.0, 0.0)])
+def test_trace_equals_smoothed_delta(n, box, radius):
+    """phi_xx + phi_yy + phi_zz = IDFT(W delta): the filter's trace rule
+    (del^2 phi = delta), against numpy's irfftn of the Gaussian-smoothed field.
+    Nyquist modes are kept on the diagonal, so the rule is exact."""
+    d = _field(n, box, 7)
+    h, _ = oracle.hessian(d, box, radius)
+    m = np.fft.fftfreq(n, 1.0 / n)
+    m[n // 2] = -n // 2
+    mz = np.arange(n // 2 + 1, dtype=float)
+    mz[-1] = -n // 2
+    kf = 2 * np.pi / box
+    k2 = (kf * m[:, None, None]) ** 2 + (kf * m[None, :, None]) ** 2 + (kf * mz[None, None, :]) ** 2
+    sm = d * np.exp(-0.5 * k2 * radius ** 2)
+    sm[0, 0, 0] = 0.0
+    ref = np.fft.irfftn(sm, s=(n, n, n), axes=(0, 1, 2))
+    tr = h[0] + h[1] + h[2]
+    assert np.abs(tr - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("mode", [(1, 2, 3), (5, 1, 2), (3, 6, 1), (0, 0, 2), (4, 0, 0)])
+def test_single_mode_closed_form(mode):
+    """A single Fourier mode (plus its Hermitian mirror) gives
+    phi_ij(q) = (k_i k_j / k^2) W(k) 2 Re(A e^{i k.q}) / n^3, which pins the
+    sign convention, the axis order and the normalisation of every component."""
+    n, box, radius = 8, 40.0, 2.0
+    d = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    amp = 0.7 - 1.3j
+    mx, my, mz = mode
+    d[mx, my, mz] = amp
+    if mz == 0:
+        d[(-mx) % n, (-my) % n, 0] = np.conj(amp)
+    h, _ = oracle.hessian(d, box, radius)
+    sx = mx if mx < n // 2 else mx - n
+    sy = my if my < n // 2 else my - n
+    sz = mz
+    kf = 2 * np.pi / box
+    k = np.array([kf * sx, kf * sy, kf * sz])
+    k2 = k @ k
+    q = np.indices((n, n, n))
+    phase = 2 * np.pi * (sx * q[0] + sy * q[1] + sz * q[2]) / n
+    wave = 2 * np.real(amp * np.exp(1j * phase)) / n ** 3
+    if mz == 0 and (mx, my) == ((-mx) % n, (-my) % n):
+        wave = wave / 2
+    w = np.exp(-0.5 * k2 * radius ** 2)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    for c, (i, j) in enumerate(pairs):
+        ref = k[i] * k[j] / k2 * w * wave
+        assert np.abs(h[c] - ref).max() < 1e-14 + 1e-12 * np.abs(wave).max(), (c, mode)
+
+
+def test_offdiagonal_nyquist_is_zeroed():
+    """A mode with k_x on the Nyquist index feeds xx, yy, zz, yz but never xy or
+    xz (they would not be Hermitian)."""
+    n, box = 8, 40.0
+    d = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    d[n // 2, 1, 2] = 1.0 + 0.5j
+    h, _ = oracle.hessian(d, box, 1.0)
+    assert np.abs(h[3]).max() == 0.0 and np.abs(h[4]).max() == 0.0
+    assert np.abs(h[0]).max() > 0 and np.abs(h[5]).max() > 0
+
+
+def test_direct_point_sum_matches_fft_path():
+    """The direct sum over the half-spectrum at one point (a different
+    algorithm) agrees with the FFT path."""
+    n, box, radius = 12, 80.0, 5.0
+    d = _field(n, box, 3)
+    h, _ = oracle.hessian(d, box, radius)
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        q = rng.integers(0, n, size=3)
+        for c in range(6):
+            v = oracle.hessian_point(d, box, radius, c, q)
+            assert abs(v - h[c][tuple(q)]) < 1e-12 * np.abs(h[c]).max()
+
+
+# -------------------------------------------------------- eigenvalue pins --
+
+def _random_rotation(rng):
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    return q * np.sign(np.diag(r))
+
+
+def _h6(a):
+    return np.array([a[0, 0], a[1, 1], a[2, 2], a[0, 1], a[0, 2], a[1, 2]])
+
+
+@pytest.mark.parametrize("lam", [(3.0, -1.0, 0.5), (1.0, 1.0, -2.0), (2.0, 2.0, 2.0),
+                                 (0.0, 0.0, 0.0), (1e-3, -5.0, 7.0), (4.0, 4.0 + 1e-9, 1.0)])
+def test_eigen_rotated_diagonal(lam):
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        Q = _random_rotation(rng)
+        A = Q @ np.diag(lam) @ Q.T
+        got = oracle.eig3(_h6(A))
+        ref = np.sort(np.array(lam))[::-1]
+        assert np.allclose(got, ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
+
+
+def test_eigen_characteristic_polynomial_residual():
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        h = rng.normal(size=6)
+        A = np.array([[h[0], h[3], h[4]], [h[3], h[1], h[5]], [h[4], h[5], h[2]]])
+        lam = oracle.eig3(h)
+        assert lam[0] >= lam[1] >= lam[2]
+        for l in lam:
+            assert abs(np.linalg.det(A - l * np.eye(3))) < 1e-12 * np.abs(A).max() ** 3
+        assert abs(lam.sum() - np.trace(A)) < 1e-13 * np.abs(A).max() * 3
+
+
+# ---------------------------------------------------------- collapse pins --
+
+def _spherical_series_coeffs():
+    """LPT radius series r/q = 1 - (k1 x + k2 x^2 + k3 x^3) of a sphere of
+    linear contrast x, derived here by inverting 1 + delta_NL = (r/q)^-3 with
+    the textbook vertices nu2, nu3 (Bernardeau 1994)."""
+    g = _golden("spherical_collapse.txt")
+    nu2 = Fraction(g["nu2"])
+    nu3 = Fraction(g["nu3"])
+    b, c = nu2 / 2, nu3 / 6  # delta_NL = x + b x^2 + c x^3
+    # a = 1 - (1 + y)^(-1/3) = y/3 - 2/9 y^2 + 14/81 y^3 + O(y^4), y = delta_NL
+    k1 = Fraction(1, 3)
+    k2 = b / 3 - Fraction(2, 9)
+    k3 = c / 3 - Fraction(4, 9) * b + Fraction(14, 81)
+    return k1, k2, k3
+
+
+def test_spherical_series_textbook_coefficients():
+    k1, k2, k3 = _spherical_series_coeffs()
+    assert (k1, k2, k3) == (Fraction(1, 3), Fraction(1, 21), Fraction(23, 1701))
+    # the oracle's axis coefficients for a sphere of contrast delta reproduce them
+    for delta in (0.3, 1.0, 2.5):
+        lam = np.full(3, delta / 3)
+        for i in range(3):
+            c = oracle.axis_coeffs(lam, i)
+            assert np.allclose(c, [float(k1) * delta, float(k2) * delta ** 2,
+                                   float(k3) * delta ** 3], rtol=1e-14)
+
+
+@pytest.mark.parametrize("delta", [0.05, 0.8, 1.686, 3.0, 10.0])
+def test_sphere_uncorrected_is_series_root(delta):
+    k1, k2, k3 = (float(v) for v in _spherical_series_coeffs())
+    roots = np.roots([k3, k2, k1, -1.0])
+    x3 = min(r.real for r in roots if abs(r.imag) < 1e-12 and r.real > 0)
+    assert abs(oracle.x3() - x3) < 1e-13
+    h6 = np.array([delta / 3] * 3 + [0.0] * 3)
+    F, _ = oracle.collapse_point(h6, correction=0)
+    assert abs(F - delta / x3) < 1e-13 * delta
+    # LPT overestimates the spherical collapse time: x3 > delta_c
+    assert x3 > oracle.delta_c()
+
+
+@pytest.mark.parametrize("delta", [0.05, 0.8, 1.686, 3.0, 10.0])
+def test_sphere_corrected_gives_delta_over_delta_c(delta):
+    g = _golden("spherical_collapse.txt")
+    dc = float(g["delta_c_decimal"])
+    assert abs(oracle.delta_c() - 3 / 20 * (12 * np.pi) ** (2 / 3)) < 1e-15
+    assert abs(oracle.delta_c() - dc) < 1e-13
+    rng = np.random.default_rng(4)
+    Q = _random_rotation(rng)
+    A = Q @ np.diag([delta / 3] * 3) @ Q.T  # a rotated sphere is still a sphere
+    F, _ = oracle.collapse_point(_h6(A), correction=1)
+    assert abs(F - delta / dc) < 1e-12 * delta
+
+
+@pytest.mark.parametrize("delta", [-0.1, -2.0])
+def test_underdense_sphere_never_collapses(delta):
+    h6 = np.array([delta / 3] * 3 + [0.0] * 3)
+    for corr in (0, 1):
+        F, _ = oracle.collapse_point(h6, correction=corr)
+        assert F == 0.0
+
+
+@pytest.mark.parametrize("l1", [1e-4, 0.3, 1.0, 5.0])
+def test_one_axis_is_zeldovich(l1):
+    """lambda2 = lambda3 = 0: all higher orders vanish and the first axis
+    collapses at D = 1/lambda1 (Zel'dovich), F = lambda1."""
+    rng = np.random.default_rng(9)
+    Q = _random_rotation(rng)
+    A = Q @ np.diag([l1, 0.0, 0.0]) @ Q.T
+    F, lam = oracle.collapse_point(_h6(A), correction=0)
+    assert abs(F - l1) < 1e-12 * l1 + 1e-15
+    F1, _ = oracle.collapse_point(_h6(A), correction=1)
+    assert abs(F1 - l1) < 1e-12 * l1 + 1e-15
+
+
+def test_second_order_trace_is_2lpt():
+    """Sum over axes of the D^2 terms is (3/7) mu2 D^2: the divergence of the
+    standard second-order LPT displacement.  Also: the split is covariant under
+    permutation of the eigenvalues."""
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        lam = rng.normal(size=3)
+        mu2 = lam[0] * lam[1] + lam[0] * lam[2] + lam[1] * lam[2]
+        c = np.array([oracle.axis_coeffs(lam, i) for i in range(3)])
+        assert abs(c[:, 1].sum() - 3 / 7 * mu2) < 1e-13
+        perm = rng.permutation(3)
+        cp = np.array([oracle.axis_coeffs(lam[perm], i) for i in range(3)])
+        assert np.allclose(cp, c[perm], rtol=0, atol=1e-14)
+
+
+def _first_root_scan(c, npts=1_000_000):
+    c1, c2, c3 = c
+    p = lambda d: ((c3 * d + c2) * d + c1) * d - 1.0
+    # scan a log grid wide enough to bracket any root of these magnitudes
+    d = np.concatenate([[0.0], np.logspace(-6, 8, npts)])
+    v = p(d)
+    idx = np.nonzero(v >= 0)[0]
+    if idx.size == 0:
+        return np.inf
+    i = idx[0]
+    lo, hi = d[i - 1], d[i]
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if p(mid) < 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_first_root_matches_brute_force_scan():
+    rng = np.random.default_rng(8)
+    for _ in range(300):
+        c = rng.normal(size=3) * np.array([1.0, 0.7, 0.4])
+        got = oracle.first_root(c)
+        ref = _first_root_scan(c)
+        if np.isinf(ref):
+            # the scan reaches D = 1e8; the oracle's bound is exact
+            assert np.isinf(got) or got > 1e7
+        else:
+            assert abs(got - ref) < 1e-9 * ref, (c, got, ref)
+
+
+def test_first_root_degenerate_degrees():
+    assert abs(oracle.first_root([2.0, 0.0, 0.0]) - 0.5) < 1e-15
+    assert np.isinf(oracle.first_root([-1.0, 0.0, 0.0]))
+    assert np.isinf(oracle.first_root([0.0, 0.0, 0.0]))
+    # quadratic: c2 D^2 + c1 D - 1 = 0
+    c1, c2 = 0.5, 0.25
+    ref = (-c1 + np.sqrt(c1 ** 2 + 4 * c2)) / (2 * c2)
+    assert abs(oracle.first_root([c1, c2, 0.0]) - ref) < 1e-14 * ref
+    # tangent touch: p(D) = (1/3)(D - 1)^2 (D - 3) has a double root at D = 1,
+    # where p reaches 0 at a local maximum; it is the first root.
+    got = oracle.first_root([7 / 3, -5 / 3, 1 / 3])
+    assert abs(got - 1.0) < 1e-6
+
+
+# ------------------------------------------------------- running max pins --
+
+def test_running_max_is_first_strict_argmax():
+    n, box = 8, 50.0
+    d = _field(n, box, 21)
+    radii = ic.log_radii(box / n, 12.0, 6)
+    out = oracle.collapse_times(d, box, radii, keep_all=True)
+    fa = out["f_all"]
+    ref_max = np.maximum(fa.max(axis=0), 0.0)
+    assert np.array_equal(out["fmax"], ref_max)
+    ref_idx = np.where(fa.max(axis=0) > 0, fa.argmax(axis=0), -1)
+    assert np.array_equal(out["idx"], ref_idx)
+    # the runner-up is the best of the other scales
+    fa2 = fa.copy()
+    fa2[out["idx"][out["idx"] >= 0], np.nonzero(out["idx"] >= 0)[0]] = -np.inf
+    ok = out["idx"] >= 0
+    assert np.allclose(out["f2"][ok], np.maximum(fa2.max(axis=0)[ok], 0.0))
+
+
+def test_pipeline_agrees_with_pointwise_composition():
+    n, box = 8, 50.0
+    d = _field(n, box, 5)
+    radii = ic.log_radii(box / n, 12.0, 4)
+    out = oracle.collapse_times(d, box, radii, keep_all=True)
+    for s, r in enumerate(radii):
+        h, _ = oracle.hessian(d, box, r)
+        flat = h.reshape(6, -1)
+        for q in (0, 17, 200, 511):
+            F, _ = oracle.collapse_point(flat[:, q], correction=1)
+            assert F == out["f_all"][s, q]
