@@ -1,0 +1,288 @@
+"""Benchmark of the collapse-time path: collapse updates/s (particles x radii).
+
+Workload (default): 768^3 grid, box 3072 Mpc/h, seeded Gaussian field with
+P(k) = A k^0.96 T_BBKS(k/0.21)^2, sigma8 = 0.8, seed 3, 40 Gaussian radii
+log-spaced from 120 down to 4 Mpc/h.  One step = one pin_collapse_times call
+(all radii: filter, inverse FFTs of the six Hessian components, eigenvalues,
+collapse time, running maximum) with delta(k) resident on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torchrun); the
+path has no data exchange, so value = all ranks' updates / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the paper has no GPU implementation to run).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=768, box=3072.0, seed=3, nscales=40, r_min=4.0, r_max=120.0)
+# bounded CPU sample: same 4 Mpc/h cells and spectrum on a 128^3 grid, six of
+# the forty radii (every seventh, largest first)
+CPU_SAMPLE = dict(n=128, box=512.0, seed=3, every=7)
+METRIC = "collapse updates/s (particles x scales) at 768^3"
+UNIT = "updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(nscales_total):
+    """FP64 oracle, as it stands, on the bounded sample; updates/s and cores."""
+    import oracle
+    from paper_1305_1505_gb300 import ic
+    s = CPU_SAMPLE
+    radii = ic.log_radii(WORKLOAD["r_min"], WORKLOAD["r_max"], nscales_total)[::s["every"]]
+    d = ic.delta_k(s["n"], s["box"], s["seed"], dtype=np.complex64).astype(np.complex128)
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.collapse_times(d, s["box"], radii)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": s["n"] ** 3 * radii.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d^3 grid, box %.0f Mpc/h (the same 4 Mpc/h cells), seed %d, %d of the %d radii"
+                      " (every %dth), FP64, %.1f s" % (s["n"], s["box"], s["seed"], radii.size,
+                                                       nscales_total, s["every"], dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = WORKLOAD
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(w["nscales"])
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    ms = w["n"] ** 3 * w["nscales"] / v * 1e3
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(),
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config():
+    w = WORKLOAD
+    return {"workload": "768^3 grid, box 3072 Mpc/h, seed 3, 40 radii 120->4 Mpc/h (log), "
+                        "BBKS Gamma=0.21 n=0.96 sigma8=0.8",
+            "grid": w["n"], "box_mpc_h": w["box"], "nscales": w["nscales"],
+            "parallelism": "replicas",
+            "l2": "inputs larger than L2 (delta(k) 1.8 GB, per-pass spectra 5.5-11 GB)"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_1505_gb300 import ic, pin
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    n, S = w["n"], w["nscales"]
+    radii = ic.log_radii(w["r_min"], w["r_max"], S)
+    stream = torch.cuda.Stream()
+    d32 = ic.delta_k(n, w["box"], w["seed"] + 1000 * rank if ws > 1 else w["seed"], dtype=np.complex64)
+    plan = pin.Plan(n, w["box"], radii, stream=stream)
+    dk = torch.from_numpy(d32).cuda()
+    plan.set_ic(dk)
+    F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    I = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
+    pin.pin_profile(plan.handle, 1)
+
+    def step():
+        pin.pin_collapse_times(plan.handle, F.data_ptr(), I.data_ptr(), 1)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    pass_ms = np.zeros(3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            pass_ms += np.array(pin.pin_pass_times(plan.handle))  # waits for the step
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    updates = n ** 3 * S
+    value = updates * ws / (ms / 1e3)
+
+    # end to end through the public API with host buffers: pinned delta(k) in,
+    # F_max and scale index out, copies inside the timed region
+    pin.pin_profile(plan.handle, 0)
+    hd = torch.from_numpy(d32).pin_memory()
+    hF = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    hI = torch.empty((n, n, n), dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)
+    pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)  # warm graph
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)
+        pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    barrier()
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    stats = plan.stats()
+
+    # roofline of the dominant pass (algorithmic bytes per launch, one launch per radius)
+    H = n * n * (n // 2 + 1)
+    alg = {"x": (1 + 3) * 8 * H, "y": (3 + 6) * 8 * H, "z": 6 * 8 * H + 16 * n ** 3}
+    per_launch_ms = pass_ms / (args.steps * S)
+    names = ["x", "y", "z"]
+    dom = int(np.argmax(per_launch_ms))
+    peak, peak_kind = _peaks()
+    achieved = alg[names[dom]] / (per_launch_ms[dom] / 1e3) / 1e9
+    passes = {nm: {"ms_per_launch": float(per_launch_ms[i]),
+                   "alg_bytes_per_launch": alg[nm],
+                   "gbs": alg[nm] / (per_launch_ms[i] / 1e3) / 1e9,
+                   "frac": alg[nm] / (per_launch_ms[i] / 1e3) / 1e9 / peak}
+              for i, nm in enumerate(names)}
+    if ws > 1:
+        dist.barrier()
+    if rank == 0:
+        cb = cpu_baseline(S) if ws == 1 and not args.no_cpu else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(),
+            "roofline": {"bound": "hbm", "kernel": "k_pass_" + names[dom],
+                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "passes": passes},
+            "cpu_baseline": cb,
+            "e2e": {"value": updates * ws / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(d32.nbytes), "d2h_bytes_per_step": int(8 * n ** 3)},
+            "gpu_launches": int(args.steps * pin.pin_kernels_per_call(plan.handle)),
+            "clocks": clk.summary(),
+            "fp64_redo": {"eig": stats["eig_fp64_redo"], "root": stats["root_fp64_redo"],
+                          "particle_scales": int(stats["collapse_calls"]) * updates},
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

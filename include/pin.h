@@ -1,0 +1,142 @@
+/*
+ * pin.h -- C-ABI of libpin.so, the GB300 (sm_103a) collapse-time path of the
+ * PINOCCHIO method (Monaco et al. 2013, Sec. 2.1.1 "Collapse times").
+ *
+ * The problem, as the paper states it: a Gaussian linear density field
+ * delta_l on an N^3 grid of side L (Sec. 2.1.1, Eq. "deltal") is smoothed on a
+ * set of radii R with a Gaussian filter; for each R a series of FFTs gives the
+ * deformation tensor (Hessian of the peculiar potential), and per grid point
+ * ("particle") the ellipsoidal truncation of third-order LPT with its
+ * quasi-spherical correction gives the inverse collapse time F = 1/D(t_coll)
+ * (Eq. F).  Each particle keeps the highest F along its trajectory, F_max, and
+ * the radius R_max at which it was reached.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a pin_status; nothing throws across the ABI.  The text
+ *    of the last error of a plan is available from pin_last_error().
+ *  - The caller owns every input and output buffer; the plan owns all device
+ *    workspace (pin_footprint_bytes() tells how much).
+ *  - Half-spectra are [N][N][N/2+1] complex, row major, index
+ *    (ix*N + iy)*(N/2+1) + iz; the signed wavenumber index of i is i for
+ *    i < N/2 and i - N otherwise (the Nyquist index is -N/2), k = 2 pi s / L
+ *    with L in Mpc/h.  DFT convention: d(q) = N^-3 sum_k D(k) e^{+i k.q}; the
+ *    kz = 0 and kz = N/2 planes must be Hermitian (D(-kx,-ky) = conj D(kx,ky)).
+ *  - Real fields are [N][N][N] row major, q = (x*N + y)*N + z.
+ *  - Calls on one plan are not re-entrant; different plans may be used from
+ *    different threads.  Work is enqueued on the plan's CUDA stream.
+ *  - No call makes a device wait without bound: pin_sync() takes a timeout.
+ */
+#ifndef PIN_H
+#define PIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pin_plan_s* pin_plan_t;
+
+typedef enum {
+  PIN_OK = 0,
+  PIN_EINVAL = 1,   /* bad argument: size, radius, pointer, dtype, scale index */
+  PIN_ENOMEM = 2,   /* device allocation failed (nothing is left allocated) */
+  PIN_ECUDA = 3,    /* a CUDA runtime call failed; see pin_last_error() */
+  PIN_EBUSY = 4,    /* reserved for admission control above this library */
+  PIN_ETIMEOUT = 5, /* pin_sync() expired before the plan's work finished */
+  PIN_ESTATE = 6    /* call out of order, e.g. collapse times before pin_set_ic */
+} pin_status;
+
+enum { PIN_CORR_NONE = 0, PIN_CORR_SPHERE = 1 };
+enum { PIN_FP32_FALLBACK64 = 0 };
+enum { PIN_C64 = 0, PIN_C128 = 1 };
+
+typedef struct {
+  int nx, ny, nz;        /* grid; must be equal, N in {8,16,32,48,64,96,128,192,256,384,512,768} */
+  double box;            /* side L in Mpc/h, > 0 */
+  int nscales;           /* number of radii S, 1..64 */
+  const double* radii;   /* S radii in Mpc/h (Gaussian sigma, >= 0); copied at pin_plan;
+                            processed in the given order, index 0 first (callers
+                            normally give the largest radius first, as the
+                            trajectories of Sec. 2.1.1 run from large to small R) */
+  int correction;        /* PIN_CORR_SPHERE (quasi-spherical correction, default) or
+                            PIN_CORR_NONE (pure ellipsoidal 3LPT truncation) */
+  int precision;         /* PIN_FP32_FALLBACK64: FP32 FFTs and collapse, FP64 redo of
+                            near-degenerate eigenvalues and near-tangent roots */
+  void* stream;          /* cudaStream_t to run on, or NULL for a plan-owned stream */
+} pin_plan_desc;
+
+/* Runtime counters of a plan (cumulative over its pin_collapse_times calls). */
+typedef struct {
+  uint64_t eig_fp64_redo;   /* particle-scales redone in FP64 for a near-degenerate pair */
+  uint64_t root_fp64_redo;  /* particle-scales redone in FP64 for a near-tangent root */
+  uint64_t collapse_calls;  /* completed pin_collapse_times calls */
+} pin_stats;
+
+/* Creates a plan: validates the description, allocates the device workspace
+ * on the current CUDA device, and builds the per-radius filter tables.
+ * On error *out is NULL and nothing stays allocated. */
+pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d);
+
+/* Device bytes a plan with this description would allocate (0 if invalid). */
+size_t pin_footprint_bytes(const pin_plan_desc* d);
+
+/* Loads the linear density field delta(k) (Sec. 2.1.1, Eq. "deltal"), a
+ * half-spectrum as described above, dtype PIN_C64 (interleaved float) or
+ * PIN_C128 (interleaved double, rounded to FP32 on the device), from host
+ * memory (on_device = 0) or device memory (on_device = 1).  The data are
+ * copied; the caller may reuse its buffer when the call returns (host input)
+ * or once the plan's stream has passed this point (device input). */
+pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_device);
+
+/* Runs the whole collapse-time loop over all radii (Sec. 2.1.1): filter,
+ * inverse 3D FFTs of the six Hessian components, eigenvalues, collapse time F,
+ * running maximum.  Outputs (caller-owned, N^3 each, real-field layout):
+ *   F_max[q]     highest F over all radii, 0 if the particle never collapses;
+ *   scale_idx[q] index of the radius where F_max was reached (first such
+ *                index on exact ties), -1 if never collapses.
+ * on_device = 1: both are device pointers; the call only enqueues work and
+ * returns (use pin_sync or the stream).  on_device = 0: host pointers; the
+ * call returns when the results are in host memory. */
+pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, int on_device);
+
+/* The six real components of the deformation tensor phi_ij(q) at radius
+ * index `scale` (the a1-a2 steps alone), out6 = [6][N^3] floats in the order
+ * xx, yy, zz, xy, xz, yz.  Same on_device semantics as pin_collapse_times. */
+pin_status pin_hessian(pin_plan_t p, int scale, float* out6, int on_device);
+
+/* Zel'dovich (first-order LPT) displacement of the unsmoothed field,
+ * psi(k) = i k delta(k) / k^2 (so that delta = -div psi), Sec. 2.1.2:
+ * out psi = [3][N^3] floats (x, y, z components, Mpc/h).  Odd-order Nyquist
+ * modes are zeroed.  Same on_device semantics as pin_collapse_times. */
+pin_status pin_displacements(pin_plan_t p, float* psi, int on_device);
+
+/* Waits for the plan's enqueued work, polling; PIN_ETIMEOUT after timeout_ns
+ * nanoseconds (timeout_ns < 0: no limit).  The device is never made to wait. */
+pin_status pin_sync(pin_plan_t p, int64_t timeout_ns);
+
+pin_status pin_get_stats(pin_plan_t p, pin_stats* out);
+
+/* Number of kernels one pin_collapse_times call launches (for accounting). */
+int pin_kernels_per_call(pin_plan_t p);
+
+/* Measurement hooks.  pin_profile(p, 1) makes later pin_collapse_times calls
+ * record CUDA events around each pass of each radius (on the plan's stream,
+ * inside its graph); pin_pass_times() then waits for the plan's work and
+ * returns, for the last completed call, the device time in milliseconds summed
+ * over radii of the x pass (filter + transform), the y pass and the z pass
+ * (c2r + eigenvalues + collapse + running max): ms3[0..2]. */
+pin_status pin_profile(pin_plan_t p, int enable);
+pin_status pin_pass_times(pin_plan_t p, double* ms3);
+
+const char* pin_strerror(pin_status s);
+const char* pin_last_error(pin_plan_t p);
+
+/* Releases the plan and its device workspace (waits for its work first). */
+void pin_destroy(pin_plan_t p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

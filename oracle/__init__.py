@@ -36,6 +36,9 @@ def lib():
         L.or_hessian_point.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_hessian_point.restype = ctypes.c_double
+        L.or_displacement.argtypes = [_dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.or_hessian_points.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp]
         L.or_eig3.argtypes = [_dp, _dp]
         L.or_axis_coeffs.argtypes = [_dp, ctypes.c_int, _dp]
         L.or_first_root.argtypes = [_dp]
@@ -92,10 +95,33 @@ def hessian(delta_half, box, radius):
     return out, mi.value
 
 
+def displacement(delta_half, box):
+    """(3, n, n, n) FP64 Zel'dovich displacement psi = i k delta / k^2."""
+    d = _c128(delta_half)
+    n = d.shape[0]
+    out = np.empty((3, n, n, n), dtype=np.float64)
+    rc = lib().or_displacement(_p(d.view(np.float64)), n, box, _p(out))
+    if rc:
+        raise ValueError("or_displacement failed: %d" % rc)
+    return out
+
+
 def hessian_point(delta_half, box, radius, comp, q):
     d = _c128(delta_half)
     return lib().or_hessian_point(_p(d.view(np.float64)), d.shape[0], box, radius, comp,
                                   int(q[0]), int(q[1]), int(q[2]))
+
+
+def hessian_points(delta_half, box, radius, q_list):
+    """(npts, 6) Hessian components at flat grid indices q by direct summation."""
+    d = _c128(delta_half)
+    q = np.ascontiguousarray(q_list, dtype=np.int64)
+    out = np.empty((q.size, 6))
+    rc = lib().or_hessian_points(_p(d.view(np.float64)), d.shape[0], box, radius, q.size,
+                                 _p(q, ctypes.c_longlong), _p(out))
+    if rc:
+        raise ValueError("or_hessian_points failed: %d" % rc)
+    return out
 
 
 def eig3(h6):

@@ -238,6 +238,104 @@ double or_hessian_point(const double* delta_half_ri, int n, double box, double r
   return total / ((double)n * n * n);
 }
 
+/* All six components at several grid points by the direct sum over every
+ * mode, phi_c(q) = N^-3 sum_k T_c(k) e^{i k.q} (the half-spectrum's modes with
+ * 0 < kz < n/2 counted twice).  e^{i k.q} is the product of three per-axis
+ * phases, tabulated per point.  out is [npts][6]. */
+int or_hessian_points(const double* delta_half_ri, int n, double box, double radius, int npts,
+                      const long long* q_list, double* out) {
+  const double complex* half = (const double complex*)delta_half_ri;
+  const int nh = n / 2 + 1;
+  const double kf = 2.0 * M_PI / box;
+  double complex* ph = malloc(sizeof(double complex) * (size_t)npts * 3 * n);
+  if (!ph) return -2;
+  for (int p = 0; p < npts; ++p) {
+    long long q = q_list[p];
+    int qz = (int)(q % n), qy = (int)((q / n) % n), qx = (int)(q / ((long long)n * n));
+    int qq[3] = {qx, qy, qz};
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < n; ++i) {
+        double ang = 2.0 * M_PI * (double)(((long long)i * qq[a]) % n) / n;
+        ph[((size_t)p * 3 + a) * n + i] = cos(ang) + I * sin(ang);
+      }
+  }
+  for (int i = 0; i < npts * 6; ++i) out[i] = 0.0;
+#pragma omp parallel
+  {
+    double* acc = calloc((size_t)npts * 6, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+    for (int ix = 0; ix < n; ++ix) {
+      for (int iy = 0; iy < n; ++iy) {
+        for (int iz = 0; iz < nh; ++iz) {
+          int s[3] = {signed_index(ix, n), signed_index(iy, n), iz < n / 2 ? iz : -(n / 2)};
+          double k[3] = {kf * s[0], kf * s[1], kf * s[2]};
+          double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+          if (k2 == 0.0) continue;
+          double w = exp(-0.5 * k2 * radius * radius) / k2;
+          double mult[6];
+          for (int c = 0; c < 6; ++c) {
+            int ci = COMP_I[c], cj = COMP_J[c];
+            int nyq = (ci != cj) && (s[ci] == -n / 2 || s[cj] == -n / 2);
+            mult[c] = nyq ? 0.0 : k[ci] * k[cj] * w;
+          }
+          double complex d = half[((size_t)ix * n + iy) * nh + iz];
+          double weight = (iz == 0 || iz == n / 2) ? 1.0 : 2.0;
+          for (int p = 0; p < npts; ++p) {
+            const double complex* pp = ph + (size_t)p * 3 * n;
+            double re = weight * creal(d * pp[ix] * pp[n + iy] * pp[2 * n + iz]);
+            for (int c = 0; c < 6; ++c) acc[p * 6 + c] += mult[c] * re;
+          }
+        }
+      }
+    }
+#pragma omp critical
+    for (int i = 0; i < npts * 6; ++i) out[i] += acc[i];
+    free(acc);
+  }
+  const double norm = 1.0 / ((double)n * n * n);
+  for (int i = 0; i < npts * 6; ++i) out[i] *= norm;
+  free(ph);
+  return 0;
+}
+
+/* Zel'dovich displacement of the unsmoothed field (Sec. 2.1.2: particles
+ * and halos are displaced with the ZA, first-order LPT): x = q + psi with
+ * psi = -grad phi and del^2 phi = delta, i.e. psi_i(k) = i k_i delta(k) / k^2,
+ * so that delta = -div psi.  A mode whose k_i sits on the Nyquist index is
+ * zeroed for component i (the odd multiplier breaks Hermitian symmetry). */
+int or_displacement(const double* delta_half_ri, int n, double box, double* out3) {
+  if (n < 2 || (n & 1)) return -1;
+  const double complex* half = (const double complex*)delta_half_ri;
+  const int nh = n / 2 + 1;
+  const size_t n3 = (size_t)n * n * n;
+  const double kf = 2.0 * M_PI / box;
+  double complex* full = malloc(sizeof(double complex) * n3);
+  if (!full) return -2;
+  for (int c = 0; c < 3; ++c) {
+#pragma omp parallel for schedule(static)
+    for (int ix = 0; ix < n; ++ix) {
+      for (int iy = 0; iy < n; ++iy) {
+        for (int iz = 0; iz < n; ++iz) {
+          int mirrored = iz > n / 2;
+          size_t src = mirrored ? ((size_t)((n - ix) % n) * n + (n - iy) % n) * nh + (n - iz)
+                                : ((size_t)ix * n + iy) * nh + iz;
+          int s[3] = {signed_index(ix, n), signed_index(iy, n), signed_index(iz, n)};
+          double k[3] = {kf * s[0], kf * s[1], kf * s[2]};
+          double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+          double complex d = mirrored ? conj(half[src]) : half[src];
+          double complex t = 0.0;
+          if (k2 > 0.0 && s[c] != -n / 2) t = I * k[c] / k2 * d;
+          full[((size_t)ix * n + iy) * n + iz] = t;
+        }
+      }
+    }
+    idft3d(full, n);
+    for (size_t q = 0; q < n3; ++q) out3[c * n3 + q] = creal(full[q]);
+  }
+  free(full);
+  return 0;
+}
+
 /* ------------------------------------------------------- eigenvalues -- */
 
 /* Cyclic Jacobi on a symmetric 3x3 matrix; eigenvalues sorted descending. */

@@ -16,6 +16,9 @@ int or_hessian(const double* delta_half_ri, int n, double box, double radius, do
                double* max_imag);
 double or_hessian_point(const double* delta_half_ri, int n, double box, double radius,
                         int comp, int qx, int qy, int qz);
+int or_hessian_points(const double* delta_half_ri, int n, double box, double radius, int npts,
+                      const long long* q_list, double* out);
+int or_displacement(const double* delta_half_ri, int n, double box, double* out3);
 void or_eig3(const double* h6, double* lam);
 void or_axis_coeffs(const double* lam, int i, double* c);
 double or_first_root(const double* c);

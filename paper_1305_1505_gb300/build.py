@@ -40,7 +40,7 @@ def _stale(target, deps):
 def cmd_pin(extra=()):
     return ([NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared",
                              "-Xcompiler", "-fPIC", "-I", INC, "-I", os.path.join(PKG, "csrc"),
-                             "-o", LIBPIN] + list(extra) + _sources_pin() + ["-lcuda"])
+                             "-o", LIBPIN] + list(extra) + _sources_pin())
 
 
 def cmd_ic():

@@ -1,0 +1,166 @@
+// Per-particle eigenvalues of the deformation tensor and the ellipsoidal
+// collapse time F = 1 / D(t_coll) (Sec. 2.1.1, Eq. F), templated on the
+// arithmetic type so that the same code runs in FP32 and, for the rare
+// ill-conditioned particles, in FP64.
+//
+// Collapse model (ellipsoidal truncation of third-order LPT with the growing
+// mode D as the clock; the paper cites the formulas to earlier work, this is
+// the reading used throughout): in the eigenframe, with mu1 = sum lambda,
+// mu2 = sum_{i<j} lambda_i lambda_j, mu3 = prod lambda and
+// e_i = lambda_i (lambda_j + lambda_k) / 2, axis i is compressed by
+//   a_i(D) = c1 D + c2 D^2 + c3 D^3,
+//   c1 = lambda_i, c2 = (3/7) e_i,
+//   c3 = (10/84)(lambda_i (e_j + e_k) + e_i (lambda_j + lambda_k)) - mu3 / 9,
+// and orbit crossing of the first axis is the smallest D > 0 with a_i(D) = 1
+// over the three axes.  Dividing a_i(D) = 1 by D^3 turns it into the monic
+// cubic in F = 1/D
+//   g_i(F) = F^3 - c1 F^2 - c2 F - c3 = 0,
+// so the smallest positive D is the LARGEST positive real root F of g_i, and
+// F = max_i F_i (0 when no axis collapses).  That root is taken in closed form
+// (Cardano / trigonometric) and polished by Newton steps on g_i.
+//
+// Quasi-spherical correction (Sec. 2.1.1): for mu1 > 0,
+//   F += mu1 (1/delta_c - 1/x3) exp(-(eps/0.1)^2),  eps = (lambda1 - lambda3)/|mu1|,
+// which makes a sphere collapse exactly at F = delta/delta_c; x3 is the
+// uncorrected spherical root (x/3 + x^2/21 + 23 x^3/1701 = 1).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pin {
+
+template <typename T> struct M;
+template <> struct M<float> {
+  __device__ __forceinline__ static float sqrt_(float x) { return sqrtf(x); }
+  __device__ __forceinline__ static float acos_(float x) { return acosf(x); }
+  __device__ __forceinline__ static float cos_(float x) { return cosf(x); }
+  __device__ __forceinline__ static float cbrt_(float x) { return cbrtf(x); }
+  __device__ __forceinline__ static float exp_(float x) { return expf(x); }
+  __device__ __forceinline__ static float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+};
+template <> struct M<double> {
+  __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
+  __device__ __forceinline__ static double acos_(double x) { return acos(x); }
+  __device__ __forceinline__ static double cos_(double x) { return cos(x); }
+  __device__ __forceinline__ static double cbrt_(double x) { return cbrt(x); }
+  __device__ __forceinline__ static double exp_(double x) { return exp(x); }
+  __device__ __forceinline__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
+};
+
+// Closed-form eigenvalues of the symmetric 3x3 matrix
+// h = (xx, yy, zz, xy, xz, yz), sorted lam[0] >= lam[1] >= lam[2]
+// (trigonometric solution of the characteristic cubic, Smith 1961).
+// Returns |r| = |det(B)|/2, B = (A - qI)/p; |r| -> 1 marks a near-degenerate
+// pair, whose split the trigonometric form resolves poorly in FP32.
+template <typename T>
+__device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
+  using F = M<T>;
+  const T q = (h[0] + h[1] + h[2]) / T(3);
+  const T b0 = h[0] - q, b1 = h[1] - q, b2 = h[2] - q;
+  const T off = h[3] * h[3] + h[4] * h[4] + h[5] * h[5];
+  const T p2 = b0 * b0 + b1 * b1 + b2 * b2 + T(2) * off;
+  if (!(p2 > T(0))) {
+    lam[0] = lam[1] = lam[2] = q;
+    return T(1);
+  }
+  const T p = F::sqrt_(p2 / T(6));
+  // det(A - qI)
+  const T det = b0 * (b1 * b2 - h[5] * h[5]) - h[3] * (h[3] * b2 - h[5] * h[4]) +
+                h[4] * (h[3] * h[5] - b1 * h[4]);
+  T r = det / (T(2) * p * p * p);
+  r = r > T(1) ? T(1) : (r < T(-1) ? T(-1) : r);
+  const T phi = F::acos_(r) / T(3);
+  const T two_pi_3 = T(2.0943951023931954923);
+  const T l0 = q + T(2) * p * F::cos_(phi);
+  const T l2 = q + T(2) * p * F::cos_(phi + two_pi_3);
+  lam[0] = l0;
+  lam[2] = l2;
+  lam[1] = T(3) * q - l0 - l2;
+  return r < T(0) ? -r : r;
+}
+
+// Largest real root of g(F) = F^3 - c1 F^2 - c2 F - c3, clamped at 0 from
+// below (no positive root: the axis never collapses).  kappa receives
+// |g'(F)| / (3F^2 + 2|c1|F + |c2|), small near a tangent crossing.
+template <typename T>
+__device__ __forceinline__ T largest_root(T c1, T c2, T c3, T& kappa) {
+  using F = M<T>;
+  const T s = c1 / T(3);
+  const T p = -c2 - c1 * s;                                   // b - a^2/3
+  const T q = -c3 - c1 * c2 / T(3) - T(2) * c1 * s * s;        // 2a^3/27 - ab/3 + c
+  const T hq = q / T(2), tp = p / T(3);
+  const T disc = hq * hq + tp * tp * tp;
+  T t;
+  if (disc <= T(0) && p < T(0)) {
+    // three real roots t_k = m cos(theta/3 - 2 pi k/3); the largest is k = 0
+    const T m = T(2) * F::sqrt_(-tp);
+    T arg = T(3) * q / (p * m);
+    arg = arg > T(1) ? T(1) : (arg < T(-1) ? T(-1) : arg);
+    t = m * F::cos_(F::acos_(arg) / T(3));
+  } else {
+    // one real root: t = u - p/(3u), u the cube root of larger magnitude
+    const T sd = F::sqrt_(disc > T(0) ? disc : T(0));
+    const T w = hq >= T(0) ? -hq - sd : -hq + sd;
+    const T u = F::cbrt_(w);
+    t = (u != T(0)) ? u - tp / u : T(0);
+  }
+  T x = t + s;
+  // Newton polish on g
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const T g = ((x - c1) * x - c2) * x - c3;
+    const T dg = (T(3) * x - T(2) * c1) * x - c2;
+    if (dg != T(0)) {
+      const T nx = x - g / dg;
+      // stay at or above the largest root: g' > 0 there
+      x = nx;
+    }
+  }
+  const T dg = (T(3) * x - T(2) * c1) * x - c2;
+  const T ac1 = c1 < T(0) ? -c1 : c1, ac2 = c2 < T(0) ? -c2 : c2, ax = x < T(0) ? -x : x;
+  const T scale = T(3) * x * x + T(2) * ac1 * ax + ac2;
+  kappa = scale > T(0) ? (dg < T(0) ? -dg : dg) / scale : T(1);
+  return x > T(0) ? x : T(0);
+}
+
+template <typename T>
+struct CollapseConsts {
+  T dcorr;   // 1/delta_c - 1/x3
+  int correction;
+};
+
+// F for sorted eigenvalues lam; kappa_min receives the conditioning of the
+// root that set F (1 when nothing collapses).
+template <typename T>
+__device__ __forceinline__ T collapse_from_eigs(const T lam[3], const CollapseConsts<T>& cc,
+                                                T& kappa_min) {
+  using F = M<T>;
+  const T mu1 = lam[0] + lam[1] + lam[2];
+  const T mu3 = lam[0] * lam[1] * lam[2];
+  T e[3];
+  e[0] = lam[0] * (lam[1] + lam[2]) / T(2);
+  e[1] = lam[1] * (lam[0] + lam[2]) / T(2);
+  e[2] = lam[2] * (lam[0] + lam[1]) / T(2);
+  T best = T(0);
+  kappa_min = T(1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    const T c1 = lam[i];
+    const T c2 = T(3) / T(7) * e[i];
+    const T c3 = T(10) / T(84) * (lam[i] * (e[j] + e[k]) + e[i] * (lam[j] + lam[k])) - mu3 / T(9);
+    T kap;
+    const T Fi = largest_root<T>(c1, c2, c3, kap);
+    if (Fi > best) {
+      best = Fi;
+      kappa_min = kap;
+    }
+  }
+  if (cc.correction && mu1 > T(0)) {
+    const T eps = (lam[0] - lam[2]) / mu1;
+    const T z = eps / T(0.1);
+    best += mu1 * cc.dcorr * F::exp_(-z * z);
+  }
+  return best;
+}
+
+}  // namespace pin

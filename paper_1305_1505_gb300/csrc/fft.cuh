@@ -1,0 +1,211 @@
+// Register-resident inverse DFTs and the two-level column FFT used by every
+// pass of the collapse-time path (Sec. 2.1.1: "for each smoothing radius the
+// code performs a series of FFTs to compute the deformation tensor").
+//
+// Convention: inverse transforms, X[k] = sum_n x[n] exp(+2 pi i n k / N), no
+// normalisation here (the 1/N of each axis is folded into the per-axis
+// multiplier tables).
+//
+// Two-level decomposition of a length-N line, N = E * P:
+//   n = p + P t   (p in [0,P): thread of the line, t in [0,E): register slot)
+//   k = k1 + E k2 (k1 in [0,E), k2 in [0,P))
+//   X[k1 + E k2] = sum_p w_P^{p k2} w_N^{p k1} sum_t w_E^{t k1} x[p + P t]
+// Level 1 is a length-E DFT entirely in one thread's registers; after the
+// twiddle w_N^{p k1} one shared-memory exchange hands every thread E/P values
+// of k1 with all P values of p, and level 2 is E/P length-P DFTs, again in
+// registers.  One shared-memory round trip per line and transform.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pin {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }  // a * i
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// exp(+2 pi i j / n) for the register-DFT sizes, filled once per device from
+// double precision host values (pin.cu).  Indices are compile-time constants
+// after unrolling, so every read is a constant-bank operand.
+constexpr int kTwSizes[] = {4, 8, 12, 16, 24, 32, 48, 64};
+constexpr int kTwTotal = 4 + 8 + 12 + 16 + 24 + 32 + 48 + 64;
+__host__ __device__ constexpr int tw_offset(int n) {
+  return n == 4 ? 0 : n == 8 ? 4 : n == 12 ? 12 : n == 16 ? 24 : n == 24 ? 40
+       : n == 32 ? 64 : n == 48 ? 96 : n == 64 ? 144 : -1;
+}
+// Defined here (one translation unit includes this header).
+__constant__ float2 c_tw[kTwTotal];
+
+template <int N>
+__device__ __forceinline__ float2 twc(int j) {
+  static_assert(tw_offset(N) >= 0, "no twiddle table for this size");
+  return c_tw[tw_offset(N) + j];
+}
+
+template <int N> struct DFT;
+
+template <> struct DFT<1> {
+  __device__ __forceinline__ static void run(float2 (&)[1]) {}
+};
+
+template <> struct DFT<2> {
+  __device__ __forceinline__ static void run(float2 (&v)[2]) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <> struct DFT<3> {
+  __device__ __forceinline__ static void run(float2 (&v)[3]) {
+    // w = exp(2 pi i / 3) = -1/2 + i sqrt(3)/2
+    const float h = 0.86602540378443864676f;
+    float2 a = v[0], s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    float2 m = make_float2(fmaf(-0.5f, s.x, a.x), fmaf(-0.5f, s.y, a.y));
+    v[0] = cadd(a, s);
+    v[1] = make_float2(m.x - h * d.y, m.y + h * d.x);
+    v[2] = make_float2(m.x + h * d.y, m.y - h * d.x);
+  }
+};
+
+template <> struct DFT<4> {
+  __device__ __forceinline__ static void run(float2 (&v)[4]) {
+    float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    float2 s13 = cadd(v[1], v[3]), d13 = cmuli(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  }
+};
+
+// Composite N = R * M, natural order in and out:
+//   n = M r + m, k = k1 + R k2:  X[k1 + R k2] = sum_m w_M^{m k2} w_N^{m k1} DFT_R(x[M r + m])[k1]
+template <int R, int M>
+__device__ __forceinline__ void dft_split(float2 (&v)[R * M]) {
+  constexpr int N = R * M;
+  float2 y[N];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    float2 t[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) t[r] = v[M * r + m];
+    DFT<R>::run(t);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) y[M * k1 + m] = (m * k1 == 0) ? t[k1] : cmul(t[k1], twc<N>(m * k1));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R; ++k1) {
+    float2 t[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) t[m] = y[M * k1 + m];
+    DFT<M>::run(t);
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) v[k1 + R * k2] = t[k2];
+  }
+}
+
+template <int N> struct SplitOf;
+template <> struct SplitOf<8> { static constexpr int R = 2; };
+template <> struct SplitOf<12> { static constexpr int R = 3; };
+template <> struct SplitOf<16> { static constexpr int R = 4; };
+template <> struct SplitOf<24> { static constexpr int R = 3; };
+template <> struct SplitOf<32> { static constexpr int R = 4; };
+template <> struct SplitOf<48> { static constexpr int R = 3; };
+template <> struct SplitOf<64> { static constexpr int R = 4; };
+
+template <int N> struct DFT {
+  __device__ __forceinline__ static void run(float2 (&v)[N]) {
+    dft_split<SplitOf<N>::R, N / SplitOf<N>::R>(v);
+  }
+};
+
+// Per-size decomposition N = E * P of a line (E register slots per thread,
+// P threads per line, P divides E so that level 2 hands each thread E/P
+// whole length-P transforms).
+template <int N> struct Shape;
+template <> struct Shape<8>    { static constexpr int E = 8,  P = 1; };
+template <> struct Shape<16>   { static constexpr int E = 16, P = 1; };
+template <> struct Shape<32>   { static constexpr int E = 8,  P = 4; };
+template <> struct Shape<48>   { static constexpr int E = 12, P = 4; };
+template <> struct Shape<64>   { static constexpr int E = 8,  P = 8; };
+template <> struct Shape<96>   { static constexpr int E = 24, P = 4; };
+template <> struct Shape<128>  { static constexpr int E = 16, P = 8; };
+template <> struct Shape<192>  { static constexpr int E = 24, P = 8; };
+template <> struct Shape<256>  { static constexpr int E = 16, P = 16; };
+template <> struct Shape<384>  { static constexpr int E = 48, P = 8; };
+template <> struct Shape<512>  { static constexpr int E = 32, P = 16; };
+template <> struct Shape<768>  { static constexpr int E = 48, P = 16; };
+template <> struct Shape<1024> { static constexpr int E = 64, P = 16; };
+
+// Shared-memory layouts for the level-1 -> level-2 exchange of one tile of
+// lines.  Index of value (k1, p) of line c.
+//  - Strided lines (passes along x and y): consecutive lanes are consecutive
+//    lines (columns of a row-major array), layout [k1][p][c].
+//  - Contiguous lines (pass along z): consecutive lanes are consecutive p of
+//    one line, layout [c][k1][p] with the p extent padded to P+1 so that the
+//    level-2 reads (stride P+1) do not collide on a bank.
+template <int E, int P, int TC>
+struct XLayoutCols {
+  static constexpr int kSize = E * P * TC;
+  __device__ __forceinline__ static int at(int k1, int p, int c) { return (k1 * P + p) * TC + c; }
+};
+template <int E, int P, int NC>
+struct XLayoutLines {
+  static constexpr int kSize = NC * E * (P + 1);
+  __device__ __forceinline__ static int at(int k1, int p, int c) { return (c * E + k1) * (P + 1) + p; }
+};
+
+// Level-2 twiddles w_N^{p k1}, laid out [k1][p] in shared memory.
+template <int E, int P>
+__device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { return s_tw[k1 * P + p]; }
+
+// Inverse FFT of one line held as v[t] = x[p + P t] by thread p of the line.
+// On return v[i * P + k2] = X[(p + P i) + E k2] for i in [0, E/P), k2 in [0, P)
+// (for P == 1: v[k] = X[k]).  All threads of the block must call it; it
+// synchronises once inside and leaves the exchange buffer in use (callers
+// synchronise before writing s_x again).
+template <int N, class Layout>
+__device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c, float2* s_x,
+                                         const float2* s_tw) {
+  constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  DFT<E>::run(v);
+  if constexpr (P > 1) {
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) {
+      float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P>(s_tw, k1, p));
+      s_x[Layout::at(k1, p, c)] = z;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < E / P; ++i) {
+      float2 t[P];
+#pragma unroll
+      for (int q = 0; q < P; ++q) t[q] = s_x[Layout::at(p + P * i, q, c)];
+      DFT<P>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) v[i * P + k2] = t[k2];
+    }
+  } else {
+    (void)p; (void)c; (void)s_x; (void)s_tw;
+  }
+}
+
+// Output frequency of register slot j after fft_line.
+template <int N>
+__device__ __forceinline__ int fft_out_index(int p, int j) {
+  constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  if constexpr (P == 1) {
+    (void)p;
+    return j;
+  } else {
+    int i = j / P, k2 = j % P;
+    return p + P * i + E * k2;
+  }
+}
+
+}  // namespace pin

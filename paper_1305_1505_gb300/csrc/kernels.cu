@@ -1,0 +1,365 @@
+// The three passes of one smoothing radius (Sec. 2.1.1, Collapse times):
+//   x pass  : filter (x factors of W and k_i k_j) fused into the inverse DFT
+//             along x, three outputs;
+//   y pass  : y factors and the inverse DFT along y, six outputs;
+//   z pass  : z factors, complex-to-real inverse DFT along z of the six
+//             Hessian components (two per complex transform), then per grid
+//             point the eigenvalues, the collapse time F = 1/D_c and the
+//             running maximum F_max with its radius index, written in place.
+// Each thread block owns a tile of lines; every line is transformed with the
+// two-level register FFT of fft.cuh (one shared-memory exchange per line).
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "collapse.cuh"
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace pin {
+
+// ---------------------------------------------------------------- x pass --
+// Lines along x: column index col in [0, N*nhp) enumerates (ky, kz); element
+// (kx, col) sits at kx*N*nhp + col, so a row of TC columns is contiguous.
+template <int N, int TC>
+__global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_x(ArgsX a) {
+  constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  using L = XLayoutCols<E, P, TC>;
+  extern __shared__ float4 smem_raw[];
+  float2* s_x = reinterpret_cast<float2*>(smem_raw);
+  float2* s_tw = s_x + L::kSize;
+  float* s_m = reinterpret_cast<float*>(s_tw + E * P);  // [3][N] multipliers
+  __shared__ float2* s_dst[3];
+  __shared__ int s_xm[3];
+  const int tid = threadIdx.x, c = tid % TC, p = tid / TC;
+  for (int i = tid; i < E * P; i += TC * P) s_tw[i] = a.tw[i];
+  for (int i = tid; i < 3 * N; i += TC * P) s_m[i] = a.mult[i];
+  if (tid < 3) {
+    s_dst[tid] = a.dst[tid];
+    s_xm[tid] = a.xm[tid];
+  }
+  __syncthreads();
+  const int ncols = N * a.nhp;
+  const int col = blockIdx.x * TC + c;
+  const bool ok = col < ncols;
+  const float2* src = a.src + (ok ? col : 0) + p * ncols;
+  const int tstride = P * ncols;
+#pragma unroll 1
+  for (int f = 0; f < a.nout; ++f) {
+    const float* mt = s_m + s_xm[f] * N + p;
+    float2 v[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+      const float2 x = ok ? __ldg(src + t * tstride) : make_float2(0.f, 0.f);
+      v[t] = cscale(x, mt[P * t]);
+    }
+    fft_line<N, L>(v, p, c, s_x, s_tw);
+    float2* d = s_dst[f] + (ok ? col : 0);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int row = fft_out_index<N>(p, j);
+      if (ok) d[row * ncols] = v[j];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- y pass --
+// Lines along y: column col in [0, N*nhp) enumerates (x, kz); element
+// (ky, col) sits at (x*N + ky)*nhp + kz.
+template <int N, int TC>
+__global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_y(ArgsY a) {
+  constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  using L = XLayoutCols<E, P, TC>;
+  extern __shared__ float4 smem_raw[];
+  float2* s_x = reinterpret_cast<float2*>(smem_raw);
+  float2* s_tw = s_x + L::kSize;
+  float* s_m = reinterpret_cast<float*>(s_tw + E * P);  // [3][N] multipliers
+  __shared__ float2* s_dst[kMaxFields];
+  __shared__ const float2* s_src[kMaxFields];
+  __shared__ int s_ym[kMaxFields];
+  const int tid = threadIdx.x, c = tid % TC, p = tid / TC;
+  for (int i = tid; i < E * P; i += TC * P) s_tw[i] = a.tw[i];
+  for (int i = tid; i < 3 * N; i += TC * P) s_m[i] = a.mult[i];
+  if (tid < kMaxFields) {
+    s_dst[tid] = a.dst[tid];
+    s_src[tid] = a.src[a.sel[tid] < 3 ? a.sel[tid] : 0];
+    s_ym[tid] = a.ym[tid];
+  }
+  __syncthreads();
+  const int nhp = a.nhp;
+  const int ncols = N * nhp;
+  const int col = blockIdx.x * TC + c;
+  const bool ok = col < ncols;
+  const int x = ok ? col / nhp : 0, kz = ok ? col % nhp : 0;
+  const int base = x * N * nhp + kz;
+  const int tstride = P * nhp;
+#pragma unroll 1
+  for (int f = 0; f < a.nout; ++f) {
+    const float* mt = s_m + s_ym[f] * N + p;
+    const float2* s = s_src[f] + base + p * nhp;
+    float2 v[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+      const float2 xv = ok ? __ldg(s + t * tstride) : make_float2(0.f, 0.f);
+      v[t] = cscale(xv, mt[P * t]);
+    }
+    fft_line<N, L>(v, p, c, s_x, s_tw);
+    float2* d = s_dst[f] + base;
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int row = fft_out_index<N>(p, j);
+      if (ok) d[row * nhp] = v[j];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- z pass --
+// Lines along z: line index l = x*N + y, the half line src[f][l*nhp + kz],
+// kz in [0, N/2], is contiguous.  Fields are paired (A + iB) into one complex
+// length-N transform whose real and imaginary parts are the two real lines.
+template <int N, int LINES, bool DUMP>
+__global__ void __launch_bounds__(3 * LINES * Shape<N>::P) k_pass_z(ArgsZ a) {
+  constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  constexpr int NC = 3 * LINES;  // at most three pairs per line
+  using L = XLayoutLines<E, P, NC>;
+  extern __shared__ float4 smem_raw[];
+  float2* s_x = reinterpret_cast<float2*>(smem_raw);
+  constexpr int kXBytes = L::kSize * 8, kFBytes = LINES * 6 * N * 4;
+  constexpr int kBufBytes = kXBytes > kFBytes ? kXBytes : kFBytes;
+  float2* s_tw = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem_raw) + kBufBytes);
+  float* s_f = reinterpret_cast<float*>(smem_raw);
+  const int nthreads = NC * P;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < E * P; i += nthreads) s_tw[i] = a.tw[i];
+  __syncthreads();
+
+  const int npairs = (a.nfields + 1) / 2;
+  const int c = tid / P, p = tid % P;
+  const int ln = c / 3, pair = c % 3;
+  const int nlines = N * N;
+  const int line = blockIdx.x * LINES + ln;
+  const bool active = pair < npairs && line < nlines;
+  const int fa = 2 * pair, fb = 2 * pair + 1;
+  const bool hasb = active && fb < a.nfields;
+  const int nhp = a.nhp;
+
+  float2 v[E];
+  {
+    const float2* A = active ? a.src[fa] + (size_t)line * nhp : nullptr;
+    const float2* B = hasb ? a.src[fb] + (size_t)line * nhp : nullptr;
+    const float* ma = a.mult + (active ? a.zm[fa] : 0) * N;
+    const float* mb = a.mult + (hasb ? a.zm[fb] : 0) * N;
+    const bool ia = active && a.muli[fa], ib = hasb && a.muli[fb];
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+      const int n = p + P * t;
+      const int m = n <= N / 2 ? n : N - n;
+      float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
+      if (active) {
+        xa = cscale(__ldg(A + m), __ldg(ma + m));
+        if (ia) xa = cmuli(xa);
+      }
+      if (hasb) {
+        xb = cscale(__ldg(B + m), __ldg(mb + m));
+        if (ib) xb = cmuli(xb);
+      }
+      if (n == 0 || n == N / 2) {
+        xa.y = 0.f;
+        xb.y = 0.f;
+      } else if (n > N / 2) {
+        xa = cconj(xa);
+        xb = cconj(xb);
+      }
+      v[t] = make_float2(xa.x - xb.y, xa.y + xb.x);  // A + iB
+    }
+  }
+  fft_line<N, L>(v, p, c, s_x, s_tw);
+
+  if constexpr (DUMP) {
+    if (active) {
+      float* oa = a.out[fa] + (size_t)line * N;
+      float* ob = hasb ? a.out[fb] + (size_t)line * N : nullptr;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int z = fft_out_index<N>(p, j);
+        oa[z] = v[j].x;
+        if (hasb) ob[z] = v[j].y;
+      }
+    }
+    return;
+  } else {
+    __syncthreads();  // exchange buffer becomes the field buffer
+    if (pair < npairs) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int z = fft_out_index<N>(p, j);
+        s_f[(ln * 6 + fa) * N + z] = v[j].x;
+        s_f[(ln * 6 + fb) * N + z] = v[j].y;
+      }
+    }
+    __syncthreads();
+    CollapseConsts<float> ccf{a.dcorr_f, a.correction};
+    CollapseConsts<double> ccd{a.dcorr_d, a.correction};
+    for (int pt = tid; pt < LINES * N; pt += nthreads) {
+      const int l = pt / N, z = pt % N;
+      const int gl = blockIdx.x * LINES + l;
+      if (gl >= nlines) continue;
+      float h[6];
+#pragma unroll
+      for (int f = 0; f < 6; ++f) h[f] = s_f[(l * 6 + f) * N + z];
+      float lam[3];
+      const float rabs = eig3<float>(h, lam);
+      float kap;
+      float F = collapse_from_eigs<float>(lam, ccf, kap);
+      const bool redo_eig = rabs > 1.f - a.tau_eig;
+      const bool redo_root = kap < a.tau_root;
+      if (redo_eig || redo_root) {
+        double hd[6], ld[3], kd;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) hd[f] = (double)h[f];
+        eig3<double>(hd, ld);
+        F = (float)collapse_from_eigs<double>(ld, ccd, kd);
+        atomicAdd(a.counters + (redo_eig ? 0 : 1), 1ull);
+      }
+      const size_t q = (size_t)gl * N + z;
+      const float fm = a.fmax[q];
+      if (F > fm) {
+        a.fmax[q] = F;
+        a.idx[q] = a.scale;
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------------- dispatch --
+
+template <int N> struct Cfg {
+  static constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  static constexpr int TC = P >= 8 ? 16 : (P == 4 ? 32 : 64);
+  static constexpr int LINES = 64 / P;
+  static constexpr size_t smem_xy = (size_t)XLayoutCols<E, P, TC>::kSize * 8 + (size_t)E * P * 8 + (size_t)3 * N * 4;
+  static constexpr size_t xz = (size_t)XLayoutLines<E, P, 3 * LINES>::kSize * 8;
+  static constexpr size_t fz = (size_t)LINES * 6 * N * 4;
+  static constexpr size_t smem_z = (xz > fz ? xz : fz) + (size_t)E * P * 8;
+  static constexpr int threads_xy = TC * P;
+  static constexpr int threads_z = 3 * LINES * P;
+};
+
+template <int N>
+static cudaError_t set_attrs() {
+  using C = Cfg<N>;
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_pass_x<N, C::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass_y<N, C::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_pass_z<N, C::LINES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
+}
+
+template <int N>
+static PassShape shape_of() {
+  using C = Cfg<N>;
+  return PassShape{C::E, C::P, C::TC, C::LINES, C::smem_xy, C::smem_z, C::threads_xy, C::threads_z};
+}
+
+template <int N>
+static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
+  using C = Cfg<N>;
+  const long ncols = (long)N * a.nhp;
+  const unsigned grid = (unsigned)((ncols + C::TC - 1) / C::TC);
+  k_pass_x<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t run_y(const ArgsY& a, cudaStream_t st) {
+  using C = Cfg<N>;
+  const long ncols = (long)N * a.nhp;
+  const unsigned grid = (unsigned)((ncols + C::TC - 1) / C::TC);
+  k_pass_y<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t run_z(const ArgsZ& a, bool dump, cudaStream_t st) {
+  using C = Cfg<N>;
+  const long nlines = (long)N * N;
+  const unsigned grid = (unsigned)((nlines + C::LINES - 1) / C::LINES);
+  if (dump) k_pass_z<N, C::LINES, true><<<grid, C::threads_z, C::smem_z, st>>>(a);
+  else k_pass_z<N, C::LINES, false><<<grid, C::threads_z, C::smem_z, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define PIN_SIZES(X) X(8) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
+
+bool size_supported(int n) {
+  switch (n) {
+#define CASE(N) case N: return true;
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return false;
+  }
+}
+
+PassShape pass_shape(int n) {
+  switch (n) {
+#define CASE(N) case N: return shape_of<N>();
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return PassShape{};
+  }
+}
+
+cudaError_t prepare_kernels(int n) {
+  switch (n) {
+#define CASE(N) case N: return set_attrs<N>();
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_x(int n, const ArgsX& a, cudaStream_t st) {
+  switch (n) {
+#define CASE(N) case N: return run_x<N>(a, st);
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st) {
+  switch (n) {
+#define CASE(N) case N: return run_y<N>(a, st);
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st) {
+  switch (n) {
+#define CASE(N) case N: return run_z<N>(a, dump, st);
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t upload_constant_twiddles() {
+  float2 h[kTwTotal];
+  for (int n : kTwSizes) {
+    const int off = tw_offset(n);
+    for (int j = 0; j < n; ++j) {
+      const double ang = 2.0 * M_PI * (double)j / (double)n;
+      h[off + j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  }
+  return cudaMemcpyToSymbol(c_tw, h, sizeof(h));
+}
+
+}  // namespace pin

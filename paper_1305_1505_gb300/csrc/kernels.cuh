@@ -1,0 +1,84 @@
+// Launch interface of the collapse-time passes (kernels.cu).
+//
+// Spectral arrays are half-spectra stored [kx][ky][kz] with kz padded to an
+// even stride NHP >= N/2+1 (pad modes are zero), complex64.  The filtered
+// Hessian spectrum of Sec. 2.1.1,
+//   T_ij(k) = (k_i k_j / k^2) W(kR) delta(k),
+// is separable once Phi0 = delta / k^2 is formed (once per field):
+//   T_ij = mx(kx) my(ky) mz(kz) Phi0,   m in {W, k W, k^2 W} per axis
+// (W = exp(-k^2 R^2/2) = Wx Wy Wz, and k carries a zero on the Nyquist index
+// for the odd multipliers), so the x pass needs three transforms and only the
+// y and z passes carry all six components.
+#pragma once
+#include <cstddef>
+#include <cuda_runtime.h>
+
+namespace pin {
+
+constexpr int kMaxFields = 6;
+
+// x pass: for each output f, dst[f] = IDFT_x(mult[xm[f]] * src).
+struct ArgsX {
+  const float2* src;
+  float2* dst[3];
+  int xm[3];
+  int nout;
+  const float* mult;  // [3][N] multipliers of this radius (W, kW, k^2W, each / N)
+  const float2* tw;   // level-2 twiddles [E][P]
+  int nhp;
+};
+
+// y pass: dst[f] = IDFT_y(mult[ym[f]] * src[sel[f]]).
+struct ArgsY {
+  const float2* src[3];
+  float2* dst[kMaxFields];
+  int sel[kMaxFields];
+  int ym[kMaxFields];
+  int nout;
+  const float* mult;
+  const float2* tw;
+  int nhp;
+};
+
+// z pass: c2r of each field (times i where muli is set) after the z
+// multiplier, then either the collapse update or a dump of the real fields.
+struct ArgsZ {
+  const float2* src[kMaxFields];
+  int zm[kMaxFields];
+  int muli[kMaxFields];
+  int nfields;
+  const float* mult;
+  const float2* tw;
+  int nhp;
+  // collapse mode
+  float* fmax;
+  int* idx;
+  int scale;
+  int correction;
+  float dcorr_f;
+  double dcorr_d;
+  float tau_eig;   // FP64 redo when |r| > 1 - tau_eig
+  float tau_root;  // FP64 redo when kappa < tau_root
+  unsigned long long* counters;  // [0] eigen redo, [1] root redo
+  // dump mode
+  float* out[kMaxFields];
+};
+
+struct PassShape {
+  int E, P;
+  int tc;         // columns per block, x/y passes
+  int lines;      // lines per block, z pass
+  size_t smem_xy; // dynamic shared bytes, x/y passes
+  size_t smem_z;
+  int threads_xy, threads_z;
+};
+
+bool size_supported(int n);
+PassShape pass_shape(int n);
+cudaError_t prepare_kernels(int n);  // sets shared-memory attributes (once per device)
+cudaError_t launch_x(int n, const ArgsX& a, cudaStream_t st);
+cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st);
+cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st);
+cudaError_t upload_constant_twiddles();  // per device
+
+}  // namespace pin

@@ -1,0 +1,578 @@
+// C-ABI of the collapse-time path (declared in include/pin.h).
+//
+// A plan owns the device workspace of one grid size and radius list:
+//   phi0            Phi0(k) = delta(k) / k^2, half-spectrum, padded stride nhp
+//   U[3], V[6]      outputs of the x and y passes
+//   fmax, idx       running maximum of F and its radius index (Sec. 2.1.1)
+//   mult            per-radius axis multipliers {W, kW, k^2 W} / N
+// pin_collapse_times replays one CUDA graph holding the whole radius loop.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pin.h"
+
+using namespace pin;
+
+struct pin_plan_s {
+  int n = 0, nhp = 0, nscales = 0, correction = 1, precision = 0;
+  double box = 0.0;
+  std::vector<double> radii;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  PassShape shape{};
+  size_t spec_elems = 0;  // complex elements of one padded half-spectrum
+  float2* phi0 = nullptr;
+  float2* U = nullptr;    // 3 spectra
+  float2* V = nullptr;    // 6 spectra
+  float* fmax = nullptr;
+  int* idx = nullptr;
+  float* mult = nullptr;  // (nscales + 1) x 3 x n; the last set has R = 0
+  float2* tw = nullptr;
+  unsigned long long* counters = nullptr;  // [0] eig redo, [1] root redo
+  bool ic_set = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  uint64_t calls = 0;
+  double dcorr = 0.0;
+  bool profile = false;             // graph carries per-pass event records
+  std::vector<cudaEvent_t> events;  // 4 per radius: before x, after x, y, z
+  std::string last_error;
+};
+
+namespace {
+
+std::mutex g_init_mu;
+std::vector<int> g_tw_done;                 // per device
+std::vector<std::vector<int>> g_attr_done;  // per device, per size
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+
+pin_status fail(pin_plan_t p, pin_status s, const std::string& msg) {
+  if (p) p->last_error = msg;
+  return s;
+}
+
+pin_status cuda_fail(pin_plan_t p, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(p, e == cudaErrorMemoryAllocation ? PIN_ENOMEM : PIN_ECUDA, m);
+}
+
+#define PIN_CK(p, call)                                    \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((p), e_, #call); \
+  } while (0)
+
+int padded_half(int n) { return (n / 2 + 1 + 1) & ~1; }
+
+double delta_c_value() { return 3.0 / 20.0 * std::pow(12.0 * M_PI, 2.0 / 3.0); }
+
+// Uncorrected spherical collapse root: x/3 + x^2/21 + 23 x^3/1701 = 1, Newton
+// from x = 2 (the function is increasing and convex on x > 0).
+double x3_value() {
+  double x = 2.0;
+  for (int i = 0; i < 60; ++i) {
+    double f = x / 3.0 + x * x / 21.0 + 23.0 * x * x * x / 1701.0 - 1.0;
+    double d = 1.0 / 3.0 + 2.0 * x / 21.0 + 69.0 * x * x / 1701.0;
+    double nx = x - f / d;
+    if (nx == x) break;
+    x = nx;
+  }
+  return x;
+}
+
+bool validate(const pin_plan_desc* d, std::string* why) {
+  if (!d) { *why = "null descriptor"; return false; }
+  if (d->nx != d->ny || d->ny != d->nz) { *why = "non-cubic grids are not supported"; return false; }
+  if (!size_supported(d->nx)) { *why = "unsupported grid size " + std::to_string(d->nx); return false; }
+  if (!(d->box > 0.0) || !std::isfinite(d->box)) { *why = "box must be positive"; return false; }
+  if (d->nscales < 1 || d->nscales > 64) { *why = "nscales must be in 1..64"; return false; }
+  if (!d->radii) { *why = "null radii"; return false; }
+  for (int s = 0; s < d->nscales; ++s)
+    if (!(d->radii[s] >= 0.0) || !std::isfinite(d->radii[s])) { *why = "radii must be finite and >= 0"; return false; }
+  if (d->correction != PIN_CORR_NONE && d->correction != PIN_CORR_SPHERE) { *why = "bad correction mode"; return false; }
+  if (d->precision != PIN_FP32_FALLBACK64) { *why = "bad precision mode"; return false; }
+  return true;
+}
+
+size_t footprint(int n, int nscales) {
+  const size_t spec = (size_t)n * n * padded_half(n);
+  const size_t n3 = (size_t)n * n * n;
+  return spec * 8 * 10 + n3 * 8 + (size_t)(nscales + 1) * 3 * n * 4 + (size_t)n * 8 + 64;
+}
+
+// Per-axis multipliers for one radius: {W, k W, k^2 W} / n with
+// W = exp(-k^2 R^2 / 2), k = 2 pi s / L; k W is zero on the Nyquist index.
+void fill_mult(float* out, int n, double box, double radius) {
+  for (int i = 0; i < n; ++i) {
+    const int s = i < n / 2 ? i : i - n;
+    const double k = 2.0 * M_PI * s / box;
+    const double w = std::exp(-0.5 * k * k * radius * radius) / n;
+    out[0 * n + i] = (float)w;
+    out[1 * n + i] = (i == n / 2) ? 0.0f : (float)(k * w);
+    out[2 * n + i] = (float)(k * k * w);
+  }
+}
+
+__global__ void k_load_phi0(const void* src, int dtype, int n, int nhp, double box, float2* phi0) {
+  const int nh = n / 2 + 1;
+  const size_t total = (size_t)n * n * nhp;
+  const double kf = 2.0 * M_PI / box;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int iz = (int)(i % nhp);
+    const size_t r = i / nhp;
+    const int iy = (int)(r % n), ix = (int)(r / n);
+    float2 out = make_float2(0.f, 0.f);
+    if (iz < nh) {
+      const size_t j = r * nh + iz;
+      float2 d;
+      if (dtype == PIN_C64) {
+        d = reinterpret_cast<const float2*>(src)[j];
+      } else {
+        const double2 dd = reinterpret_cast<const double2*>(src)[j];
+        d = make_float2((float)dd.x, (float)dd.y);
+      }
+      const double sx = ix < n / 2 ? ix : ix - n, sy = iy < n / 2 ? iy : iy - n;
+      const double sz = iz < n / 2 ? iz : -(n / 2);
+      const double k2 = kf * kf * (sx * sx + sy * sy + sz * sz);
+      if (k2 > 0.0) {
+        const float inv = (float)(1.0 / k2);
+        out = make_float2(d.x * inv, d.y * inv);
+      }
+    }
+    phi0[i] = out;
+  }
+}
+
+pin_status ensure_device_init(pin_plan_t p) {
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  int dev = p->device;
+  if ((int)g_tw_done.size() <= dev) {
+    g_tw_done.resize(dev + 1, 0);
+    g_attr_done.resize(dev + 1);
+  }
+  if (!g_tw_done[dev]) {
+    PIN_CK(p, upload_constant_twiddles());
+    g_tw_done[dev] = 1;
+  }
+  auto& v = g_attr_done[dev];
+  if ((int)v.size() <= p->n) v.resize(p->n + 1, 0);
+  if (!v[p->n]) {
+    PIN_CK(p, prepare_kernels(p->n));
+    v[p->n] = 1;
+  }
+  return PIN_OK;
+}
+
+void release(pin_plan_t p) {
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  cudaFree(p->phi0);
+  cudaFree(p->U);
+  cudaFree(p->V);
+  cudaFree(p->fmax);
+  cudaFree(p->idx);
+  cudaFree(p->mult);
+  cudaFree(p->tw);
+  cudaFree(p->counters);
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  p->events.clear();
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  p->graph_exec = nullptr;
+  p->graph = nullptr;
+}
+
+float2* spec(pin_plan_t p, float2* base, int f) { return base + (size_t)f * p->spec_elems; }
+
+// Filter-and-transform passes of one radius (mult set `ms`), ending in the
+// collapse update (dump == nullptr) or a dump of the six real components.
+pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
+  const float* mult = p->mult + (size_t)ms * 3 * p->n;
+  const bool rec = p->profile && dump == nullptr && !p->events.empty();
+  if (rec) PIN_CK(p, cudaEventRecord(p->events[4 * scale + 0], p->stream));
+  ArgsX ax{};
+  ax.src = p->phi0;
+  for (int f = 0; f < 3; ++f) { ax.dst[f] = spec(p, p->U, f); ax.xm[f] = f; }
+  ax.nout = 3;
+  ax.mult = mult;
+  ax.tw = p->tw;
+  ax.nhp = p->nhp;
+  PIN_CK(p, launch_x(p->n, ax, p->stream));
+  if (rec) PIN_CK(p, cudaEventRecord(p->events[4 * scale + 1], p->stream));
+
+  // y pass: xx <- U2, yy <- U0 (k_y^2), zz <- U0, xy <- U1 (k_y), xz <- U1, yz <- U0 (k_y)
+  static const int sel[6] = {2, 0, 0, 1, 1, 0};
+  static const int ym[6] = {0, 2, 0, 1, 0, 1};
+  static const int zm[6] = {0, 0, 2, 0, 1, 1};
+  ArgsY ay{};
+  for (int f = 0; f < 3; ++f) ay.src[f] = spec(p, p->U, f);
+  for (int f = 0; f < 6; ++f) { ay.dst[f] = spec(p, p->V, f); ay.sel[f] = sel[f]; ay.ym[f] = ym[f]; }
+  ay.nout = 6;
+  ay.mult = mult;
+  ay.tw = p->tw;
+  ay.nhp = p->nhp;
+  PIN_CK(p, launch_y(p->n, ay, p->stream));
+  if (rec) PIN_CK(p, cudaEventRecord(p->events[4 * scale + 2], p->stream));
+
+  ArgsZ az{};
+  for (int f = 0; f < 6; ++f) { az.src[f] = spec(p, p->V, f); az.zm[f] = zm[f]; az.muli[f] = 0; }
+  az.nfields = 6;
+  az.mult = mult;
+  az.tw = p->tw;
+  az.nhp = p->nhp;
+  az.fmax = p->fmax;
+  az.idx = p->idx;
+  az.scale = scale;
+  az.correction = p->correction;
+  az.dcorr_d = p->dcorr;
+  az.dcorr_f = (float)p->dcorr;
+  az.tau_eig = 2e-4f;
+  az.tau_root = 1e-3f;
+  az.counters = p->counters;
+  if (dump)
+    for (int f = 0; f < 6; ++f) az.out[f] = dump[f];
+  PIN_CK(p, launch_z(p->n, az, dump != nullptr, p->stream));
+  if (rec) PIN_CK(p, cudaEventRecord(p->events[4 * scale + 3], p->stream));
+  return PIN_OK;
+}
+
+pin_status enqueue_collapse(pin_plan_t p) {
+  const size_t n3 = (size_t)p->n * p->n * p->n;
+  PIN_CK(p, cudaMemsetAsync(p->fmax, 0, n3 * sizeof(float), p->stream));
+  PIN_CK(p, cudaMemsetAsync(p->idx, 0xFF, n3 * sizeof(int), p->stream));
+  for (int s = 0; s < p->nscales; ++s) {
+    pin_status st = enqueue_radius(p, s, s, nullptr);
+    if (st != PIN_OK) return st;
+  }
+  return PIN_OK;
+}
+
+pin_status ensure_graph(pin_plan_t p) {
+  if (p->graph_exec) return PIN_OK;
+  PIN_CK(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  pin_status st = enqueue_collapse(p);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+  if (st != PIN_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaStreamEndCapture");
+  p->graph = g;
+  e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    p->graph = nullptr;
+    p->graph_exec = nullptr;
+    return cuda_fail(p, e, "cudaGraphInstantiate");
+  }
+  return PIN_OK;
+}
+
+pin_status check_plan(pin_plan_t p) {
+  if (!p) return PIN_EINVAL;
+  cudaError_t e = cudaSetDevice(p->device);
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaSetDevice");
+  return PIN_OK;
+}
+
+pin_status finish_host(pin_plan_t p) {
+  PIN_CK(p, cudaStreamSynchronize(p->stream));
+  return PIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pin_footprint_bytes(const pin_plan_desc* d) {
+  std::string why;
+  if (!validate(d, &why)) return 0;
+  return footprint(d->nx, d->nscales);
+}
+
+pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
+  if (!out) return PIN_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (!validate(d, &why)) return PIN_EINVAL;
+  pin_plan_s* p = new (std::nothrow) pin_plan_s();
+  if (!p) return PIN_ENOMEM;
+  p->n = d->nx;
+  p->nhp = padded_half(p->n);
+  p->box = d->box;
+  p->nscales = d->nscales;
+  p->radii.assign(d->radii, d->radii + d->nscales);
+  p->correction = d->correction;
+  p->precision = d->precision;
+  p->shape = pass_shape(p->n);
+  p->spec_elems = (size_t)p->n * p->n * p->nhp;
+  p->dcorr = 1.0 / delta_c_value() - 1.0 / x3_value();
+  auto bail = [&](pin_status s) {
+    release(p);
+    delete p;
+    return s;
+  };
+  if (cudaGetDevice(&p->device) != cudaSuccess) return bail(PIN_ECUDA);
+  if (ensure_device_init(p) != PIN_OK) return bail(PIN_ECUDA);
+  if (d->stream) {
+    p->stream = (cudaStream_t)d->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PIN_ECUDA);
+    p->own_stream = true;
+  }
+  const size_t n3 = (size_t)p->n * p->n * p->n;
+  const size_t mult_elems = (size_t)(p->nscales + 1) * 3 * p->n;
+  if (cudaMalloc(&p->phi0, p->spec_elems * 8) != cudaSuccess ||
+      cudaMalloc(&p->U, 3 * p->spec_elems * 8) != cudaSuccess ||
+      cudaMalloc(&p->V, 6 * p->spec_elems * 8) != cudaSuccess ||
+      cudaMalloc(&p->fmax, n3 * 4) != cudaSuccess || cudaMalloc(&p->idx, n3 * 4) != cudaSuccess ||
+      cudaMalloc(&p->mult, mult_elems * 4) != cudaSuccess ||
+      cudaMalloc(&p->tw, (size_t)p->n * 8) != cudaSuccess ||
+      cudaMalloc(&p->counters, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PIN_ENOMEM);
+  }
+  std::vector<float> mult(mult_elems);
+  for (int s = 0; s < p->nscales; ++s) fill_mult(mult.data() + (size_t)s * 3 * p->n, p->n, p->box, p->radii[s]);
+  fill_mult(mult.data() + (size_t)p->nscales * 3 * p->n, p->n, p->box, 0.0);
+  // level-2 twiddles w_N^{p k1} in [k1][p] order
+  const int E = p->shape.E, P = p->shape.P;
+  std::vector<float2> tw((size_t)p->n);
+  for (int k1 = 0; k1 < E; ++k1)
+    for (int q = 0; q < P; ++q) {
+      const double ang = 2.0 * M_PI * (double)((long)q * k1 % p->n) / p->n;
+      tw[(size_t)k1 * P + q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  if (cudaMemcpy(p->mult, mult.data(), mult_elems * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(p->counters, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
+    return bail(PIN_ECUDA);
+  *out = p;
+  return PIN_OK;
+}
+
+pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!delta_k) return fail(p, PIN_EINVAL, "null delta_k");
+  if (dtype != PIN_C64 && dtype != PIN_C128) return fail(p, PIN_EINVAL, "dtype must be PIN_C64 or PIN_C128");
+  const size_t nh = (size_t)p->n / 2 + 1;
+  const size_t bytes = (size_t)p->n * p->n * nh * (dtype == PIN_C64 ? 8 : 16);
+  const void* src = delta_k;
+  if (!on_device) {
+    // stage through the V workspace (6 spectra >= one C128 half-spectrum)
+    PIN_CK(p, cudaMemcpyAsync(p->V, delta_k, bytes, cudaMemcpyHostToDevice, p->stream));
+    src = p->V;
+  }
+  const size_t total = p->spec_elems;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, 152 * 64);
+  k_load_phi0<<<blocks, threads, 0, p->stream>>>(src, dtype, p->n, p->nhp, p->box, p->phi0);
+  PIN_CK(p, cudaGetLastError());
+  if (!on_device) PIN_CK(p, cudaStreamSynchronize(p->stream));
+  p->ic_set = true;
+  return PIN_OK;
+}
+
+pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!F_max || !scale_idx) return fail(p, PIN_EINVAL, "null output");
+  if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
+  st = ensure_graph(p);
+  if (st != PIN_OK) return st;
+  PIN_CK(p, cudaGraphLaunch(p->graph_exec, p->stream));
+  const size_t n3 = (size_t)p->n * p->n * p->n;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  PIN_CK(p, cudaMemcpyAsync(F_max, p->fmax, n3 * 4, kind, p->stream));
+  PIN_CK(p, cudaMemcpyAsync(scale_idx, p->idx, n3 * 4, kind, p->stream));
+  p->calls++;
+  if (!on_device) return finish_host(p);
+  return PIN_OK;
+}
+
+pin_status pin_hessian(pin_plan_t p, int scale, float* out6, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!out6) return fail(p, PIN_EINVAL, "null output");
+  if (scale < 0 || scale >= p->nscales) return fail(p, PIN_EINVAL, "scale index out of range");
+  if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
+  const size_t n3 = (size_t)p->n * p->n * p->n;
+  float* dev = out6;
+  if (!on_device) PIN_CK(p, cudaMallocAsync((void**)&dev, 6 * n3 * 4, p->stream));
+  float* outs[6];
+  for (int f = 0; f < 6; ++f) outs[f] = dev + (size_t)f * n3;
+  st = enqueue_radius(p, scale, scale, outs);
+  if (st == PIN_OK && !on_device) {
+    cudaError_t e = cudaMemcpyAsync(out6, dev, 6 * n3 * 4, cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) st = cuda_fail(p, e, "cudaMemcpyAsync");
+  }
+  if (!on_device) {
+    cudaFreeAsync(dev, p->stream);
+    if (st == PIN_OK) st = finish_host(p);
+  }
+  return st;
+}
+
+pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!psi) return fail(p, PIN_EINVAL, "null output");
+  if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
+  const size_t n3 = (size_t)p->n * p->n * p->n;
+  float* dev = psi;
+  if (!on_device) PIN_CK(p, cudaMallocAsync((void**)&dev, 3 * n3 * 4, p->stream));
+  const float* mult = p->mult + (size_t)p->nscales * 3 * p->n;  // R = 0: no smoothing
+  ArgsX ax{};
+  ax.src = p->phi0;
+  ax.dst[0] = spec(p, p->U, 0);
+  ax.dst[1] = spec(p, p->U, 1);
+  ax.xm[0] = 0;
+  ax.xm[1] = 1;
+  ax.nout = 2;
+  ax.mult = mult;
+  ax.tw = p->tw;
+  ax.nhp = p->nhp;
+  cudaError_t e = launch_x(p->n, ax, p->stream);
+  // psi_x <- U1, psi_y <- U0 (k_y), psi_z <- U0; z: psi_z gets k_z; all times i
+  ArgsY ay{};
+  ay.src[0] = spec(p, p->U, 0);
+  ay.src[1] = spec(p, p->U, 1);
+  const int sel[3] = {1, 0, 0}, ym[3] = {0, 1, 0}, zm[3] = {0, 0, 1};
+  for (int f = 0; f < 3; ++f) { ay.dst[f] = spec(p, p->V, f); ay.sel[f] = sel[f]; ay.ym[f] = ym[f]; }
+  ay.nout = 3;
+  ay.mult = mult;
+  ay.tw = p->tw;
+  ay.nhp = p->nhp;
+  if (e == cudaSuccess) e = launch_y(p->n, ay, p->stream);
+  ArgsZ az{};
+  for (int f = 0; f < 3; ++f) {
+    az.src[f] = spec(p, p->V, f);
+    az.zm[f] = zm[f];
+    az.muli[f] = 1;
+    az.out[f] = dev + (size_t)f * n3;
+  }
+  az.nfields = 3;
+  az.mult = mult;
+  az.tw = p->tw;
+  az.nhp = p->nhp;
+  if (e == cudaSuccess) e = launch_z(p->n, az, true, p->stream);
+  if (e != cudaSuccess) st = cuda_fail(p, e, "displacement passes");
+  if (st == PIN_OK && !on_device) {
+    e = cudaMemcpyAsync(psi, dev, 3 * n3 * 4, cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) st = cuda_fail(p, e, "cudaMemcpyAsync");
+  }
+  if (!on_device) {
+    cudaFreeAsync(dev, p->stream);
+    if (st == PIN_OK) st = finish_host(p);
+  }
+  return st;
+}
+
+pin_status pin_sync(pin_plan_t p, int64_t timeout_ns) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(p->stream);
+    if (e == cudaSuccess) return PIN_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(p, e, "cudaStreamQuery");
+    if (timeout_ns >= 0) {
+      const auto dt = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+      if (dt >= timeout_ns) return fail(p, PIN_ETIMEOUT, "pin_sync timed out");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+pin_status pin_get_stats(pin_plan_t p, pin_stats* out) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!out) return fail(p, PIN_EINVAL, "null stats");
+  unsigned long long c[2] = {0, 0};
+  PIN_CK(p, cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, p->stream));
+  PIN_CK(p, cudaStreamSynchronize(p->stream));
+  out->eig_fp64_redo = c[0];
+  out->root_fp64_redo = c[1];
+  out->collapse_calls = p->calls;
+  return PIN_OK;
+}
+
+int pin_kernels_per_call(pin_plan_t p) { return p ? 3 * p->nscales : 0; }
+
+pin_status pin_profile(pin_plan_t p, int enable) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  const bool want = enable != 0;
+  if (want == p->profile) return PIN_OK;
+  PIN_CK(p, cudaStreamSynchronize(p->stream));
+  if (want && p->events.empty()) {
+    p->events.resize(4 * (size_t)p->nscales, nullptr);
+    for (auto& e : p->events) PIN_CK(p, cudaEventCreate(&e));
+  }
+  p->profile = want;
+  // rebuild the graph with (or without) the event records
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->graph_exec = nullptr;
+  p->graph = nullptr;
+  return PIN_OK;
+}
+
+pin_status pin_pass_times(pin_plan_t p, double* ms3) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!ms3) return fail(p, PIN_EINVAL, "null output");
+  if (!p->profile || p->events.empty() || p->calls == 0) return fail(p, PIN_ESTATE, "profiling is off or nothing ran");
+  PIN_CK(p, cudaStreamSynchronize(p->stream));
+  ms3[0] = ms3[1] = ms3[2] = 0.0;
+  for (int s = 0; s < p->nscales; ++s)
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      PIN_CK(p, cudaEventElapsedTime(&ms, p->events[4 * s + k], p->events[4 * s + k + 1]));
+      ms3[k] += ms;
+    }
+  return PIN_OK;
+}
+
+const char* pin_strerror(pin_status s) {
+  switch (s) {
+    case PIN_OK: return "ok";
+    case PIN_EINVAL: return "invalid argument";
+    case PIN_ENOMEM: return "out of device memory";
+    case PIN_ECUDA: return "CUDA error";
+    case PIN_EBUSY: return "busy";
+    case PIN_ETIMEOUT: return "timed out";
+    case PIN_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* pin_last_error(pin_plan_t p) { return p ? p->last_error.c_str() : ""; }
+
+void pin_destroy(pin_plan_t p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  release(p);
+  delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+"""Thin ctypes binding of libpin.so (C-ABI in include/pin.h).
+
+Argument marshalling only: every step of the collapse-time path runs in the
+CUDA kernels of csrc/.  There is no CPU fallback; if the native library is
+missing or no GPU is present the calls raise.
+
+The functions keep the C names (pin_plan, pin_set_ic, pin_collapse_times,
+pin_hessian, pin_displacements, pin_sync, ...).  `Plan` and `collapse_times`
+are conveniences over them that take PyTorch device tensors (PyTorch provides
+device memory and streams only).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PIN_OK, PIN_EINVAL, PIN_ENOMEM, PIN_ECUDA, PIN_EBUSY, PIN_ETIMEOUT, PIN_ESTATE = range(7)
+PIN_CORR_NONE, PIN_CORR_SPHERE = 0, 1
+PIN_FP32_FALLBACK64 = 0
+PIN_C64, PIN_C128 = 0, 1
+
+MAX_SCALES = 64
+
+
+class PinError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (_strerror(status), status, msg))
+        self.status = status
+
+
+class pin_plan_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("box", ctypes.c_double), ("nscales", ctypes.c_int),
+                ("radii", ctypes.POINTER(ctypes.c_double)), ("correction", ctypes.c_int),
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class pin_stats(ctypes.Structure):
+    _fields_ = [("eig_fp64_redo", ctypes.c_uint64), ("root_fp64_redo", ctypes.c_uint64),
+                ("collapse_calls", ctypes.c_uint64)]
+
+
+# every symbol include/pin.h declares
+EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_hessian",
+           "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
+           "pin_profile", "pin_pass_times",
+           "pin_strerror", "pin_last_error", "pin_destroy")
+
+_lib = None
+
+
+def load(path=None):
+    """Loads libpin.so (building it in-tree if stale) and declares signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.ensure_pin()
+    if not os.path.exists(path):
+        raise RuntimeError("libpin.so not found at %s; run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    L.pin_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(pin_plan_desc)]
+    L.pin_plan.restype = ctypes.c_int
+    L.pin_footprint_bytes.argtypes = [ctypes.POINTER(pin_plan_desc)]
+    L.pin_footprint_bytes.restype = ctypes.c_size_t
+    L.pin_set_ic.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
+    L.pin_set_ic.restype = ctypes.c_int
+    L.pin_collapse_times.argtypes = [P, P, P, ctypes.c_int]
+    L.pin_collapse_times.restype = ctypes.c_int
+    L.pin_hessian.argtypes = [P, ctypes.c_int, P, ctypes.c_int]
+    L.pin_hessian.restype = ctypes.c_int
+    L.pin_displacements.argtypes = [P, P, ctypes.c_int]
+    L.pin_displacements.restype = ctypes.c_int
+    L.pin_sync.argtypes = [P, ctypes.c_int64]
+    L.pin_sync.restype = ctypes.c_int
+    L.pin_get_stats.argtypes = [P, ctypes.POINTER(pin_stats)]
+    L.pin_get_stats.restype = ctypes.c_int
+    L.pin_kernels_per_call.argtypes = [P]
+    L.pin_kernels_per_call.restype = ctypes.c_int
+    L.pin_profile.argtypes = [P, ctypes.c_int]
+    L.pin_profile.restype = ctypes.c_int
+    L.pin_pass_times.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    L.pin_pass_times.restype = ctypes.c_int
+    L.pin_strerror.argtypes = [ctypes.c_int]
+    L.pin_strerror.restype = ctypes.c_char_p
+    L.pin_last_error.argtypes = [P]
+    L.pin_last_error.restype = ctypes.c_char_p
+    L.pin_destroy.argtypes = [P]
+    L.pin_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _strerror(status):
+    try:
+        return load().pin_strerror(status).decode()
+    except Exception:  # library unavailable while formatting an error
+        return "status"
+
+
+def _check(status, plan=None):
+    if status != PIN_OK:
+        msg = ""
+        if plan is not None:
+            msg = load().pin_last_error(plan).decode(errors="replace")
+        raise PinError(status, msg)
+
+
+def make_desc(n, box, radii, correction=PIN_CORR_SPHERE, stream=None):
+    r = np.ascontiguousarray(radii, dtype=np.float64)
+    d = pin_plan_desc(n, n, n, float(box), int(r.size),
+                      r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(correction),
+                      PIN_FP32_FALLBACK64, ctypes.c_void_p(stream) if stream else None)
+    d._radii_keepalive = r
+    return d
+
+
+# ---- C names ---------------------------------------------------------------
+
+def pin_plan(desc):
+    h = ctypes.c_void_p()
+    st = load().pin_plan(ctypes.byref(h), ctypes.byref(desc))
+    _check(st)
+    return h
+
+
+def pin_footprint_bytes(desc):
+    return load().pin_footprint_bytes(ctypes.byref(desc))
+
+
+def pin_set_ic(plan, delta_k_ptr, dtype, on_device):
+    _check(load().pin_set_ic(plan, ctypes.c_void_p(delta_k_ptr), dtype, int(on_device)), plan)
+
+
+def pin_collapse_times(plan, fmax_ptr, idx_ptr, on_device):
+    _check(load().pin_collapse_times(plan, ctypes.c_void_p(fmax_ptr), ctypes.c_void_p(idx_ptr),
+                                     int(on_device)), plan)
+
+
+def pin_hessian(plan, scale, out_ptr, on_device):
+    _check(load().pin_hessian(plan, int(scale), ctypes.c_void_p(out_ptr), int(on_device)), plan)
+
+
+def pin_displacements(plan, out_ptr, on_device):
+    _check(load().pin_displacements(plan, ctypes.c_void_p(out_ptr), int(on_device)), plan)
+
+
+def pin_sync(plan, timeout_ns=-1):
+    return load().pin_sync(plan, int(timeout_ns))
+
+
+def pin_get_stats(plan):
+    s = pin_stats()
+    _check(load().pin_get_stats(plan, ctypes.byref(s)), plan)
+    return dict(eig_fp64_redo=s.eig_fp64_redo, root_fp64_redo=s.root_fp64_redo,
+                collapse_calls=s.collapse_calls)
+
+
+def pin_kernels_per_call(plan):
+    return load().pin_kernels_per_call(plan)
+
+
+def pin_profile(plan, enable):
+    _check(load().pin_profile(plan, int(enable)), plan)
+
+
+def pin_pass_times(plan):
+    ms = (ctypes.c_double * 3)()
+    _check(load().pin_pass_times(plan, ms), plan)
+    return list(ms)
+
+
+def pin_strerror(status):
+    return load().pin_strerror(status).decode()
+
+
+def pin_last_error(plan):
+    return load().pin_last_error(plan).decode(errors="replace")
+
+
+def pin_destroy(plan):
+    load().pin_destroy(plan)
+
+
+# ---- conveniences over PyTorch device memory --------------------------------
+
+class Plan:
+    """Owns one pin plan; methods take torch tensors (device or host)."""
+
+    def __init__(self, n, box, radii, correction=PIN_CORR_SPHERE, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("pin needs a CUDA device; none is available")
+        self.n = int(n)
+        self.box = float(box)
+        self.radii = np.ascontiguousarray(radii, dtype=np.float64)
+        s = stream.cuda_stream if stream is not None else None
+        self._desc = make_desc(self.n, self.box, self.radii, correction, s)
+        self.handle = pin_plan(self._desc)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                pin_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def close(self):
+        self.__del__()
+
+    def set_ic(self, delta_k):
+        """delta_k: (n, n, n//2+1) complex64/complex128 tensor or numpy array."""
+        import torch
+        if isinstance(delta_k, np.ndarray):
+            a = np.ascontiguousarray(delta_k)
+            dt = PIN_C64 if a.dtype == np.complex64 else PIN_C128
+            if a.dtype not in (np.complex64, np.complex128):
+                raise TypeError("delta_k must be complex64 or complex128")
+            pin_set_ic(self.handle, a.ctypes.data, dt, 0)
+            return
+        t = delta_k.contiguous()
+        dt = {torch.complex64: PIN_C64, torch.complex128: PIN_C128}[t.dtype]
+        if t.is_cuda:
+            torch.cuda.current_stream().synchronize()  # producer stream -> plan stream
+        pin_set_ic(self.handle, t.data_ptr(), dt, 1 if t.is_cuda else 0)
+        if t.is_cuda:
+            self.sync()
+
+    def collapse_times(self, fmax=None, idx=None, sync=True):
+        """Returns (F_max float32, scale_idx int32) tensors of shape (n,n,n),
+        on the device unless host tensors are passed in.  With sync=False the
+        work is only enqueued on the plan's stream (call .sync() before use)."""
+        import torch
+        n = self.n
+        if fmax is None:
+            fmax = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        if idx is None:
+            idx = torch.empty((n, n, n), dtype=torch.int32, device=fmax.device)
+        if fmax.is_cuda != idx.is_cuda:
+            raise ValueError("F_max and scale_idx must both be on the device or both on the host")
+        if fmax.is_cuda:
+            torch.cuda.current_stream().synchronize()  # outputs allocated on torch's stream
+        pin_collapse_times(self.handle, fmax.data_ptr(), idx.data_ptr(), 1 if fmax.is_cuda else 0)
+        if sync and fmax.is_cuda:
+            self.sync()
+        return fmax, idx
+
+    def hessian(self, scale):
+        import torch
+        n = self.n
+        out = torch.empty((6, n, n, n), dtype=torch.float32, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        pin_hessian(self.handle, scale, out.data_ptr(), 1)
+        self.sync()
+        return out
+
+    def displacements(self):
+        import torch
+        n = self.n
+        out = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        pin_displacements(self.handle, out.data_ptr(), 1)
+        self.sync()
+        return out
+
+    def sync(self, timeout_s=None):
+        st = pin_sync(self.handle, -1 if timeout_s is None else int(timeout_s * 1e9))
+        _check(st, self.handle)
+
+    def stats(self):
+        return pin_get_stats(self.handle)
+
+
+def collapse_times(delta_k, radii, box, correction=PIN_CORR_SPHERE):
+    """One-shot: (F_max, scale_idx) for the half-spectrum delta_k."""
+    n = delta_k.shape[0]
+    plan = Plan(n, box, radii, correction)
+    try:
+        plan.set_ic(delta_k)
+        f, i = plan.collapse_times()
+        plan.sync()
+        return f, i
+    finally:
+        plan.close()

@@ -1,0 +1,64 @@
+"""The C-ABI libraries load and export every declared symbol; argument
+validation works without a GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1305_1505_gb300 import build, pin
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pin_\w+)\s*\(", txt)))
+
+
+def test_libpin_exports_every_declared_symbol():
+    lib = ctypes.CDLL(build.ensure_pin())
+    names = _declared("pin.h")
+    assert "pin_plan" in names and "pin_collapse_times" in names and "pin_displacements" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(pin.EXPORTS) == set(names)
+
+
+def test_libpin_ic_exports_every_declared_symbol():
+    lib = ctypes.CDLL(build.ensure_ic())
+    for name in _declared("pin_ic.h"):
+        assert hasattr(lib, name), name
+
+
+def test_validation_without_gpu():
+    L = pin.load()
+    assert pin.pin_strerror(pin.PIN_EINVAL) == "invalid argument"
+    good = pin.make_desc(64, 100.0, [10.0, 5.0])
+    assert pin.pin_footprint_bytes(good) > 64 ** 3 * 8
+    for bad in (pin.make_desc(60, 100.0, [1.0]),       # unsupported size
+                pin.make_desc(64, -1.0, [1.0]),        # bad box
+                pin.make_desc(64, 100.0, [-1.0]),      # bad radius
+                pin.make_desc(64, 100.0, [np.nan]),
+                pin.make_desc(64, 100.0, [1.0] * 65)):  # too many radii
+        assert pin.pin_footprint_bytes(bad) == 0
+        h = ctypes.c_void_p()
+        assert L.pin_plan(ctypes.byref(h), ctypes.byref(bad)) == pin.PIN_EINVAL
+        assert not h.value
+    nc = pin.make_desc(64, 100.0, [1.0])
+    nc.ny = 32
+    assert pin.pin_footprint_bytes(nc) == 0
+    nc = pin.make_desc(64, 100.0, [1.0])
+    nc.correction = 7
+    assert pin.pin_footprint_bytes(nc) == 0
+
+
+def test_null_plan_calls_are_rejected():
+    L = pin.load()
+    assert L.pin_set_ic(None, None, 0, 0) == pin.PIN_EINVAL
+    assert L.pin_collapse_times(None, None, None, 0) == pin.PIN_EINVAL
+    assert L.pin_sync(None, 0) == pin.PIN_EINVAL
+    assert L.pin_kernels_per_call(None) == 0
+    L.pin_destroy(None)

@@ -358,3 +358,62 @@ def test_pipeline_agrees_with_pointwise_composition():
         for q in (0, 17, 200, 511):
             F, _ = oracle.collapse_point(flat[:, q], correction=1)
             assert F == out["f_all"][s, q]
+
+
+# ------------------------------------------------------ displacement pins --
+
+@pytest.mark.parametrize("mode", [(1, 2, 3), (5, 1, 2), (0, 0, 2), (4, 0, 1)])
+def test_displacement_single_mode_closed_form(mode):
+    """psi = i k delta / k^2 for one mode gives
+    psi(q) = -(k / k^2) 2 Im(A e^{i k.q}) / n^3 (zero along a Nyquist axis)."""
+    n, box = 8, 40.0
+    d = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    amp = 0.4 + 0.9j
+    mx, my, mz = mode
+    d[mx, my, mz] = amp
+    if mz == 0:
+        d[(-mx) % n, (-my) % n, 0] = np.conj(amp)
+    psi = oracle.displacement(d, box)
+    s = [mx if mx < n // 2 else mx - n, my if my < n // 2 else my - n, mz]
+    kf = 2 * np.pi / box
+    k = kf * np.array(s, dtype=float)
+    k2 = k @ k
+    q = np.indices((n, n, n))
+    phase = 2 * np.pi * (s[0] * q[0] + s[1] * q[1] + s[2] * q[2]) / n
+    wave = -2 * np.imag(amp * np.exp(1j * phase)) / n ** 3
+    for c in range(3):
+        ref = np.zeros_like(wave) if s[c] == -n // 2 else k[c] / k2 * wave
+        assert np.abs(psi[c] - ref).max() < 1e-15 + 1e-12 * np.abs(wave).max()
+
+
+def test_displacement_divergence_is_minus_delta():
+    """-div psi = delta, checked in real space with numpy's spectral derivative
+    (a library routine), away from the odd-order Nyquist modes."""
+    n, box = 12, 60.0
+    d = _field(n, box, 9)
+    # drop every mode with a Nyquist index so the spectral derivative is exact
+    d[n // 2, :, :] = 0
+    d[:, n // 2, :] = 0
+    d[:, :, n // 2] = 0
+    psi = oracle.displacement(d, box)
+    kf = 2 * np.pi / box
+    div = 0
+    for c in range(3):
+        f = np.fft.rfftn(psi[c], axes=(0, 1, 2))
+        m = np.fft.fftfreq(n, 1.0 / n) if c < 2 else np.arange(n // 2 + 1)
+        shape = [1, 1, 1]
+        shape[c] = -1
+        div = div + np.fft.irfftn(1j * kf * m.reshape(shape) * f, s=(n, n, n), axes=(0, 1, 2))
+    ref = np.fft.irfftn(d, s=(n, n, n), axes=(0, 1, 2))
+    assert np.abs(-div - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_multi_point_direct_sum_matches_fft_path():
+    n, box, radius = 16, 90.0, 4.0
+    d = _field(n, box, 13)
+    h, _ = oracle.hessian(d, box, radius)
+    rng = np.random.default_rng(1)
+    q = rng.integers(0, n ** 3, size=7)
+    got = oracle.hessian_points(d, box, radius, q)
+    ref = h.reshape(6, -1)[:, q].T
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(h).max()
