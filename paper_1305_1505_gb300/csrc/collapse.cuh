@@ -25,25 +25,26 @@
 // uncorrected spherical root (x/3 + x^2/21 + 23 x^3/1701 = 1).
 #pragma once
 #include <cuda_runtime.h>
+#include <cmath>
 
 namespace pin {
 
 template <typename T> struct M;
 template <> struct M<float> {
-  __device__ __forceinline__ static float sqrt_(float x) { return sqrtf(x); }
-  __device__ __forceinline__ static float acos_(float x) { return acosf(x); }
-  __device__ __forceinline__ static float cos_(float x) { return cosf(x); }
-  __device__ __forceinline__ static float cbrt_(float x) { return cbrtf(x); }
-  __device__ __forceinline__ static float exp_(float x) { return expf(x); }
-  __device__ __forceinline__ static float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+  __host__ __device__ __forceinline__ static float sqrt_(float x) { return std::sqrt(x); }
+  __host__ __device__ __forceinline__ static float acos_(float x) { return std::acos(x); }
+  __host__ __device__ __forceinline__ static float cos_(float x) { return std::cos(x); }
+  __host__ __device__ __forceinline__ static float cbrt_(float x) { return std::cbrt(x); }
+  __host__ __device__ __forceinline__ static float exp_(float x) { return std::exp(x); }
+  __host__ __device__ __forceinline__ static float fma_(float a, float b, float c) { return std::fma(a, b, c); }
 };
 template <> struct M<double> {
-  __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
-  __device__ __forceinline__ static double acos_(double x) { return acos(x); }
-  __device__ __forceinline__ static double cos_(double x) { return cos(x); }
-  __device__ __forceinline__ static double cbrt_(double x) { return cbrt(x); }
-  __device__ __forceinline__ static double exp_(double x) { return exp(x); }
-  __device__ __forceinline__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
+  __host__ __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
+  __host__ __device__ __forceinline__ static double acos_(double x) { return acos(x); }
+  __host__ __device__ __forceinline__ static double cos_(double x) { return cos(x); }
+  __host__ __device__ __forceinline__ static double cbrt_(double x) { return cbrt(x); }
+  __host__ __device__ __forceinline__ static double exp_(double x) { return exp(x); }
+  __host__ __device__ __forceinline__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
 };
 
 // Closed-form eigenvalues of the symmetric 3x3 matrix
@@ -52,7 +53,7 @@ template <> struct M<double> {
 // Returns |r| = |det(B)|/2, B = (A - qI)/p; |r| -> 1 marks a near-degenerate
 // pair, whose split the trigonometric form resolves poorly in FP32.
 template <typename T>
-__device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
+__host__ __device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
   using F = M<T>;
   const T q = (h[0] + h[1] + h[2]) / T(3);
   const T b0 = h[0] - q, b1 = h[1] - q, b2 = h[2] - q;
@@ -82,11 +83,11 @@ __device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
 // below (no positive root: the axis never collapses).  kappa receives
 // |g'(F)| / (3F^2 + 2|c1|F + |c2|), small near a tangent crossing.
 template <typename T>
-__device__ __forceinline__ T largest_root(T c1, T c2, T c3, T& kappa) {
+__host__ __device__ __forceinline__ T largest_root(T c1, T c2, T c3, T& kappa) {
   using F = M<T>;
   const T s = c1 / T(3);
   const T p = -c2 - c1 * s;                                   // b - a^2/3
-  const T q = -c3 - c1 * c2 / T(3) - T(2) * c1 * s * s;        // 2a^3/27 - ab/3 + c
+  const T q = -c3 - c1 * c2 / T(3) - T(2) * s * s * s;         // 2a^3/27 - ab/3 + c
   const T hq = q / T(2), tp = p / T(3);
   const T disc = hq * hq + tp * tp * tp;
   T t;
@@ -131,7 +132,7 @@ struct CollapseConsts {
 // F for sorted eigenvalues lam; kappa_min receives the conditioning of the
 // root that set F (1 when nothing collapses).
 template <typename T>
-__device__ __forceinline__ T collapse_from_eigs(const T lam[3], const CollapseConsts<T>& cc,
+__host__ __device__ __forceinline__ T collapse_from_eigs(const T lam[3], const CollapseConsts<T>& cc,
                                                 T& kappa_min) {
   using F = M<T>;
   const T mu1 = lam[0] + lam[1] + lam[2];

@@ -204,7 +204,7 @@ float2* spec(pin_plan_t p, float2* base, int f) { return base + (size_t)f * p->s
 pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   const float* mult = p->mult + (size_t)ms * 3 * p->n;
   const bool rec = p->profile && dump == nullptr && !p->events.empty();
-  if (rec) PIN_CK(p, cudaEventRecord(p->events[4 * scale + 0], p->stream));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 0], p->stream, cudaEventRecordExternal));
   ArgsX ax{};
   ax.src = p->phi0;
   for (int f = 0; f < 3; ++f) { ax.dst[f] = spec(p, p->U, f); ax.xm[f] = f; }
@@ -213,7 +213,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   ax.tw = p->tw;
   ax.nhp = p->nhp;
   PIN_CK(p, launch_x(p->n, ax, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecord(p->events[4 * scale + 1], p->stream));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 1], p->stream, cudaEventRecordExternal));
 
   // y pass: xx <- U2, yy <- U0 (k_y^2), zz <- U0, xy <- U1 (k_y), xz <- U1, yz <- U0 (k_y)
   static const int sel[6] = {2, 0, 0, 1, 1, 0};
@@ -227,7 +227,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   ay.tw = p->tw;
   ay.nhp = p->nhp;
   PIN_CK(p, launch_y(p->n, ay, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecord(p->events[4 * scale + 2], p->stream));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 2], p->stream, cudaEventRecordExternal));
 
   ArgsZ az{};
   for (int f = 0; f < 6; ++f) { az.src[f] = spec(p, p->V, f); az.zm[f] = zm[f]; az.muli[f] = 0; }
@@ -247,7 +247,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   if (dump)
     for (int f = 0; f < 6; ++f) az.out[f] = dump[f];
   PIN_CK(p, launch_z(p->n, az, dump != nullptr, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecord(p->events[4 * scale + 3], p->stream));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 3], p->stream, cudaEventRecordExternal));
   return PIN_OK;
 }
 

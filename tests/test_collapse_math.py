@@ -1,0 +1,84 @@
+"""The CUDA path's per-particle arithmetic (csrc/collapse.cuh, compiled for
+the host) against the FP64 oracle: eigenvalues and collapse time F in FP64
+and FP32 on random triplets and on the limits (sphere, one axis)."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+OUT = os.path.join(ROOT, "paper_1305_1505_gb300", "_build", "libcollapse_host.so")
+DP = ctypes.POINTER(ctypes.c_double)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+                           "-I", os.path.join(ROOT, "paper_1305_1505_gb300", "csrc"),
+                           "-o", OUT, os.path.join(HERE, "collapse_host.cu")])
+    L = ctypes.CDLL(OUT)
+    L.host_collapse.argtypes = [DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, DP]
+    L.host_collapse.restype = ctypes.c_double
+    L.host_eig.argtypes = [DP, DP, ctypes.c_int]
+    L.host_eig.restype = ctypes.c_double
+    return L
+
+
+def _F(L, lam, corr, use_float):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    k = ctypes.c_double()
+    dcorr = 1 / oracle.delta_c() - 1 / oracle.x3()
+    return L.host_collapse(lam.ctypes.data_as(DP), corr, use_float, dcorr, ctypes.byref(k)), k.value
+
+
+def test_collapse_fp64_matches_oracle(lib):
+    rng = np.random.default_rng(0)
+    for _ in range(5000):
+        lam = np.sort(rng.normal(size=3) * 0.6)[::-1]
+        for corr in (0, 1):
+            g, _ = _F(lib, lam, corr, 0)
+            o = oracle.collapse_F(lam, corr)
+            assert abs(g - o) <= 1e-10 * max(1.0, abs(o)), (lam, corr, g, o)
+
+
+def test_collapse_fp32_within_tolerance_or_flagged(lib):
+    rng = np.random.default_rng(1)
+    for _ in range(5000):
+        lam = np.sort(rng.normal(size=3) * 0.6)[::-1]
+        g, kap = _F(lib, lam, 1, 1)
+        o = oracle.collapse_F(lam, 1)
+        if kap >= 1e-3:  # not sent to the FP64 redo
+            assert abs(g - o) <= 1e-4 * abs(o) + 1e-6, (lam, g, o, kap)
+
+
+@pytest.mark.parametrize("delta", [0.1, 1.0, 4.0])
+def test_limits(lib, delta):
+    g, _ = _F(lib, [delta / 3] * 3, 1, 0)
+    assert abs(g - delta / oracle.delta_c()) < 1e-12 * delta
+    g, _ = _F(lib, [delta, 0.0, 0.0], 0, 0)
+    assert abs(g - delta) < 1e-12 * delta
+    g, _ = _F(lib, [-delta / 3] * 3, 1, 0)
+    assert g == 0.0
+
+
+def test_eigen_fp64_and_fp32(lib):
+    rng = np.random.default_rng(2)
+    for _ in range(3000):
+        h = rng.normal(size=6)
+        for use_float, tol in ((0, 1e-12), (1, 2e-5)):
+            lam = np.empty(3)
+            r = lib.host_eig(h.ctypes.data_as(DP), lam.ctypes.data_as(DP), use_float)
+            ref = oracle.eig3(h)
+            if use_float and 1 - r < 2e-4:
+                continue  # near-degenerate: the kernel redoes these in FP64
+            assert np.abs(lam - ref).max() <= tol * np.abs(h).max(), (h, lam, ref)
