@@ -138,17 +138,17 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(),
+            "config": _config(WORKLOAD),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _config():
-    w = WORKLOAD
-    return {"workload": "768^3 grid, box 3072 Mpc/h, seed 3, 40 radii 120->4 Mpc/h (log), "
-                        "BBKS Gamma=0.21 n=0.96 sigma8=0.8",
+def _config(w):
+    return {"workload": "%d^3 grid, box %.0f Mpc/h, seed %d, %d radii %.0f->%.0f Mpc/h (log), "
+                        "BBKS Gamma=0.21 n=0.96 sigma8=0.8"
+                        % (w["n"], w["box"], w["seed"], w["nscales"], w["r_max"], w["r_min"]),
             "grid": w["n"], "box_mpc_h": w["box"], "nscales": w["nscales"],
             "parallelism": "replicas",
             "l2": "inputs larger than L2 (delta(k) 1.8 GB, per-pass spectra 5.5-11 GB)"}
@@ -164,7 +164,12 @@ def run_ours(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
-    w = WORKLOAD
+    w = dict(WORKLOAD)
+    if args.grid:
+        # smaller grid with the same 4 Mpc/h cells (profiling captures)
+        w["n"], w["box"] = args.grid, 4.0 * args.grid
+    if args.nscales:
+        w["nscales"] = args.nscales
     n, S = w["n"], w["nscales"]
     radii = ic.log_radii(w["r_min"], w["r_max"], S)
     stream = torch.cuda.Stream()
@@ -212,18 +217,20 @@ def run_ours(args):
     # end to end through the public API with host buffers: pinned delta(k) in,
     # F_max and scale index out, copies inside the timed region
     pin.pin_profile(plan.handle, 0)
-    hd = torch.from_numpy(d32).pin_memory()
-    hF = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
-    hI = torch.empty((n, n, n), dtype=torch.int32).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)
-    pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)  # warm graph
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e_s = float("nan")
+    if not args.no_e2e:
+        hd = torch.from_numpy(d32).pin_memory()
+        hF = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+        hI = torch.empty((n, n, n), dtype=torch.int32).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
         pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)
-        pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+        pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)  # warm graph
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)
+            pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
     barrier()
     if ws > 1:
         t = torch.tensor([e2e_s], device="cuda")
@@ -251,13 +258,13 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w),
             "roofline": {"bound": "hbm", "kernel": "k_pass_" + names[dom],
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "passes": passes},
             "cpu_baseline": cb,
-            "e2e": {"value": updates * ws / e2e_s, "unit": UNIT,
+            "e2e": None if args.no_e2e else {"value": updates * ws / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(d32.nbytes), "d2h_bytes_per_step": int(8 * n ** 3)},
             "gpu_launches": int(args.steps * pin.pin_kernels_per_call(plan.handle)),
             "clocks": clk.summary(),
@@ -278,6 +285,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="grid side for profiling captures (box = 4 Mpc/h per cell); default 768")
+    ap.add_argument("--nscales", type=int, default=0, help="number of radii; default 40")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
