@@ -130,6 +130,34 @@ int pin_kernels_per_call(pin_plan_t p);
 pin_status pin_profile(pin_plan_t p, int enable);
 pin_status pin_pass_times(pin_plan_t p, double* ms3);
 
+/* Largest grid side the no-allocation entry point below accepts. */
+#define PIN_NOALLOC_MAX_N 64
+
+/* pin_collapse_times without any device allocation, for callers that cannot
+ * allocate at call time: a serving process whose pool already holds all the
+ * memory it may use, code running inside an allocator hook, or a latency-
+ * critical caller that cannot accept cudaFree's implicit device-wide
+ * synchronisation.  (The paper has no counterpart; this is an interface
+ * convenience over the same passes.)
+ *
+ * Inputs and outputs are device pointers owned by the caller: delta_k is the
+ * half-spectrum (dtype PIN_C64 or PIN_C128, layout as for pin_set_ic), radii
+ * the nscales radii in host memory, F_max and scale_idx the N^3 outputs, with
+ * the meaning of pin_collapse_times.  Work is enqueued on `stream` (NULL: the
+ * legacy default stream) and the call returns without waiting.
+ *
+ * The workspace is one static device array of about 11.2 MB, sized for
+ * n <= PIN_NOALLOC_MAX_N, which every GPU that loads this library holds until
+ * the process exits.  Larger n returns PIN_EINVAL, as do the argument errors
+ * of pin_plan.  The first call on a device sets that device up (looks up the
+ * array's address, loads constant tables, sets kernel limits); make it before
+ * any stream capture.  All calls share the array and it keeps the previous
+ * call's contents (each call rewrites everything it reads); calls whose work
+ * overlaps on the GPU race on it, so the caller must serialise them. */
+pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype, int n, double box,
+                                      int nscales, const double* radii, int correction,
+                                      float* F_max, int32_t* scale_idx, void* stream);
+
 const char* pin_strerror(pin_status s);
 const char* pin_last_error(pin_plan_t p);
 

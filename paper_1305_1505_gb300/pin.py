@@ -45,7 +45,7 @@ class pin_stats(ctypes.Structure):
 # every symbol include/pin.h declares
 EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_hessian",
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
-           "pin_profile", "pin_pass_times",
+           "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc",
            "pin_strerror", "pin_last_error", "pin_destroy")
 
 _lib = None
@@ -83,6 +83,10 @@ def load(path=None):
     L.pin_profile.restype = ctypes.c_int
     L.pin_pass_times.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     L.pin_pass_times.restype = ctypes.c_int
+    L.pin_collapse_times_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_int, P, P, P]
+    L.pin_collapse_times_noalloc.restype = ctypes.c_int
     L.pin_strerror.argtypes = [ctypes.c_int]
     L.pin_strerror.restype = ctypes.c_char_p
     L.pin_last_error.argtypes = [P]
@@ -170,6 +174,19 @@ def pin_pass_times(plan):
     ms = (ctypes.c_double * 3)()
     _check(load().pin_pass_times(plan, ms), plan)
     return list(ms)
+
+
+def pin_collapse_times_noalloc(delta_k_ptr, dtype, n, box, radii, correction, fmax_ptr, idx_ptr,
+                               stream_ptr=None):
+    """No-allocation collapse times for n <= 64 (device pointers in and out);
+    for callers that cannot allocate device memory at call time."""
+    r = np.ascontiguousarray(radii, dtype=np.float64)
+    st = load().pin_collapse_times_noalloc(ctypes.c_void_p(delta_k_ptr), int(dtype), int(n),
+                                           float(box), int(r.size),
+                                           r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           int(correction), ctypes.c_void_p(fmax_ptr),
+                                           ctypes.c_void_p(idx_ptr), ctypes.c_void_p(stream_ptr))
+    _check(st)
 
 
 def pin_strerror(status):
