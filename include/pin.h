@@ -71,6 +71,8 @@ typedef struct {
 typedef struct {
   uint64_t eig_fp64_redo;   /* particle-scales redone in FP64 for a near-degenerate pair */
   uint64_t root_fp64_redo;  /* particle-scales redone in FP64 for a near-tangent root */
+  uint64_t fp64_queue_overflow; /* of those, kept at FP32 because the redo queue of a
+                                   radius (1/64 of the grid) was full */
   uint64_t collapse_calls;  /* completed pin_collapse_times calls */
 } pin_stats;
 
@@ -126,7 +128,8 @@ int pin_kernels_per_call(pin_plan_t p);
  * inside its graph); pin_pass_times() then waits for the plan's work and
  * returns, for the last completed call, the device time in milliseconds summed
  * over radii of the x pass (filter + transform), the y pass and the z pass
- * (c2r + eigenvalues + collapse + running max): ms3[0..2]. */
+ * (c2r + eigenvalues + collapse + running max, with the FP64 redo of the
+ * queued ill-conditioned particles): ms3[0..2]. */
 pin_status pin_profile(pin_plan_t p, int enable);
 pin_status pin_pass_times(pin_plan_t p, double* ms3);
 
@@ -146,7 +149,7 @@ pin_status pin_pass_times(pin_plan_t p, double* ms3);
  * the meaning of pin_collapse_times.  Work is enqueued on `stream` (NULL: the
  * legacy default stream) and the call returns without waiting.
  *
- * The workspace is one static device array of about 11.2 MB, sized for
+ * The workspace is one static device array of about 11.3 MB, sized for
  * n <= PIN_NOALLOC_MAX_N, which every GPU that loads this library holds until
  * the process exits.  Larger n returns PIN_EINVAL, as do the argument errors
  * of pin_plan.  The first call on a device sets that device up (looks up the

@@ -39,6 +39,7 @@ def _stale(target, deps):
 
 def cmd_pin(extra=()):
     return ([NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared",
+                             "-Werror", "cross-execution-space-call",
                              "-Xcompiler", "-fPIC", "-I", INC, "-I", os.path.join(PKG, "csrc"),
                              "-o", LIBPIN] + list(extra) + _sources_pin())
 

@@ -29,22 +29,85 @@
 
 namespace pin {
 
+// Arithmetic of one precision.  FP64 (the redo of ill-conditioned particles)
+// uses the accurate library functions.  FP32 keeps the hot loop short:
+//  - acos: Abramowitz & Stegun 4.4.46 (Hastings) sqrt(1-x) * (degree-7
+//    polynomial), |error| <= 2e-8 on [0, 1], mirrored for x < 0;
+//  - sin/cos of arguments in [0, pi] and exp of non-positive arguments: the
+//    hardware approximations (absolute error ~2^-21 for sin/cos);
+//  - cbrt: exp2(log2|x| / 3) from the hardware approximations, then one
+//    Newton step u <- (2u + x/u^2)/3, which squares the relative error;
+//  - division: the two-ulp fast form.
+// On the host (unit tests) the same formulas run with the C++ library
+// standing in for the hardware approximations.
 template <typename T> struct M;
 template <> struct M<float> {
-  __host__ __device__ __forceinline__ static float sqrt_(float x) { return std::sqrt(x); }
-  __host__ __device__ __forceinline__ static float acos_(float x) { return std::acos(x); }
-  __host__ __device__ __forceinline__ static float cos_(float x) { return std::cos(x); }
-  __host__ __device__ __forceinline__ static float cbrt_(float x) { return std::cbrt(x); }
-  __host__ __device__ __forceinline__ static float exp_(float x) { return std::exp(x); }
-  __host__ __device__ __forceinline__ static float fma_(float a, float b, float c) { return std::fma(a, b, c); }
+  __host__ __device__ __forceinline__ static float sqrt_(float x) { return sqrtf(x); }
+  __host__ __device__ __forceinline__ static float div_(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+  }
+  __host__ __device__ __forceinline__ static float acos_(float x) {
+    const float ax = fabsf(x);
+    float poly = -0.0012624911f;
+    poly = fmaf(poly, ax, 0.0066700901f);
+    poly = fmaf(poly, ax, -0.0170881256f);
+    poly = fmaf(poly, ax, 0.0308918810f);
+    poly = fmaf(poly, ax, -0.0501743046f);
+    poly = fmaf(poly, ax, 0.0889789874f);
+    poly = fmaf(poly, ax, -0.2145988016f);
+    poly = fmaf(poly, ax, 1.5707963050f);
+    const float r = sqrtf(1.0f - ax) * poly;
+    return x < 0.0f ? 3.14159265358979f - r : r;
+  }
+  __host__ __device__ __forceinline__ static void sincos_(float x, float* sn, float* cs) {
+#ifdef __CUDA_ARCH__
+    __sincosf(x, sn, cs);
+#else
+    *sn = std::sin(x);
+    *cs = std::cos(x);
+#endif
+  }
+  __host__ __device__ __forceinline__ static float cos_(float x) {
+#ifdef __CUDA_ARCH__
+    return __cosf(x);
+#else
+    return std::cos(x);
+#endif
+  }
+  __host__ __device__ __forceinline__ static float exp_(float x) {
+#ifdef __CUDA_ARCH__
+    return __expf(x);
+#else
+    return std::exp(x);
+#endif
+  }
+  __host__ __device__ __forceinline__ static float cbrt_(float x) {
+    if (x == 0.0f) return 0.0f;
+    const float ax = fabsf(x);
+#ifdef __CUDA_ARCH__
+    float u = exp2f(__log2f(ax) * (1.0f / 3.0f));
+#else
+    float u = std::exp2(std::log2(ax) * (1.0f / 3.0f));
+#endif
+    u = (2.0f * u + div_(ax, u * u)) * (1.0f / 3.0f);
+    return x < 0.0f ? -u : u;
+  }
 };
 template <> struct M<double> {
   __host__ __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
+  __host__ __device__ __forceinline__ static double div_(double a, double b) { return a / b; }
   __host__ __device__ __forceinline__ static double acos_(double x) { return acos(x); }
+  __host__ __device__ __forceinline__ static void sincos_(double x, double* sn, double* cs) {
+    *sn = sin(x);
+    *cs = cos(x);
+  }
   __host__ __device__ __forceinline__ static double cos_(double x) { return cos(x); }
-  __host__ __device__ __forceinline__ static double cbrt_(double x) { return cbrt(x); }
   __host__ __device__ __forceinline__ static double exp_(double x) { return exp(x); }
-  __host__ __device__ __forceinline__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
+  __host__ __device__ __forceinline__ static double cbrt_(double x) { return cbrt(x); }
 };
 
 // Closed-form eigenvalues of the symmetric 3x3 matrix
@@ -55,7 +118,8 @@ template <> struct M<double> {
 template <typename T>
 __host__ __device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
   using F = M<T>;
-  const T q = (h[0] + h[1] + h[2]) / T(3);
+  const T third = T(1) / T(3);
+  const T q = (h[0] + h[1] + h[2]) * third;
   const T b0 = h[0] - q, b1 = h[1] - q, b2 = h[2] - q;
   const T off = h[3] * h[3] + h[4] * h[4] + h[5] * h[5];
   const T p2 = b0 * b0 + b1 * b1 + b2 * b2 + T(2) * off;
@@ -63,16 +127,18 @@ __host__ __device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
     lam[0] = lam[1] = lam[2] = q;
     return T(1);
   }
-  const T p = F::sqrt_(p2 / T(6));
+  const T p = F::sqrt_(p2 * (T(1) / T(6)));
   // det(A - qI)
   const T det = b0 * (b1 * b2 - h[5] * h[5]) - h[3] * (h[3] * b2 - h[5] * h[4]) +
                 h[4] * (h[3] * h[5] - b1 * h[4]);
-  T r = det / (T(2) * p * p * p);
+  T r = F::div_(det, T(2) * p * p * p);
   r = r > T(1) ? T(1) : (r < T(-1) ? T(-1) : r);
-  const T phi = F::acos_(r) / T(3);
-  const T two_pi_3 = T(2.0943951023931954923);
-  const T l0 = q + T(2) * p * F::cos_(phi);
-  const T l2 = q + T(2) * p * F::cos_(phi + two_pi_3);
+  const T phi = F::acos_(r) * third;
+  T sn, cs;
+  F::sincos_(phi, &sn, &cs);
+  // cos(phi + 2 pi/3) = -cos(phi)/2 - (sqrt(3)/2) sin(phi)
+  const T l0 = q + T(2) * p * cs;
+  const T l2 = q - p * (cs + T(1.7320508075688772935) * sn);
   lam[0] = l0;
   lam[2] = l2;
   lam[1] = T(3) * q - l0 - l2;
@@ -85,24 +151,25 @@ __host__ __device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
 template <typename T>
 __host__ __device__ __forceinline__ T largest_root(T c1, T c2, T c3, T& kappa) {
   using F = M<T>;
-  const T s = c1 / T(3);
+  const T third = T(1) / T(3);
+  const T s = c1 * third;
   const T p = -c2 - c1 * s;                                   // b - a^2/3
-  const T q = -c3 - c1 * c2 / T(3) - T(2) * s * s * s;         // 2a^3/27 - ab/3 + c
-  const T hq = q / T(2), tp = p / T(3);
+  const T q = -c3 - c2 * s - T(2) * s * s * s;                 // 2a^3/27 - ab/3 + c
+  const T hq = q * T(0.5), tp = p * third;
   const T disc = hq * hq + tp * tp * tp;
   T t;
   if (disc <= T(0) && p < T(0)) {
     // three real roots t_k = m cos(theta/3 - 2 pi k/3); the largest is k = 0
     const T m = T(2) * F::sqrt_(-tp);
-    T arg = T(3) * q / (p * m);
+    T arg = F::div_(T(3) * q, p * m);
     arg = arg > T(1) ? T(1) : (arg < T(-1) ? T(-1) : arg);
-    t = m * F::cos_(F::acos_(arg) / T(3));
+    t = m * F::cos_(F::acos_(arg) * third);
   } else {
     // one real root: t = u - p/(3u), u the cube root of larger magnitude
     const T sd = F::sqrt_(disc > T(0) ? disc : T(0));
     const T w = hq >= T(0) ? -hq - sd : -hq + sd;
     const T u = F::cbrt_(w);
-    t = (u != T(0)) ? u - tp / u : T(0);
+    t = (u != T(0)) ? u - F::div_(tp, u) : T(0);
   }
   T x = t + s;
   // Newton polish on g
@@ -110,16 +177,12 @@ __host__ __device__ __forceinline__ T largest_root(T c1, T c2, T c3, T& kappa) {
   for (int it = 0; it < 2; ++it) {
     const T g = ((x - c1) * x - c2) * x - c3;
     const T dg = (T(3) * x - T(2) * c1) * x - c2;
-    if (dg != T(0)) {
-      const T nx = x - g / dg;
-      // stay at or above the largest root: g' > 0 there
-      x = nx;
-    }
+    if (dg != T(0)) x = x - F::div_(g, dg);
   }
   const T dg = (T(3) * x - T(2) * c1) * x - c2;
   const T ac1 = c1 < T(0) ? -c1 : c1, ac2 = c2 < T(0) ? -c2 : c2, ax = x < T(0) ? -x : x;
   const T scale = T(3) * x * x + T(2) * ac1 * ax + ac2;
-  kappa = scale > T(0) ? (dg < T(0) ? -dg : dg) / scale : T(1);
+  kappa = scale > T(0) ? F::div_(dg < T(0) ? -dg : dg, scale) : T(1);
   return x > T(0) ? x : T(0);
 }
 
@@ -129,18 +192,37 @@ struct CollapseConsts {
   int correction;
 };
 
+// True when g(F) = F^3 - c1 F^2 - c2 F - c3 has no real root at or above T:
+// g(T) > 0 and g stays positive beyond T, i.e. g' has no real root, or the
+// right critical point F* = (c1 + sqrt(c1^2 + 3 c2))/3 lies at or below T, or
+// g(F*) > 0 (g is increasing beyond F*).  Exact up to rounding, and far
+// cheaper than solving the cubic.
+template <typename T>
+__host__ __device__ __forceinline__ bool no_root_from(T c1, T c2, T c3, T t) {
+  using F = M<T>;
+  const T gt = ((t - c1) * t - c2) * t - c3;
+  if (!(gt > T(0))) return false;
+  const T d = c1 * c1 + T(3) * c2;
+  if (d < T(0)) return true;
+  const T fs = (c1 + F::sqrt_(d)) * (T(1) / T(3));
+  if (fs <= t) return true;
+  return ((fs - c1) * fs - c2) * fs - c3 > T(0);
+}
+
 // F for sorted eigenvalues lam; kappa_min receives the conditioning of the
-// root that set F (1 when nothing collapses).
+// root that set F (1 when nothing collapses).  The axis of the largest
+// eigenvalue is solved first; the other two are solved only when they can
+// collapse earlier (no_root_from), which is rare.
 template <typename T>
 __host__ __device__ __forceinline__ T collapse_from_eigs(const T lam[3], const CollapseConsts<T>& cc,
-                                                T& kappa_min) {
+                                                         T& kappa_min) {
   using F = M<T>;
   const T mu1 = lam[0] + lam[1] + lam[2];
   const T mu3 = lam[0] * lam[1] * lam[2];
   T e[3];
-  e[0] = lam[0] * (lam[1] + lam[2]) / T(2);
-  e[1] = lam[1] * (lam[0] + lam[2]) / T(2);
-  e[2] = lam[2] * (lam[0] + lam[1]) / T(2);
+  e[0] = T(0.5) * lam[0] * (lam[1] + lam[2]);
+  e[1] = T(0.5) * lam[1] * (lam[0] + lam[2]);
+  e[2] = T(0.5) * lam[2] * (lam[0] + lam[1]);
   T best = T(0);
   kappa_min = T(1);
 #pragma unroll
@@ -148,7 +230,9 @@ __host__ __device__ __forceinline__ T collapse_from_eigs(const T lam[3], const C
     const int j = (i + 1) % 3, k = (i + 2) % 3;
     const T c1 = lam[i];
     const T c2 = T(3) / T(7) * e[i];
-    const T c3 = T(10) / T(84) * (lam[i] * (e[j] + e[k]) + e[i] * (lam[j] + lam[k])) - mu3 / T(9);
+    const T c3 = T(10) / T(84) * (lam[i] * (e[j] + e[k]) + e[i] * (lam[j] + lam[k])) -
+                 mu3 * (T(1) / T(9));
+    if (i > 0 && no_root_from<T>(c1, c2, c3, best)) continue;
     T kap;
     const T Fi = largest_root<T>(c1, c2, c3, kap);
     if (Fi > best) {
@@ -157,8 +241,7 @@ __host__ __device__ __forceinline__ T collapse_from_eigs(const T lam[3], const C
     }
   }
   if (cc.correction && mu1 > T(0)) {
-    const T eps = (lam[0] - lam[2]) / mu1;
-    const T z = eps / T(0.1);
+    const T z = F::div_(T(10) * (lam[0] - lam[2]), mu1);  // eps / 0.1
     best += mu1 * cc.dcorr * F::exp_(-z * z);
   }
   return best;

@@ -21,8 +21,24 @@ namespace pin {
 // ---------------------------------------------------------------- x pass --
 // Lines along x: column index col in [0, N*nhp) enumerates (ky, kz); element
 // (kx, col) sits at kx*N*nhp + col, so a row of TC columns is contiguous.
+// Resident blocks per SM the register budget is sized for (shared memory
+// already limits the long-line passes to one or two blocks per SM).
+#ifndef PIN_XY_MINB
+#define PIN_XY_MINB 1
+#endif
+#ifndef PIN_Z_MINB
+#define PIN_Z_MINB 2
+#endif
+// Independent particles per iteration of the collapse loop.
+#ifndef PIN_Z_ILP
+#define PIN_Z_ILP 2
+#endif
+template <int N> struct MinBlocks {
+  static constexpr int xy = N >= 384 ? PIN_XY_MINB : 1, z = N >= 384 ? PIN_Z_MINB : 1;
+};
+
 template <int N, int TC>
-__global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_x(ArgsX a) {
+__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(ArgsX a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
   using L = XLayoutCols<E, P, TC>;
   extern __shared__ float4 smem_raw[];
@@ -68,7 +84,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_x(ArgsX a) {
 // Lines along y: column col in [0, N*nhp) enumerates (x, kz); element
 // (ky, col) sits at (x*N + ky)*nhp + kz.
 template <int N, int TC>
-__global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_y(ArgsY a) {
+__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(ArgsY a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
   using L = XLayoutCols<E, P, TC>;
   extern __shared__ float4 smem_raw[];
@@ -77,7 +93,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_y(ArgsY a) {
   float* s_m = reinterpret_cast<float*>(s_tw + E * P);  // [3][N] multipliers
   __shared__ float2* s_dst[kMaxFields];
   __shared__ const float2* s_src[kMaxFields];
-  __shared__ int s_ym[kMaxFields];
+  __shared__ int s_ym[kMaxFields], s_zm[kMaxFields], s_mi[kMaxFields];
   const int tid = threadIdx.x, c = tid % TC, p = tid / TC;
   for (int i = tid; i < E * P; i += TC * P) s_tw[i] = a.tw[i];
   for (int i = tid; i < 3 * N; i += TC * P) s_m[i] = a.mult[i];
@@ -85,6 +101,8 @@ __global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_y(ArgsY a) {
     s_dst[tid] = a.dst[tid];
     s_src[tid] = a.src[a.sel[tid] < 3 ? a.sel[tid] : 0];
     s_ym[tid] = a.ym[tid];
+    s_zm[tid] = a.zm[tid];
+    s_mi[tid] = a.muli[tid];
   }
   __syncthreads();
   const int nhp = a.nhp;
@@ -105,11 +123,16 @@ __global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_y(ArgsY a) {
       v[t] = cscale(xv, mt[P * t]);
     }
     fft_line<N, L>(v, p, c, s_x, s_tw);
+    // z factor of this column (kz < N/2 + 1; pad columns carry zeros anyway)
+    const float zf = (ok && kz <= N / 2) ? s_m[s_zm[f] * N + kz] : 0.f;
+    const bool mi = s_mi[f] != 0;
     float2* d = s_dst[f] + base;
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int row = fft_out_index<N>(p, j);
-      if (ok) d[row * nhp] = v[j];
+      float2 o = cscale(v[j], zf);
+      if (mi) o = cmuli(o);
+      if (ok) d[row * nhp] = o;
     }
     __syncthreads();
   }
@@ -120,7 +143,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P) k_pass_y(ArgsY a) {
 // kz in [0, N/2], is contiguous.  Fields are paired (A + iB) into one complex
 // length-N transform whose real and imaginary parts are the two real lines.
 template <int N, int LINES, bool DUMP>
-__global__ void __launch_bounds__(3 * LINES * Shape<N>::P) k_pass_z(ArgsZ a) {
+__global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pass_z(ArgsZ a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
   constexpr int NC = 3 * LINES;  // at most three pairs per line
   using L = XLayoutLines<E, P, NC>;
@@ -149,22 +172,13 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P) k_pass_z(ArgsZ a) {
   {
     const float2* A = active ? a.src[fa] + (size_t)line * nhp : nullptr;
     const float2* B = hasb ? a.src[fb] + (size_t)line * nhp : nullptr;
-    const float* ma = a.mult + (active ? a.zm[fa] : 0) * N;
-    const float* mb = a.mult + (hasb ? a.zm[fb] : 0) * N;
-    const bool ia = active && a.muli[fa], ib = hasb && a.muli[fb];
 #pragma unroll
     for (int t = 0; t < E; ++t) {
       const int n = p + P * t;
       const int m = n <= N / 2 ? n : N - n;
       float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
-      if (active) {
-        xa = cscale(__ldg(A + m), __ldg(ma + m));
-        if (ia) xa = cmuli(xa);
-      }
-      if (hasb) {
-        xb = cscale(__ldg(B + m), __ldg(mb + m));
-        if (ib) xb = cmuli(xb);
-      }
+      if (active) xa = __ldg(A + m);
+      if (hasb) xb = __ldg(B + m);
       if (n == 0 || n == N / 2) {
         xa.y = 0.f;
         xb.y = 0.f;
@@ -201,36 +215,80 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P) k_pass_z(ArgsZ a) {
     }
     __syncthreads();
     CollapseConsts<float> ccf{a.dcorr_f, a.correction};
-    CollapseConsts<double> ccd{a.dcorr_d, a.correction};
-    for (int pt = tid; pt < LINES * N; pt += nthreads) {
-      const int l = pt / N, z = pt % N;
-      const int gl = blockIdx.x * LINES + l;
-      if (gl >= nlines) continue;
-      float h[6];
+    // PIN_Z_ILP independent particles per iteration: the collapse arithmetic
+    // is a long dependent chain, and the transform leaves few warps per SM
+    constexpr int kPts = LINES * N;
+    constexpr int U = PIN_Z_ILP;
+    for (int base_pt = tid; base_pt < kPts; base_pt += U * nthreads) {
+      float h[U][6], lam[U][3], F[U], kap[U], rabs[U];
+      int q[U];
+      bool valid[U];
 #pragma unroll
-      for (int f = 0; f < 6; ++f) h[f] = s_f[(l * 6 + f) * N + z];
-      float lam[3];
-      const float rabs = eig3<float>(h, lam);
-      float kap;
-      float F = collapse_from_eigs<float>(lam, ccf, kap);
-      const bool redo_eig = rabs > 1.f - a.tau_eig;
-      const bool redo_root = kap < a.tau_root;
-      if (redo_eig || redo_root) {
-        double hd[6], ld[3], kd;
+      for (int u = 0; u < U; ++u) {
+        const int pt = base_pt + u * nthreads;
+        const int l = pt / N, z = pt % N;
+        const int gl = blockIdx.x * LINES + l;
+        valid[u] = pt < kPts && gl < nlines;
+        q[u] = gl * N + z;
 #pragma unroll
-        for (int f = 0; f < 6; ++f) hd[f] = (double)h[f];
-        eig3<double>(hd, ld);
-        F = (float)collapse_from_eigs<double>(ld, ccd, kd);
-        atomicAdd(a.counters + (redo_eig ? 0 : 1), 1ull);
+        for (int f = 0; f < 6; ++f) h[u][f] = valid[u] ? s_f[(l * 6 + f) * N + z] : 0.f;
       }
-      const size_t q = (size_t)gl * N + z;
-      const float fm = a.fmax[q];
-      if (F > fm) {
-        a.fmax[q] = F;
-        a.idx[q] = a.scale;
+#pragma unroll
+      for (int u = 0; u < U; ++u) rabs[u] = eig3<float>(h[u], lam[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) F[u] = collapse_from_eigs<float>(lam[u], ccf, kap[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!valid[u]) continue;
+        const bool redo_eig = rabs[u] > 1.f - a.tau_eig;
+        const bool redo_root = kap[u] < a.tau_root;
+        if (redo_eig || redo_root) {
+          atomicAdd(a.counters + (redo_eig ? 0 : 1), 1ull);
+          const unsigned slot = atomicAdd(a.redo_count, 1u);
+          if (slot < a.redo_cap) {
+            RedoEntry e;
+            e.q = q[u];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) e.h[f] = h[u][f];
+            e.pad = 0;
+            a.redo_list[slot] = e;
+            continue;  // the redo kernel updates this particle
+          }
+          atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
+        }
+        const float fm = a.fmax[q[u]];
+        if (F[u] > fm) {
+          a.fmax[q[u]] = F[u];
+          a.idx[q[u]] = a.scale;
+        }
       }
     }
   }
+}
+
+// FP64 redo of the queued particles of one radius (grid-stride; each particle
+// appears once per radius, so the in-place update has no race).
+__global__ void __launch_bounds__(128) k_redo64(ArgsZ a) {
+  const unsigned cnt = *a.redo_count;
+  const unsigned n = cnt < a.redo_cap ? cnt : a.redo_cap;
+  CollapseConsts<double> ccd{a.dcorr_d, a.correction};
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const RedoEntry e = a.redo_list[i];
+    double h[6], lam[3], kap;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) h[f] = (double)e.h[f];
+    eig3<double>(h, lam);
+    const float F = (float)collapse_from_eigs<double>(lam, ccd, kap);
+    if (F > a.fmax[e.q]) {
+      a.fmax[e.q] = F;
+      a.idx[e.q] = a.scale;
+    }
+  }
+}
+
+cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st) {
+  k_redo64<<<2 * 152, 128, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 // -------------------------------------------------------------- dispatch --

@@ -28,26 +28,35 @@ struct ArgsX {
   int nhp;
 };
 
-// y pass: dst[f] = IDFT_y(mult[ym[f]] * src[sel[f]]).
+// y pass: dst[f] = zfac[f](kz) * IDFT_y(mult[ym[f]] * src[sel[f]]), where the
+// z factor mult[zm[f]](kz), times i when muli[f], is constant along a y line.
 struct ArgsY {
   const float2* src[3];
   float2* dst[kMaxFields];
   int sel[kMaxFields];
   int ym[kMaxFields];
+  int zm[kMaxFields];
+  int muli[kMaxFields];
   int nout;
   const float* mult;
   const float2* tw;
   int nhp;
 };
 
-// z pass: c2r of each field (times i where muli is set) after the z
-// multiplier, then either the collapse update or a dump of the real fields.
+// A particle whose FP32 collapse is ill-conditioned (near-degenerate
+// eigenvalue pair or near-tangent root): its grid index and the six FP32
+// Hessian components, finished in FP64 by the redo kernel.
+struct RedoEntry {
+  int q;
+  float h[6];
+  int pad;
+};
+
+// z pass: c2r of each field (its z factor already applied by the y pass),
+// then either the collapse update or a dump of the real fields.
 struct ArgsZ {
   const float2* src[kMaxFields];
-  int zm[kMaxFields];
-  int muli[kMaxFields];
   int nfields;
-  const float* mult;
   const float2* tw;
   int nhp;
   // collapse mode
@@ -59,7 +68,10 @@ struct ArgsZ {
   double dcorr_d;
   float tau_eig;   // FP64 redo when |r| > 1 - tau_eig
   float tau_root;  // FP64 redo when kappa < tau_root
-  unsigned long long* counters;  // [0] eigen redo, [1] root redo
+  unsigned long long* counters;  // [0] eigen redo, [1] root redo, [2] list overflow
+  RedoEntry* redo_list;          // FP64 redo queue of this radius
+  unsigned* redo_count;          // zeroed before the z pass
+  unsigned redo_cap;
   // dump mode
   float* out[kMaxFields];
 };
@@ -79,6 +91,8 @@ cudaError_t prepare_kernels(int n);  // sets shared-memory attributes (once per 
 cudaError_t launch_x(int n, const ArgsX& a, cudaStream_t st);
 cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st);
 cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st);
+// FP64 redo of the particles the z pass queued (after it, same stream).
+cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st);
 cudaError_t upload_constant_twiddles();  // per device
 
 }  // namespace pin

@@ -37,10 +37,13 @@ constexpr size_t kOffU = kOffPhi0 + kSpecBytes;
 constexpr size_t kOffV = kOffU + 3 * kSpecBytes;
 constexpr size_t kOffMult = kOffV + 6 * kSpecBytes;
 constexpr size_t kOffTw = kOffMult + kMultBytes;
+constexpr size_t kRedoCap = (size_t)kMaxN * kMaxN * kMaxN / 64;
 constexpr size_t kOffCnt = kOffTw + kTwBytes;
-constexpr size_t kScratchBytes = ((kOffCnt + 2 * sizeof(unsigned long long)) + 255) & ~(size_t)255;
+constexpr size_t kOffRedoCount = kOffCnt + 4 * sizeof(unsigned long long);
+constexpr size_t kOffRedo = (kOffRedoCount + sizeof(unsigned) + 255) & ~(size_t)255;
+constexpr size_t kScratchBytes = (kOffRedo + kRedoCap * sizeof(pin::RedoEntry) + 255) & ~(size_t)255;
 
-// The whole workspace of this entry point (about 11.2 MB for N <= 64).  In host
+// The whole workspace of this entry point (about 11.3 MB for N <= 64).  In host
 // code this name is only a stand-in for the symbol, never a device address:
 // the address comes from cudaGetSymbolAddress at set-up.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -171,6 +174,8 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
   float* mult = reinterpret_cast<float*>(base + kOffMult);
   float2* tw = reinterpret_cast<float2*>(base + kOffTw);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + kOffCnt);
+  unsigned* redo_count = reinterpret_cast<unsigned*>(base + kOffRedoCount);
+  pin::RedoEntry* redo_list = reinterpret_cast<pin::RedoEntry*>(base + kOffRedo);
   const double dcorr = noalloc_dcorr();
   const size_t n3 = (size_t)n * n * n;
 
@@ -179,7 +184,7 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
   k_noalloc_tables<<<tblocks, tthreads, 0, cs>>>(rr, nscales, n, box, sh.E, sh.P, mult, tw);
   k_noalloc_phi0<<<(unsigned)((spec + 255) / 256), 256, 0, cs>>>(delta_k, dtype, n, nhp, box, phi0);
   if (cudaGetLastError() != cudaSuccess) return PIN_ECUDA;
-  if (cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), cs) != cudaSuccess ||
+  if (cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), cs) != cudaSuccess ||
       cudaMemsetAsync(F_max, 0, n3 * sizeof(float), cs) != cudaSuccess ||
       cudaMemsetAsync(scale_idx, 0xFF, n3 * sizeof(int32_t), cs) != cudaSuccess)
     return PIN_ECUDA;
@@ -198,15 +203,20 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
     ax.nhp = nhp;
     pin::ArgsY ay{};
     for (int f = 0; f < 3; ++f) ay.src[f] = U + f * spec;
-    for (int f = 0; f < 6; ++f) { ay.dst[f] = V + f * spec; ay.sel[f] = sel[f]; ay.ym[f] = ym[f]; }
+    for (int f = 0; f < 6; ++f) {
+      ay.dst[f] = V + f * spec;
+      ay.sel[f] = sel[f];
+      ay.ym[f] = ym[f];
+      ay.zm[f] = zm[f];
+      ay.muli[f] = 0;
+    }
     ay.nout = 6;
     ay.mult = m;
     ay.tw = tw;
     ay.nhp = nhp;
     pin::ArgsZ az{};
-    for (int f = 0; f < 6; ++f) { az.src[f] = V + f * spec; az.zm[f] = zm[f]; az.muli[f] = 0; }
+    for (int f = 0; f < 6; ++f) az.src[f] = V + f * spec;
     az.nfields = 6;
-    az.mult = m;
     az.tw = tw;
     az.nhp = nhp;
     az.fmax = F_max;
@@ -218,8 +228,12 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
     az.tau_eig = 2e-4f;
     az.tau_root = 1e-3f;
     az.counters = cnt;
+    az.redo_list = redo_list;
+    az.redo_count = redo_count;
+    az.redo_cap = (unsigned)kRedoCap;
     if (pin::launch_x(n, ax, cs) != cudaSuccess || pin::launch_y(n, ay, cs) != cudaSuccess ||
-        pin::launch_z(n, az, false, cs) != cudaSuccess)
+        cudaMemsetAsync(redo_count, 0, sizeof(unsigned), cs) != cudaSuccess ||
+        pin::launch_z(n, az, false, cs) != cudaSuccess || pin::launch_redo(az, cs) != cudaSuccess)
       return PIN_ECUDA;
   }
   return PIN_OK;

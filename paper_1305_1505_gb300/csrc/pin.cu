@@ -39,7 +39,10 @@ struct pin_plan_s {
   int* idx = nullptr;
   float* mult = nullptr;  // (nscales + 1) x 3 x n; the last set has R = 0
   float2* tw = nullptr;
-  unsigned long long* counters = nullptr;  // [0] eig redo, [1] root redo
+  unsigned long long* counters = nullptr;  // [0] eig redo, [1] root redo, [2] queue overflow
+  RedoEntry* redo_list = nullptr;          // FP64 redo queue, reused by every radius
+  unsigned* redo_count = nullptr;
+  unsigned redo_cap = 0;
   bool ic_set = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -109,10 +112,17 @@ bool validate(const pin_plan_desc* d, std::string* why) {
   return true;
 }
 
+// FP64 redo queue capacity: 1/64 of the grid (observed rate ~2e-4), at least 64 Ki.
+unsigned redo_capacity(int n) {
+  const size_t n3 = (size_t)n * n * n;
+  return (unsigned)std::max<size_t>(65536, n3 / 64);
+}
+
 size_t footprint(int n, int nscales) {
   const size_t spec = (size_t)n * n * padded_half(n);
   const size_t n3 = (size_t)n * n * n;
-  return spec * 8 * 10 + n3 * 8 + (size_t)(nscales + 1) * 3 * n * 4 + (size_t)n * 8 + 64;
+  return spec * 8 * 10 + n3 * 8 + (size_t)(nscales + 1) * 3 * n * 4 + (size_t)n * 8 + 64 +
+         (size_t)redo_capacity(n) * sizeof(RedoEntry) + 16;
 }
 
 // Per-axis multipliers for one radius: {W, k W, k^2 W} / n with
@@ -190,6 +200,8 @@ void release(pin_plan_t p) {
   cudaFree(p->mult);
   cudaFree(p->tw);
   cudaFree(p->counters);
+  cudaFree(p->redo_list);
+  cudaFree(p->redo_count);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   p->events.clear();
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -221,7 +233,13 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   static const int zm[6] = {0, 0, 2, 0, 1, 1};
   ArgsY ay{};
   for (int f = 0; f < 3; ++f) ay.src[f] = spec(p, p->U, f);
-  for (int f = 0; f < 6; ++f) { ay.dst[f] = spec(p, p->V, f); ay.sel[f] = sel[f]; ay.ym[f] = ym[f]; }
+  for (int f = 0; f < 6; ++f) {
+    ay.dst[f] = spec(p, p->V, f);
+    ay.sel[f] = sel[f];
+    ay.ym[f] = ym[f];
+    ay.zm[f] = zm[f];
+    ay.muli[f] = 0;
+  }
   ay.nout = 6;
   ay.mult = mult;
   ay.tw = p->tw;
@@ -230,9 +248,8 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 2], p->stream, cudaEventRecordExternal));
 
   ArgsZ az{};
-  for (int f = 0; f < 6; ++f) { az.src[f] = spec(p, p->V, f); az.zm[f] = zm[f]; az.muli[f] = 0; }
+  for (int f = 0; f < 6; ++f) az.src[f] = spec(p, p->V, f);
   az.nfields = 6;
-  az.mult = mult;
   az.tw = p->tw;
   az.nhp = p->nhp;
   az.fmax = p->fmax;
@@ -244,9 +261,14 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   az.tau_eig = 2e-4f;
   az.tau_root = 1e-3f;
   az.counters = p->counters;
+  az.redo_list = p->redo_list;
+  az.redo_count = p->redo_count;
+  az.redo_cap = p->redo_cap;
   if (dump)
     for (int f = 0; f < 6; ++f) az.out[f] = dump[f];
+  if (!dump) PIN_CK(p, cudaMemsetAsync(p->redo_count, 0, sizeof(unsigned), p->stream));
   PIN_CK(p, launch_z(p->n, az, dump != nullptr, p->stream));
+  if (!dump) PIN_CK(p, launch_redo(az, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 3], p->stream, cudaEventRecordExternal));
   return PIN_OK;
 }
@@ -323,6 +345,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   p->shape = pass_shape(p->n);
   p->spec_elems = (size_t)p->n * p->n * p->nhp;
   p->dcorr = 1.0 / delta_c_value() - 1.0 / x3_value();
+  p->redo_cap = redo_capacity(p->n);
   auto bail = [&](pin_status s) {
     release(p);
     delete p;
@@ -344,7 +367,9 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
       cudaMalloc(&p->fmax, n3 * 4) != cudaSuccess || cudaMalloc(&p->idx, n3 * 4) != cudaSuccess ||
       cudaMalloc(&p->mult, mult_elems * 4) != cudaSuccess ||
       cudaMalloc(&p->tw, (size_t)p->n * 8) != cudaSuccess ||
-      cudaMalloc(&p->counters, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&p->counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&p->redo_list, (size_t)redo_capacity(p->n) * sizeof(RedoEntry)) != cudaSuccess ||
+      cudaMalloc(&p->redo_count, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     return bail(PIN_ENOMEM);
   }
@@ -361,7 +386,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
     }
   if (cudaMemcpy(p->mult, mult.data(), mult_elems * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(p->counters, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
+      cudaMemset(p->counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess)
     return bail(PIN_ECUDA);
   *out = p;
   return PIN_OK;
@@ -455,7 +480,13 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   ay.src[0] = spec(p, p->U, 0);
   ay.src[1] = spec(p, p->U, 1);
   const int sel[3] = {1, 0, 0}, ym[3] = {0, 1, 0}, zm[3] = {0, 0, 1};
-  for (int f = 0; f < 3; ++f) { ay.dst[f] = spec(p, p->V, f); ay.sel[f] = sel[f]; ay.ym[f] = ym[f]; }
+  for (int f = 0; f < 3; ++f) {
+    ay.dst[f] = spec(p, p->V, f);
+    ay.sel[f] = sel[f];
+    ay.ym[f] = ym[f];
+    ay.zm[f] = zm[f];
+    ay.muli[f] = 1;
+  }
   ay.nout = 3;
   ay.mult = mult;
   ay.tw = p->tw;
@@ -464,12 +495,9 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   ArgsZ az{};
   for (int f = 0; f < 3; ++f) {
     az.src[f] = spec(p, p->V, f);
-    az.zm[f] = zm[f];
-    az.muli[f] = 1;
     az.out[f] = dev + (size_t)f * n3;
   }
   az.nfields = 3;
-  az.mult = mult;
   az.tw = p->tw;
   az.nhp = p->nhp;
   if (e == cudaSuccess) e = launch_z(p->n, az, true, p->stream);
@@ -506,16 +534,17 @@ pin_status pin_get_stats(pin_plan_t p, pin_stats* out) {
   pin_status st = check_plan(p);
   if (st != PIN_OK) return st;
   if (!out) return fail(p, PIN_EINVAL, "null stats");
-  unsigned long long c[2] = {0, 0};
+  unsigned long long c[3] = {0, 0, 0};
   PIN_CK(p, cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, p->stream));
   PIN_CK(p, cudaStreamSynchronize(p->stream));
   out->eig_fp64_redo = c[0];
   out->root_fp64_redo = c[1];
+  out->fp64_queue_overflow = c[2];
   out->collapse_calls = p->calls;
   return PIN_OK;
 }
 
-int pin_kernels_per_call(pin_plan_t p) { return p ? 3 * p->nscales : 0; }
+int pin_kernels_per_call(pin_plan_t p) { return p ? 4 * p->nscales : 0; }
 
 pin_status pin_profile(pin_plan_t p, int enable) {
   pin_status st = check_plan(p);

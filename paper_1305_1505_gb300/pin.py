@@ -39,7 +39,7 @@ class pin_plan_desc(ctypes.Structure):
 
 class pin_stats(ctypes.Structure):
     _fields_ = [("eig_fp64_redo", ctypes.c_uint64), ("root_fp64_redo", ctypes.c_uint64),
-                ("collapse_calls", ctypes.c_uint64)]
+                ("fp64_queue_overflow", ctypes.c_uint64), ("collapse_calls", ctypes.c_uint64)]
 
 
 # every symbol include/pin.h declares
@@ -56,7 +56,8 @@ def load(path=None):
     global _lib
     if _lib is not None:
         return _lib
-    path = path or _build.ensure_pin()
+    # PIN_LIBRARY selects another build of the same sources (e.g. a tuning variant)
+    path = path or os.environ.get("PIN_LIBRARY") or _build.ensure_pin()
     if not os.path.exists(path):
         raise RuntimeError("libpin.so not found at %s; run __graft_entry__.build()" % path)
     L = ctypes.CDLL(path)
@@ -159,7 +160,7 @@ def pin_get_stats(plan):
     s = pin_stats()
     _check(load().pin_get_stats(plan, ctypes.byref(s)), plan)
     return dict(eig_fp64_redo=s.eig_fp64_redo, root_fp64_redo=s.root_fp64_redo,
-                collapse_calls=s.collapse_calls)
+                fp64_queue_overflow=s.fp64_queue_overflow, collapse_calls=s.collapse_calls)
 
 
 def pin_kernels_per_call(plan):
