@@ -156,8 +156,12 @@ struct XLayoutCols {
 };
 template <int E, int P, int NC>
 struct XLayoutLines {
-  static constexpr int kSize = NC * E * (P + 1);
-  __device__ __forceinline__ static int at(int k1, int p, int c) { return (c * E + k1) * (P + 1) + p; }
+  // per-line stride padded to P (mod 16) float2, so that the 32/P lines of a
+  // warp (each 2P banks wide) tile the 32 banks
+  static constexpr int kLine0 = E * (P + 1);
+  static constexpr int kLine = P >= 16 ? kLine0 : kLine0 + ((P - kLine0 % 16) % 16 + 16) % 16;
+  static constexpr int kSize = NC * kLine;
+  __device__ __forceinline__ static int at(int k1, int p, int c) { return c * kLine + k1 * (P + 1) + p; }
 };
 
 // Level-2 twiddles w_N^{p k1}, laid out [k1][p] in shared memory.

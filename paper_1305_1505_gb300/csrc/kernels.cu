@@ -8,6 +8,7 @@
 //             running maximum F_max with its radius index, written in place.
 // Each thread block owns a tile of lines; every line is transformed with the
 // two-level register FFT of fft.cuh (one shared-memory exchange per line).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -18,9 +19,75 @@
 
 namespace pin {
 
-// ---------------------------------------------------------------- x pass --
-// Lines along x: column index col in [0, N*nhp) enumerates (ky, kz); element
-// (kx, col) sits at kx*N*nhp + col, so a row of TC columns is contiguous.
+// ------------------------------------------------------ TMA + mbarrier --
+// Source tiles of the x and y passes are brought into shared memory by the
+// tensor memory accelerator (cp.async.bulk.tensor), completing on an mbarrier.
+// Every wait is bounded (about a second of SM clocks); a block that gives up
+// reports through the pass's error word and returns.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+// Block-uniform wait: true when the staged tile has landed for every thread.
+// On a timeout the block waits once more (bounded) for its copies in flight,
+// records the error and the caller returns.
+__device__ __forceinline__ bool stage_ready(uint32_t bar, uint32_t parity, int* err) {
+  const bool ok = mbar_wait_bounded(bar, parity);
+  if (__syncthreads_and(ok)) return true;
+  mbar_wait_bounded(bar, parity);
+  if (threadIdx.x == 0) atomicExch(err, 1);
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// Staged-tile geometry of a line length: kBoxes boxes of kRows rows (a box
+// dimension is at most 256).
+template <int N> struct Stage {
+  static constexpr int kBoxes = (N + 255) / 256;
+  static constexpr int kRows = N / kBoxes;
+};
+
 // Resident blocks per SM the register budget is sized for (shared memory
 // already limits the long-line passes to one or two blocks per SM).
 #ifndef PIN_XY_MINB
@@ -37,104 +104,162 @@ template <int N> struct MinBlocks {
   static constexpr int xy = N >= 384 ? PIN_XY_MINB : 1, z = N >= 384 ? PIN_Z_MINB : 1;
 };
 
+// ---------------------------------------------------------------- x pass --
+// Lines along x: column index col in [0, N*nhp) enumerates (ky, kz); element
+// (kx, col) sits at kx*N*nhp + col, so a row of TC columns is contiguous.  A
+// persistent block walks column tiles; the staged Phi0 tile serves all
+// outputs, and the next tile is requested as soon as the last output has read
+// the current one into registers.
 template <int N, int TC>
-__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(ArgsX a) {
+__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(const __grid_constant__ ArgsX a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
   using L = XLayoutCols<E, P, TC>;
-  extern __shared__ float4 smem_raw[];
-  float2* s_x = reinterpret_cast<float2*>(smem_raw);
+  using G = Stage<N>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // staged tile [N][TC]; TMA destinations start on a 128-byte boundary
+  float2* s_st = reinterpret_cast<float2*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+  float2* s_x = s_st + N * TC;
   float2* s_tw = s_x + L::kSize;
   float* s_m = reinterpret_cast<float*>(s_tw + E * P);  // [3][N] multipliers
+  __shared__ __align__(8) unsigned long long s_bar;
   __shared__ float2* s_dst[3];
   __shared__ int s_xm[3];
   const int tid = threadIdx.x, c = tid % TC, p = tid / TC;
+  const uint32_t bar = smem_u32(&s_bar);
   for (int i = tid; i < E * P; i += TC * P) s_tw[i] = a.tw[i];
   for (int i = tid; i < 3 * N; i += TC * P) s_m[i] = a.mult[i];
   if (tid < 3) {
     s_dst[tid] = a.dst[tid];
     s_xm[tid] = a.xm[tid];
   }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
   __syncthreads();
   const int ncols = N * a.nhp;
-  const int col = blockIdx.x * TC + c;
-  const bool ok = col < ncols;
-  const float2* src = a.src + (ok ? col : 0) + p * ncols;
-  const int tstride = P * ncols;
+  const int ntiles = (ncols + TC - 1) / TC;  // the last tile may run past ncols (zero-filled)
+  auto issue = [&](int tile) {
+    mbar_expect_tx(bar, N * TC * 8);
+#pragma unroll
+    for (int b = 0; b < G::kBoxes; ++b)
+      tma_load_2d(smem_u32(s_st + b * G::kRows * TC), &a.tm, tile * TC, b * G::kRows, bar);
+  };
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+  uint32_t parity = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (!stage_ready(bar, parity, a.err)) return;
+    parity ^= 1;
+    const int col = tile * TC + c;
+    const bool ok = col < ncols;
 #pragma unroll 1
-  for (int f = 0; f < a.nout; ++f) {
-    const float* mt = s_m + s_xm[f] * N + p;
-    float2 v[E];
+    for (int f = 0; f < a.nout; ++f) {
+      const float* mt = s_m + s_xm[f] * N + p;
+      float2 v[E];
 #pragma unroll
-    for (int t = 0; t < E; ++t) {
-      const float2 x = ok ? __ldg(src + t * tstride) : make_float2(0.f, 0.f);
-      v[t] = cscale(x, mt[P * t]);
-    }
-    fft_line<N, L>(v, p, c, s_x, s_tw);
-    float2* d = s_dst[f] + (ok ? col : 0);
+      for (int t = 0; t < E; ++t) v[t] = cscale(s_st[(p + P * t) * TC + c], mt[P * t]);
+      if (f == a.nout - 1) {
+        __syncthreads();  // the tile has been read by every thread
+        if (tid == 0 && tile + (int)gridDim.x < ntiles) {
+          fence_proxy_async();
+          issue(tile + gridDim.x);
+        }
+      }
+      fft_line<N, L>(v, p, c, s_x, s_tw);
+      float2* d = s_dst[f] + (ok ? col : 0);
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int row = fft_out_index<N>(p, j);
-      if (ok) d[row * ncols] = v[j];
+      for (int j = 0; j < E; ++j)
+        if (ok) d[fft_out_index<N>(p, j) * ncols] = v[j];
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------- y pass --
-// Lines along y: column col in [0, N*nhp) enumerates (x, kz); element
-// (ky, col) sits at (x*N + ky)*nhp + kz.
+// Lines along y: a tile is TC consecutive kz of one x plane; element
+// (ky, kz) of plane x sits at (x*N + ky)*nhp + kz.  Columns past nhp are
+// zero-filled by the tensor map and not stored.
 template <int N, int TC>
-__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(ArgsY a) {
+__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(const __grid_constant__ ArgsY a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
   using L = XLayoutCols<E, P, TC>;
-  extern __shared__ float4 smem_raw[];
-  float2* s_x = reinterpret_cast<float2*>(smem_raw);
+  using G = Stage<N>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* s_st = reinterpret_cast<float2*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+  float2* s_x = s_st + N * TC;
   float2* s_tw = s_x + L::kSize;
-  float* s_m = reinterpret_cast<float*>(s_tw + E * P);  // [3][N] multipliers
+  float* s_m = reinterpret_cast<float*>(s_tw + E * P);
+  __shared__ __align__(8) unsigned long long s_bar;
   __shared__ float2* s_dst[kMaxFields];
-  __shared__ const float2* s_src[kMaxFields];
-  __shared__ int s_ym[kMaxFields], s_zm[kMaxFields], s_mi[kMaxFields];
+  __shared__ int s_sel[kMaxFields], s_ym[kMaxFields], s_zm[kMaxFields], s_mi[kMaxFields];
   const int tid = threadIdx.x, c = tid % TC, p = tid / TC;
+  const uint32_t bar = smem_u32(&s_bar);
   for (int i = tid; i < E * P; i += TC * P) s_tw[i] = a.tw[i];
   for (int i = tid; i < 3 * N; i += TC * P) s_m[i] = a.mult[i];
   if (tid < kMaxFields) {
     s_dst[tid] = a.dst[tid];
-    s_src[tid] = a.src[a.sel[tid] < 3 ? a.sel[tid] : 0];
+    s_sel[tid] = a.sel[tid] < 3 ? a.sel[tid] : 0;
     s_ym[tid] = a.ym[tid];
     s_zm[tid] = a.zm[tid];
     s_mi[tid] = a.muli[tid];
   }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
   __syncthreads();
-  const int nhp = a.nhp;
-  const int ncols = N * nhp;
-  const int col = blockIdx.x * TC + c;
-  const bool ok = col < ncols;
-  const int x = ok ? col / nhp : 0, kz = ok ? col % nhp : 0;
-  const int base = x * N * nhp + kz;
-  const int tstride = P * nhp;
+  const int nhp = a.nhp, nout = a.nout;
+  const int ktiles = (nhp + TC - 1) / TC;
+  const int ntiles = N * ktiles;
+  auto issue = [&](int tile, int src) {
+    const int x = tile / ktiles, kz0 = (tile % ktiles) * TC;
+    mbar_expect_tx(bar, N * TC * 8);
+#pragma unroll
+    for (int b = 0; b < G::kBoxes; ++b)
+      tma_load_4d(smem_u32(s_st + b * G::kRows * TC), &a.tm, kz0, b * G::kRows, x, src, bar);
+  };
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, s_sel[0]);
+  uint32_t parity = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int x = tile / ktiles, kz = (tile % ktiles) * TC + c;
+    const bool ok = kz < nhp;
+    const size_t base = (size_t)x * N * nhp + (ok ? kz : 0);
 #pragma unroll 1
-  for (int f = 0; f < a.nout; ++f) {
-    const float* mt = s_m + s_ym[f] * N + p;
-    const float2* s = s_src[f] + base + p * nhp;
-    float2 v[E];
+    for (int o = 0; o < nout; ++o) {
+      if (o == 0 || s_sel[o] != s_sel[o - 1]) {
+        if (!stage_ready(bar, parity, a.err)) return;
+        parity ^= 1;
+      }
+      const float* mt = s_m + s_ym[o] * N + p;
+      float2 v[E];
 #pragma unroll
-    for (int t = 0; t < E; ++t) {
-      const float2 xv = ok ? __ldg(s + t * tstride) : make_float2(0.f, 0.f);
-      v[t] = cscale(xv, mt[P * t]);
-    }
-    fft_line<N, L>(v, p, c, s_x, s_tw);
-    // z factor of this column (kz < N/2 + 1; pad columns carry zeros anyway)
-    const float zf = (ok && kz <= N / 2) ? s_m[s_zm[f] * N + kz] : 0.f;
-    const bool mi = s_mi[f] != 0;
-    float2* d = s_dst[f] + base;
+      for (int t = 0; t < E; ++t) v[t] = cscale(s_st[(p + P * t) * TC + c], mt[P * t]);
+      const bool last_use = (o == nout - 1) || s_sel[o + 1] != s_sel[o];
+      if (last_use) {
+        __syncthreads();  // the staged source has been read by every thread
+        if (tid == 0) {
+          if (o < nout - 1) {
+            fence_proxy_async();
+            issue(tile, s_sel[o + 1]);
+          } else if (tile + (int)gridDim.x < ntiles) {
+            fence_proxy_async();
+            issue(tile + gridDim.x, s_sel[0]);
+          }
+        }
+      }
+      fft_line<N, L>(v, p, c, s_x, s_tw);
+      // z factor of this column (kz <= N/2; pad columns carry zeros anyway)
+      const float zf = (ok && kz <= N / 2) ? s_m[s_zm[o] * N + kz] : 0.f;
+      const bool mi = s_mi[o] != 0;
+      float2* d = s_dst[o] + base;
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int row = fft_out_index<N>(p, j);
-      float2 o = cscale(v[j], zf);
-      if (mi) o = cmuli(o);
-      if (ok) d[row * nhp] = o;
+      for (int j = 0; j < E; ++j) {
+        float2 w = cscale(v[j], zf);
+        if (mi) w = cmuli(w);
+        if (ok) d[(size_t)fft_out_index<N>(p, j) * nhp] = w;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -147,7 +272,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
   constexpr int NC = 3 * LINES;  // at most three pairs per line
   using L = XLayoutLines<E, P, NC>;
-  extern __shared__ float4 smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* s_x = reinterpret_cast<float2*>(smem_raw);
   constexpr int kXBytes = L::kSize * 8, kFBytes = LINES * 6 * N * 4;
   constexpr int kBufBytes = kXBytes > kFBytes ? kXBytes : kFBytes;
@@ -220,7 +345,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
     constexpr int kPts = LINES * N;
     constexpr int U = PIN_Z_ILP;
     for (int base_pt = tid; base_pt < kPts; base_pt += U * nthreads) {
-      float h[U][6], lam[U][3], F[U], kap[U], rabs[U];
+      float h[U][6], lam[U][3], F[U], kap[U], rabs[U], fm[U];
       int q[U];
       bool valid[U];
 #pragma unroll
@@ -230,6 +355,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
         const int gl = blockIdx.x * LINES + l;
         valid[u] = pt < kPts && gl < nlines;
         q[u] = gl * N + z;
+        fm[u] = valid[u] ? a.fmax[q[u]] : 0.f;  // issued early: its latency hides under the math
 #pragma unroll
         for (int f = 0; f < 6; ++f) h[u][f] = valid[u] ? s_f[(l * 6 + f) * N + z] : 0.f;
       }
@@ -256,8 +382,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
           }
           atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
         }
-        const float fm = a.fmax[q[u]];
-        if (F[u] > fm) {
+        if (F[u] > fm[u]) {
           a.fmax[q[u]] = F[u];
           a.idx[q[u]] = a.scale;
         }
@@ -297,7 +422,9 @@ template <int N> struct Cfg {
   static constexpr int E = Shape<N>::E, P = Shape<N>::P;
   static constexpr int TC = P >= 8 ? 16 : (P == 4 ? 32 : 64);
   static constexpr int LINES = 64 / P;
-  static constexpr size_t smem_xy = (size_t)XLayoutCols<E, P, TC>::kSize * 8 + (size_t)E * P * 8 + (size_t)3 * N * 4;
+  // staged tile + exchange + twiddles + multipliers + alignment slack
+  static constexpr size_t smem_xy = (size_t)N * TC * 8 + (size_t)XLayoutCols<E, P, TC>::kSize * 8 +
+                                    (size_t)E * P * 8 + (size_t)3 * N * 4 + 128;
   static constexpr size_t xz = (size_t)XLayoutLines<E, P, 3 * LINES>::kSize * 8;
   static constexpr size_t fz = (size_t)LINES * 6 * N * 4;
   static constexpr size_t smem_z = (xz > fz ? xz : fz) + (size_t)E * P * 8;
@@ -324,11 +451,23 @@ static PassShape shape_of() {
   return PassShape{C::E, C::P, C::TC, C::LINES, C::smem_xy, C::smem_z, C::threads_xy, C::threads_z};
 }
 
+// Persistent grid: as many blocks as fit on the device at once, at most one
+// per tile.
+template <class K>
+static unsigned persistent_grid(K kernel, int threads, size_t smem, long ntiles) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  long g = (long)std::max(1, sms) * std::max(1, per_sm);
+  return (unsigned)std::min<long>(g, std::max<long>(1, ntiles));
+}
+
 template <int N>
 static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
   using C = Cfg<N>;
-  const long ncols = (long)N * a.nhp;
-  const unsigned grid = (unsigned)((ncols + C::TC - 1) / C::TC);
+  const long ntiles = ((long)N * a.nhp + C::TC - 1) / C::TC;
+  const unsigned grid = persistent_grid(k_pass_x<N, C::TC>, C::threads_xy, C::smem_xy, ntiles);
   k_pass_x<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
   return cudaGetLastError();
 }
@@ -336,8 +475,8 @@ static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
 template <int N>
 static cudaError_t run_y(const ArgsY& a, cudaStream_t st) {
   using C = Cfg<N>;
-  const long ncols = (long)N * a.nhp;
-  const unsigned grid = (unsigned)((ncols + C::TC - 1) / C::TC);
+  const long ntiles = (long)N * ((a.nhp + C::TC - 1) / C::TC);
+  const unsigned grid = persistent_grid(k_pass_y<N, C::TC>, C::threads_xy, C::smem_xy, ntiles);
   k_pass_y<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
   return cudaGetLastError();
 }
@@ -406,6 +545,58 @@ cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st) {
 #undef CASE
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ------------------------------------------------------------ tensor maps --
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  });
+  return fn;
+}
+
+// Complex64 elements are moved as 8-byte integers (no conversion; zero fill
+// outside the tensor).
+static cudaError_t encode(CUtensorMap* tm, int rank, const void* base, const cuuint64_t* dims,
+                          const cuuint64_t* strides, const cuuint32_t* box) {
+  EncodeTiledFn fn = tensor_map_encoder();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_INT64, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int n, int nhp) {
+  const PassShape sh = pass_shape(n);
+  const int boxes = (n + 255) / 256;
+  const cuuint64_t dims[2] = {(cuuint64_t)n * nhp, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)n * nhp * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)sh.tc, (cuuint32_t)(n / boxes)};
+  return encode(tm, 2, src, dims, strides, box);
+}
+
+cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int n, int nhp, size_t spec_elems) {
+  const PassShape sh = pass_shape(n);
+  const int boxes = (n + 255) / 256;
+  const cuuint64_t dims[4] = {(cuuint64_t)nhp, (cuuint64_t)n, (cuuint64_t)n, 3};
+  const cuuint64_t strides[3] = {(cuuint64_t)nhp * 8, (cuuint64_t)n * nhp * 8, (cuuint64_t)spec_elems * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)sh.tc, (cuuint32_t)(n / boxes), 1, 1};
+  return encode(tm, 4, src3, dims, strides, box);
 }
 
 cudaError_t upload_constant_twiddles() {

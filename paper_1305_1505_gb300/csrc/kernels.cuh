@@ -10,6 +10,7 @@
 // for the odd multipliers), so the x pass needs three transforms and only the
 // y and z passes carry all six components.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the encoder itself is fetched from the driver at run time)
 #include <cstddef>
 #include <cuda_runtime.h>
 
@@ -17,8 +18,11 @@ namespace pin {
 
 constexpr int kMaxFields = 6;
 
-// x pass: for each output f, dst[f] = IDFT_x(mult[xm[f]] * src).
+// x pass: for each output f, dst[f] = IDFT_x(mult[xm[f]] * src).  The source
+// tiles arrive by TMA: tm is a 2D map over src, {N*nhp columns, N rows}, box
+// {tc, rows/boxes}.
 struct ArgsX {
+  CUtensorMap tm;
   const float2* src;
   float2* dst[3];
   int xm[3];
@@ -26,11 +30,16 @@ struct ArgsX {
   const float* mult;  // [3][N] multipliers of this radius (W, kW, k^2W, each / N)
   const float2* tw;   // level-2 twiddles [E][P]
   int nhp;
+  int* err;           // set to 1 if a TMA wait gave up (bounded wait)
 };
 
 // y pass: dst[f] = zfac[f](kz) * IDFT_y(mult[ym[f]] * src[sel[f]]), where the
 // z factor mult[zm[f]](kz), times i when muli[f], is constant along a y line.
+// Outputs are processed in the given order; consecutive outputs with the same
+// source share one staged tile.  tm is a 4D map over the three source spectra
+// (stored back to back), {nhp, N, N, 3}, box {tc, rows/boxes, 1, 1}.
 struct ArgsY {
+  CUtensorMap tm;
   const float2* src[3];
   float2* dst[kMaxFields];
   int sel[kMaxFields];
@@ -41,6 +50,7 @@ struct ArgsY {
   const float* mult;
   const float2* tw;
   int nhp;
+  int* err;
 };
 
 // A particle whose FP32 collapse is ill-conditioned (near-degenerate
@@ -84,6 +94,12 @@ struct PassShape {
   size_t smem_z;
   int threads_xy, threads_z;
 };
+
+// Tensor maps of the x and y passes (host; the encoder comes from the driver
+// entry point, so no driver library is linked).  spec_elems is the stride
+// between the spectra the y map spans.
+cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int n, int nhp);
+cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int n, int nhp, size_t spec_elems);
 
 bool size_supported(int n);
 PassShape pass_shape(int n);

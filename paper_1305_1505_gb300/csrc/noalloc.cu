@@ -40,7 +40,8 @@ constexpr size_t kOffTw = kOffMult + kMultBytes;
 constexpr size_t kRedoCap = (size_t)kMaxN * kMaxN * kMaxN / 64;
 constexpr size_t kOffCnt = kOffTw + kTwBytes;
 constexpr size_t kOffRedoCount = kOffCnt + 4 * sizeof(unsigned long long);
-constexpr size_t kOffRedo = (kOffRedoCount + sizeof(unsigned) + 255) & ~(size_t)255;
+constexpr size_t kOffErr = kOffRedoCount + 16;  // cleared with the counters
+constexpr size_t kOffRedo = (kOffErr + sizeof(int) + 255) & ~(size_t)255;
 constexpr size_t kScratchBytes = (kOffRedo + kRedoCap * sizeof(pin::RedoEntry) + 255) & ~(size_t)255;
 
 // The whole workspace of this entry point (about 11.3 MB for N <= 64).  In host
@@ -175,6 +176,11 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
   float2* tw = reinterpret_cast<float2*>(base + kOffTw);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + kOffCnt);
   unsigned* redo_count = reinterpret_cast<unsigned*>(base + kOffRedoCount);
+  int* err = reinterpret_cast<int*>(base + kOffErr);
+  CUtensorMap tm_x, tm_y;
+  if (pin::make_tmap_x(&tm_x, phi0, n, nhp) != cudaSuccess ||
+      pin::make_tmap_y(&tm_y, U, n, nhp, spec) != cudaSuccess)
+    return PIN_ECUDA;
   pin::RedoEntry* redo_list = reinterpret_cast<pin::RedoEntry*>(base + kOffRedo);
   const double dcorr = noalloc_dcorr();
   const size_t n3 = (size_t)n * n * n;
@@ -184,36 +190,41 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
   k_noalloc_tables<<<tblocks, tthreads, 0, cs>>>(rr, nscales, n, box, sh.E, sh.P, mult, tw);
   k_noalloc_phi0<<<(unsigned)((spec + 255) / 256), 256, 0, cs>>>(delta_k, dtype, n, nhp, box, phi0);
   if (cudaGetLastError() != cudaSuccess) return PIN_ECUDA;
-  if (cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), cs) != cudaSuccess ||
+  if (cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long) + 32, cs) != cudaSuccess ||
       cudaMemsetAsync(F_max, 0, n3 * sizeof(float), cs) != cudaSuccess ||
       cudaMemsetAsync(scale_idx, 0xFF, n3 * sizeof(int32_t), cs) != cudaSuccess)
     return PIN_ECUDA;
 
-  static const int sel[6] = {2, 0, 0, 1, 1, 0};
-  static const int ym[6] = {0, 2, 0, 1, 0, 1};
-  static const int zm[6] = {0, 0, 2, 0, 1, 1};
+  static const int vout[6] = {0, 3, 4, 1, 2, 5};
+  static const int sel[6] = {2, 1, 1, 0, 0, 0};
+  static const int ym[6] = {0, 1, 0, 2, 0, 1};
+  static const int zm[6] = {0, 0, 1, 0, 2, 1};
   for (int s = 0; s < nscales; ++s) {
     const float* m = mult + (size_t)s * 3 * n;
     pin::ArgsX ax{};
+    ax.tm = tm_x;
     ax.src = phi0;
     for (int f = 0; f < 3; ++f) { ax.dst[f] = U + f * spec; ax.xm[f] = f; }
     ax.nout = 3;
     ax.mult = m;
     ax.tw = tw;
     ax.nhp = nhp;
+    ax.err = err;
     pin::ArgsY ay{};
+    ay.tm = tm_y;
     for (int f = 0; f < 3; ++f) ay.src[f] = U + f * spec;
-    for (int f = 0; f < 6; ++f) {
-      ay.dst[f] = V + f * spec;
-      ay.sel[f] = sel[f];
-      ay.ym[f] = ym[f];
-      ay.zm[f] = zm[f];
-      ay.muli[f] = 0;
+    for (int o = 0; o < 6; ++o) {
+      ay.dst[o] = V + vout[o] * spec;
+      ay.sel[o] = sel[o];
+      ay.ym[o] = ym[o];
+      ay.zm[o] = zm[o];
+      ay.muli[o] = 0;
     }
     ay.nout = 6;
     ay.mult = m;
     ay.tw = tw;
     ay.nhp = nhp;
+    ay.err = err;
     pin::ArgsZ az{};
     for (int f = 0; f < 6; ++f) az.src[f] = V + f * spec;
     az.nfields = 6;

@@ -43,6 +43,8 @@ struct pin_plan_s {
   RedoEntry* redo_list = nullptr;          // FP64 redo queue, reused by every radius
   unsigned* redo_count = nullptr;
   unsigned redo_cap = 0;
+  int* err = nullptr;                      // set by a pass whose bounded TMA wait gave up
+  CUtensorMap tm_x{}, tm_y{};              // Phi0 -> x pass, U[3] -> y pass
   bool ic_set = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -122,7 +124,7 @@ size_t footprint(int n, int nscales) {
   const size_t spec = (size_t)n * n * padded_half(n);
   const size_t n3 = (size_t)n * n * n;
   return spec * 8 * 10 + n3 * 8 + (size_t)(nscales + 1) * 3 * n * 4 + (size_t)n * 8 + 64 +
-         (size_t)redo_capacity(n) * sizeof(RedoEntry) + 16;
+         (size_t)redo_capacity(n) * sizeof(RedoEntry) + 16 + sizeof(int);
 }
 
 // Per-axis multipliers for one radius: {W, k W, k^2 W} / n with
@@ -202,6 +204,7 @@ void release(pin_plan_t p) {
   cudaFree(p->counters);
   cudaFree(p->redo_list);
   cudaFree(p->redo_count);
+  cudaFree(p->err);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   p->events.clear();
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -218,32 +221,39 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   const bool rec = p->profile && dump == nullptr && !p->events.empty();
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 0], p->stream, cudaEventRecordExternal));
   ArgsX ax{};
+  ax.tm = p->tm_x;
   ax.src = p->phi0;
   for (int f = 0; f < 3; ++f) { ax.dst[f] = spec(p, p->U, f); ax.xm[f] = f; }
   ax.nout = 3;
   ax.mult = mult;
   ax.tw = p->tw;
   ax.nhp = p->nhp;
+  ax.err = p->err;
   PIN_CK(p, launch_x(p->n, ax, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 1], p->stream, cudaEventRecordExternal));
 
-  // y pass: xx <- U2, yy <- U0 (k_y^2), zz <- U0, xy <- U1 (k_y), xz <- U1, yz <- U0 (k_y)
-  static const int sel[6] = {2, 0, 0, 1, 1, 0};
-  static const int ym[6] = {0, 2, 0, 1, 0, 1};
-  static const int zm[6] = {0, 0, 2, 0, 1, 1};
+  // y pass, outputs grouped by source so that each staged tile serves them in
+  // a row: V[xx] <- U2; V[xy] <- U1 (k_y), V[xz] <- U1 (z: k_z);
+  // V[yy] <- U0 (k_y^2), V[zz] <- U0 (z: k_z^2), V[yz] <- U0 (k_y; z: k_z)
+  static const int vout[6] = {0, 3, 4, 1, 2, 5};
+  static const int sel[6] = {2, 1, 1, 0, 0, 0};
+  static const int ym[6] = {0, 1, 0, 2, 0, 1};
+  static const int zm[6] = {0, 0, 1, 0, 2, 1};
   ArgsY ay{};
+  ay.tm = p->tm_y;
   for (int f = 0; f < 3; ++f) ay.src[f] = spec(p, p->U, f);
-  for (int f = 0; f < 6; ++f) {
-    ay.dst[f] = spec(p, p->V, f);
-    ay.sel[f] = sel[f];
-    ay.ym[f] = ym[f];
-    ay.zm[f] = zm[f];
-    ay.muli[f] = 0;
+  for (int o = 0; o < 6; ++o) {
+    ay.dst[o] = spec(p, p->V, vout[o]);
+    ay.sel[o] = sel[o];
+    ay.ym[o] = ym[o];
+    ay.zm[o] = zm[o];
+    ay.muli[o] = 0;
   }
   ay.nout = 6;
   ay.mult = mult;
   ay.tw = p->tw;
   ay.nhp = p->nhp;
+  ay.err = p->err;
   PIN_CK(p, launch_y(p->n, ay, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 2], p->stream, cudaEventRecordExternal));
 
@@ -313,9 +323,18 @@ pin_status check_plan(pin_plan_t p) {
   return PIN_OK;
 }
 
+// After the plan's stream has drained: a pass that gave up a bounded wait
+// left its error word set.
+pin_status check_error_word(pin_plan_t p) {
+  int err = 0;
+  PIN_CK(p, cudaMemcpy(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) return fail(p, PIN_ECUDA, "a transfer wait in the x/y pass timed out; results are invalid");
+  return PIN_OK;
+}
+
 pin_status finish_host(pin_plan_t p) {
   PIN_CK(p, cudaStreamSynchronize(p->stream));
-  return PIN_OK;
+  return check_error_word(p);
 }
 
 }  // namespace
@@ -369,7 +388,8 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
       cudaMalloc(&p->tw, (size_t)p->n * 8) != cudaSuccess ||
       cudaMalloc(&p->counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&p->redo_list, (size_t)redo_capacity(p->n) * sizeof(RedoEntry)) != cudaSuccess ||
-      cudaMalloc(&p->redo_count, sizeof(unsigned)) != cudaSuccess) {
+      cudaMalloc(&p->redo_count, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return bail(PIN_ENOMEM);
   }
@@ -386,7 +406,11 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
     }
   if (cudaMemcpy(p->mult, mult.data(), mult_elems * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(p->counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess)
+      cudaMemset(p->counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess)
+    return bail(PIN_ECUDA);
+  if (make_tmap_x(&p->tm_x, p->phi0, p->n, p->nhp) != cudaSuccess ||
+      make_tmap_y(&p->tm_y, p->U, p->n, p->nhp, p->spec_elems) != cudaSuccess)
     return bail(PIN_ECUDA);
   *out = p;
   return PIN_OK;
@@ -465,6 +489,7 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   if (!on_device) PIN_CK(p, cudaMallocAsync((void**)&dev, 3 * n3 * 4, p->stream));
   const float* mult = p->mult + (size_t)p->nscales * 3 * p->n;  // R = 0: no smoothing
   ArgsX ax{};
+  ax.tm = p->tm_x;
   ax.src = p->phi0;
   ax.dst[0] = spec(p, p->U, 0);
   ax.dst[1] = spec(p, p->U, 1);
@@ -474,11 +499,14 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   ax.mult = mult;
   ax.tw = p->tw;
   ax.nhp = p->nhp;
+  ax.err = p->err;
   cudaError_t e = launch_x(p->n, ax, p->stream);
-  // psi_x <- U1, psi_y <- U0 (k_y), psi_z <- U0; z: psi_z gets k_z; all times i
+  // psi_x <- U1, psi_y <- U0 (k_y), psi_z <- U0 (z: k_z); all times i
   ArgsY ay{};
+  ay.tm = p->tm_y;
   ay.src[0] = spec(p, p->U, 0);
   ay.src[1] = spec(p, p->U, 1);
+  ay.src[2] = spec(p, p->U, 2);
   const int sel[3] = {1, 0, 0}, ym[3] = {0, 1, 0}, zm[3] = {0, 0, 1};
   for (int f = 0; f < 3; ++f) {
     ay.dst[f] = spec(p, p->V, f);
@@ -491,6 +519,7 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   ay.mult = mult;
   ay.tw = p->tw;
   ay.nhp = p->nhp;
+  ay.err = p->err;
   if (e == cudaSuccess) e = launch_y(p->n, ay, p->stream);
   ArgsZ az{};
   for (int f = 0; f < 3; ++f) {
@@ -519,7 +548,7 @@ pin_status pin_sync(pin_plan_t p, int64_t timeout_ns) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     cudaError_t e = cudaStreamQuery(p->stream);
-    if (e == cudaSuccess) return PIN_OK;
+    if (e == cudaSuccess) return check_error_word(p);
     if (e != cudaErrorNotReady) return cuda_fail(p, e, "cudaStreamQuery");
     if (timeout_ns >= 0) {
       const auto dt = std::chrono::duration_cast<std::chrono::nanoseconds>(
