@@ -42,7 +42,14 @@ namespace pin {
 // standing in for the hardware approximations.
 template <typename T> struct M;
 template <> struct M<float> {
-  __host__ __device__ __forceinline__ static float sqrt_(float x) { return sqrtf(x); }
+  // x * rsqrt(x): two instructions, ~2 ulp, no special-case branches (x >= 0)
+  __host__ __device__ __forceinline__ static float sqrt_(float x) {
+#ifdef __CUDA_ARCH__
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+#else
+    return std::sqrt(x);
+#endif
+  }
   __host__ __device__ __forceinline__ static float div_(float a, float b) {
 #ifdef __CUDA_ARCH__
     return __fdividef(a, b);
@@ -60,7 +67,7 @@ template <> struct M<float> {
     poly = fmaf(poly, ax, 0.0889789874f);
     poly = fmaf(poly, ax, -0.2145988016f);
     poly = fmaf(poly, ax, 1.5707963050f);
-    const float r = sqrtf(1.0f - ax) * poly;
+    const float r = sqrt_(1.0f - ax) * poly;
     return x < 0.0f ? 3.14159265358979f - r : r;
   }
   __host__ __device__ __forceinline__ static void sincos_(float x, float* sn, float* cs) {
@@ -83,6 +90,21 @@ template <> struct M<float> {
     return __expf(x);
 #else
     return std::exp(x);
+#endif
+  }
+  // approximate sqrt / cbrt of x >= 0 (relative error ~1e-7 / ~1e-6): bounds only
+  __host__ __device__ __forceinline__ static float sqrt_approx(float x) {
+#ifdef __CUDA_ARCH__
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+#else
+    return x > 0.0f ? std::sqrt(x) : 0.0f;
+#endif
+  }
+  __host__ __device__ __forceinline__ static float cbrt_approx(float x) {
+#ifdef __CUDA_ARCH__
+    return x > 0.0f ? exp2f(__log2f(x) * (1.0f / 3.0f)) : 0.0f;
+#else
+    return x > 0.0f ? std::cbrt(x) : 0.0f;
 #endif
   }
   __host__ __device__ __forceinline__ static float cbrt_(float x) {
@@ -108,6 +130,8 @@ template <> struct M<double> {
   __host__ __device__ __forceinline__ static double cos_(double x) { return cos(x); }
   __host__ __device__ __forceinline__ static double exp_(double x) { return exp(x); }
   __host__ __device__ __forceinline__ static double cbrt_(double x) { return cbrt(x); }
+  __host__ __device__ __forceinline__ static double sqrt_approx(double x) { return x > 0.0 ? sqrt(x) : 0.0; }
+  __host__ __device__ __forceinline__ static double cbrt_approx(double x) { return x > 0.0 ? cbrt(x) : 0.0; }
 };
 
 // Closed-form eigenvalues of the symmetric 3x3 matrix
@@ -123,15 +147,14 @@ __host__ __device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
   const T b0 = h[0] - q, b1 = h[1] - q, b2 = h[2] - q;
   const T off = h[3] * h[3] + h[4] * h[4] + h[5] * h[5];
   const T p2 = b0 * b0 + b1 * b1 + b2 * b2 + T(2) * off;
-  if (!(p2 > T(0))) {
-    lam[0] = lam[1] = lam[2] = q;
-    return T(1);
-  }
-  const T p = F::sqrt_(p2 * (T(1) / T(6)));
+  // p2 == 0 (a multiple of the identity) gives p = 0 and three equal values
+  // through the same formulas, with r forced to 1 (flagged, redone in FP64)
+  const bool iso = !(p2 > T(0));
+  const T p = F::sqrt_(iso ? T(0) : p2 * (T(1) / T(6)));
   // det(A - qI)
   const T det = b0 * (b1 * b2 - h[5] * h[5]) - h[3] * (h[3] * b2 - h[5] * h[4]) +
                 h[4] * (h[3] * h[5] - b1 * h[4]);
-  T r = F::div_(det, T(2) * p * p * p);
+  T r = iso ? T(1) : F::div_(det, T(2) * p * p * p);
   r = r > T(1) ? T(1) : (r < T(-1) ? T(-1) : r);
   const T phi = F::acos_(r) * third;
   T sn, cs;
@@ -145,11 +168,66 @@ __host__ __device__ __forceinline__ T eig3(const T h[6], T lam[3]) {
   return r < T(0) ? -r : r;
 }
 
-// Largest real root of g(F) = F^3 - c1 F^2 - c2 F - c3, clamped at 0 from
-// below (no positive root: the axis never collapses).  kappa receives
-// |g'(F)| / (3F^2 + 2|c1|F + |c2|), small near a tangent crossing.
+// Conditioning of a root x of g: |g'(x)| / (3x^2 + 2|c1|x + |c2|), small near
+// a tangent crossing.
 template <typename T>
-__host__ __device__ __forceinline__ T largest_root(T c1, T c2, T c3, T& kappa) {
+__host__ __device__ __forceinline__ T root_kappa(T c1, T c2, T x) {
+  using F = M<T>;
+  const T dg = (T(3) * x - T(2) * c1) * x - c2;
+  const T ac1 = c1 < T(0) ? -c1 : c1, ac2 = c2 < T(0) ? -c2 : c2, ax = x < T(0) ? -x : x;
+  const T scale = T(3) * x * x + T(2) * ac1 * ax + ac2;
+  return scale > T(0) ? F::div_(dg < T(0) ? -dg : dg, scale) : T(1);
+}
+
+// Largest real root of g(F) = F^3 - c1 F^2 - c2 F - c3, clamped at 0 from
+// below (no positive root: the axis never collapses), without branches on the
+// root structure: Halley's iteration from a point on the monotone side of the
+// root.  With the depressed form t^3 + p t + q (F = t + c1/3):
+//  - if there are three real roots, or q <= 0, the largest root lies right of
+//    the inflection point c1/3, where g is convex and increasing; start at
+//    U = c1/3 + sqrt(max(-p,0)) + cbrt(max(-q,0)), an upper bound (for
+//    t >= a + b with a^2 >= -p, b^3 >= -q: t^3 + p t + q >= t(t^2 - a^2) - b^3
+//    >= 2a^2 b + 3a b^2 >= 0);
+//  - otherwise the single real root lies left of it, in the concave increasing
+//    region; it is positive only if g(0) = -c3 < 0, and the iteration starts at 0.
+// Four iterations reach ~1e-6 relative in FP32 on the coefficient ranges of
+// smoothed Gaussian fields; near-tangent roots are flagged by kappa and redone.
+template <typename T>
+__host__ __device__ __forceinline__ T largest_root_iter(T c1, T c2, T c3, T& kappa) {
+  using F = M<T>;
+  const T third = T(1) / T(3);
+  const T s = c1 * third;
+  const T p = -c2 - c1 * s;
+  const T q = -c3 - c2 * s - T(2) * s * s * s;
+  const T hq = q * T(0.5), tp = p * third;
+  const T disc = hq * hq + tp * tp * tp;
+  const bool right = disc <= T(0) || q <= T(0);
+  const T up = s + F::sqrt_approx(-p) + F::cbrt_approx(-q);
+  const bool none = !right && c3 <= T(0);  // single root, and it is not positive
+  T x = right ? up : T(0);
+  T step = T(0);
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const T g = ((x - c1) * x - c2) * x - c3;
+    const T dg = (T(3) * x - T(2) * c1) * x - c2;
+    const T d2 = T(6) * x - T(2) * c1;
+    const T den = T(2) * dg * dg - g * d2;
+    step = den != T(0) ? F::div_(T(2) * g * dg, den != T(0) ? den : T(1)) : T(0);
+    x = x - step;
+  }
+  kappa = root_kappa<T>(c1, c2, x);
+  // not converged after four steps: hand the particle to the FP64 redo
+  const T ax = x < T(0) ? -x : x, as = step < T(0) ? -step : step;
+  kappa = (as > T(2e-6) * ax + T(1e-12)) ? T(0) : kappa;
+  kappa = none ? T(1) : kappa;
+  return (none || !(x > T(0))) ? T(0) : x;
+}
+
+// Same root by the closed form (Cardano / trigonometric) with two Newton
+// polishing steps; used in FP64, where the accurate library functions make it
+// exact to rounding.
+template <typename T>
+__host__ __device__ __forceinline__ T largest_root_closed(T c1, T c2, T c3, T& kappa) {
   using F = M<T>;
   const T third = T(1) / T(3);
   const T s = c1 * third;
@@ -179,11 +257,14 @@ __host__ __device__ __forceinline__ T largest_root(T c1, T c2, T c3, T& kappa) {
     const T dg = (T(3) * x - T(2) * c1) * x - c2;
     if (dg != T(0)) x = x - F::div_(g, dg);
   }
-  const T dg = (T(3) * x - T(2) * c1) * x - c2;
-  const T ac1 = c1 < T(0) ? -c1 : c1, ac2 = c2 < T(0) ? -c2 : c2, ax = x < T(0) ? -x : x;
-  const T scale = T(3) * x * x + T(2) * ac1 * ax + ac2;
-  kappa = scale > T(0) ? F::div_(dg < T(0) ? -dg : dg, scale) : T(1);
+  kappa = root_kappa<T>(c1, c2, x);
   return x > T(0) ? x : T(0);
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ T largest_root(T c1, T c2, T c3, T& kappa) {
+  if constexpr (sizeof(T) == 4) return largest_root_iter<T>(c1, c2, c3, kappa);
+  else return largest_root_closed<T>(c1, c2, c3, kappa);
 }
 
 template <typename T>
@@ -204,9 +285,66 @@ __host__ __device__ __forceinline__ bool no_root_from(T c1, T c2, T c3, T t) {
   if (!(gt > T(0))) return false;
   const T d = c1 * c1 + T(3) * c2;
   if (d < T(0)) return true;
-  const T fs = (c1 + F::sqrt_(d)) * (T(1) / T(3));
+  const T fs = (c1 + F::sqrt_approx(d)) * (T(1) / T(3));
   if (fs <= t) return true;
   return ((fs - c1) * fs - c2) * fs - c3 > T(0);
+}
+
+// Coefficients (c1, c2, c3) of a_i(D) = c1 D + c2 D^2 + c3 D^3 for axis i.
+template <typename T>
+__host__ __device__ __forceinline__ void axis_coeffs(const T lam[3], const T e[3], T mu3, int i, T c[3]) {
+  const int j = (i + 1) % 3, k = (i + 2) % 3;
+  c[0] = lam[i];
+  c[1] = T(3) / T(7) * e[i];
+  c[2] = T(10) / T(84) * (lam[i] * (e[j] + e[k]) + e[i] * (lam[j] + lam[k])) - mu3 * (T(1) / T(9));
+}
+
+// Per-particle state between the two parts of the collapse computation.
+template <typename T>
+struct CollapseState {
+  T best, kappa, corr;
+  T c[2][3];     // coefficients of the two smaller-eigenvalue axes
+  bool need[2];  // those axes may collapse first and must be solved
+};
+
+// Common part, free of branches on the data so that independent particles
+// interleave: the axis of the largest eigenvalue, the exact test for the other
+// two (no_root_from at its root), and the quasi-spherical correction term.
+template <typename T>
+__host__ __device__ __forceinline__ void collapse_main(const T lam[3], const CollapseConsts<T>& cc,
+                                                       CollapseState<T>& st) {
+  using F = M<T>;
+  const T mu1 = lam[0] + lam[1] + lam[2];
+  const T mu3 = lam[0] * lam[1] * lam[2];
+  T e[3];
+  e[0] = T(0.5) * lam[0] * (lam[1] + lam[2]);
+  e[1] = T(0.5) * lam[1] * (lam[0] + lam[2]);
+  e[2] = T(0.5) * lam[2] * (lam[0] + lam[1]);
+  T c0[3];
+  axis_coeffs<T>(lam, e, mu3, 0, c0);
+  axis_coeffs<T>(lam, e, mu3, 1, st.c[0]);
+  axis_coeffs<T>(lam, e, mu3, 2, st.c[1]);
+  st.best = largest_root<T>(c0[0], c0[1], c0[2], st.kappa);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) st.need[a] = !no_root_from<T>(st.c[a][0], st.c[a][1], st.c[a][2], st.best);
+  const T z = F::div_(T(10) * (lam[0] - lam[2]), mu1 > T(0) ? mu1 : T(1));  // eps / 0.1
+  const T w = F::exp_(-z * z);
+  st.corr = (cc.correction && mu1 > T(0)) ? mu1 * cc.dcorr * w : T(0);
+}
+
+// Rare part: solve the smaller-eigenvalue axes that may collapse first.
+template <typename T>
+__host__ __device__ __forceinline__ void collapse_rare(CollapseState<T>& st) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    if (!st.need[a]) continue;
+    T kap;
+    const T Fi = largest_root<T>(st.c[a][0], st.c[a][1], st.c[a][2], kap);
+    if (Fi > st.best) {
+      st.best = Fi;
+      st.kappa = kap;
+    }
+  }
 }
 
 // F for sorted eigenvalues lam; kappa_min receives the conditioning of the
@@ -216,35 +354,11 @@ __host__ __device__ __forceinline__ bool no_root_from(T c1, T c2, T c3, T t) {
 template <typename T>
 __host__ __device__ __forceinline__ T collapse_from_eigs(const T lam[3], const CollapseConsts<T>& cc,
                                                          T& kappa_min) {
-  using F = M<T>;
-  const T mu1 = lam[0] + lam[1] + lam[2];
-  const T mu3 = lam[0] * lam[1] * lam[2];
-  T e[3];
-  e[0] = T(0.5) * lam[0] * (lam[1] + lam[2]);
-  e[1] = T(0.5) * lam[1] * (lam[0] + lam[2]);
-  e[2] = T(0.5) * lam[2] * (lam[0] + lam[1]);
-  T best = T(0);
-  kappa_min = T(1);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const int j = (i + 1) % 3, k = (i + 2) % 3;
-    const T c1 = lam[i];
-    const T c2 = T(3) / T(7) * e[i];
-    const T c3 = T(10) / T(84) * (lam[i] * (e[j] + e[k]) + e[i] * (lam[j] + lam[k])) -
-                 mu3 * (T(1) / T(9));
-    if (i > 0 && no_root_from<T>(c1, c2, c3, best)) continue;
-    T kap;
-    const T Fi = largest_root<T>(c1, c2, c3, kap);
-    if (Fi > best) {
-      best = Fi;
-      kappa_min = kap;
-    }
-  }
-  if (cc.correction && mu1 > T(0)) {
-    const T z = F::div_(T(10) * (lam[0] - lam[2]), mu1);  // eps / 0.1
-    best += mu1 * cc.dcorr * F::exp_(-z * z);
-  }
-  return best;
+  CollapseState<T> st;
+  collapse_main<T>(lam, cc, st);
+  if (st.need[0] || st.need[1]) collapse_rare<T>(st);
+  kappa_min = st.kappa;
+  return st.best + st.corr;
 }
 
 }  // namespace pin

@@ -361,8 +361,17 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) rabs[u] = eig3<float>(h[u], lam[u]);
+      CollapseState<float> cs[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) F[u] = collapse_from_eigs<float>(lam[u], ccf, kap[u]);
+      for (int u = 0; u < U; ++u) collapse_main<float>(lam[u], ccf, cs[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (cs[u].need[0] || cs[u].need[1]) collapse_rare<float>(cs[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        F[u] = cs[u].best + cs[u].corr;
+        kap[u] = cs[u].kappa;
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (!valid[u]) continue;
