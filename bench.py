@@ -103,6 +103,22 @@ def _dist():
     return ws, rank, local
 
 
+def replica_value(local_s, units_per_rank, world_size, device=None):
+    """Replicas: the slowest rank's time and all ranks' units over it.
+
+    Each rank processes its own realisation (no data exchange); the only
+    collective is this max over ranks of the timed duration.  Returns
+    (max_seconds, units_per_second_whole_job)."""
+    import torch
+    import torch.distributed as dist
+    t = local_s
+    if world_size > 1:
+        x = torch.tensor([float(local_s)], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, units_per_rank * world_size / t
+
+
 def cpu_baseline(nscales_total):
     """FP64 oracle, as it stands, on the bounded sample; updates/s and cores."""
     import oracle
@@ -205,13 +221,9 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    total_ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms = total_ms / args.steps
     updates = n ** 3 * S
+    total_s, _ = replica_value(ev0.elapsed_time(ev1) / 1e3, updates * args.steps, ws, "cuda")
+    ms = total_s * 1e3 / args.steps
     value = updates * ws / (ms / 1e3)
 
     # end to end through the public API with host buffers: pinned delta(k) in,
@@ -232,10 +244,8 @@ def run_ours(args):
             pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     barrier()
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    if not args.no_e2e:
+        e2e_s, _ = replica_value(e2e_s, updates, ws, "cuda")
     stats = plan.stats()
 
     # roofline of the dominant pass (algorithmic bytes per launch, one launch per radius)
