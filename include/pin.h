@@ -65,6 +65,11 @@ typedef struct {
   int precision;         /* PIN_FP32_FALLBACK64: FP32 FFTs and collapse, FP64 redo of
                             near-degenerate eigenvalues and near-tangent roots */
   void* stream;          /* cudaStream_t to run on, or NULL for a plan-owned stream */
+  int batch;             /* number of realisations B processed together (0 or 1: one);
+                            they share N, box, radii and correction.  Inputs and outputs
+                            are then B consecutive copies of the single-realisation
+                            layout; one launch per pass covers all of them.  B * N^3 must
+                            stay below 2^31.  pin_hessian and pin_displacements need B = 1. */
 } pin_plan_desc;
 
 /* Runtime counters of a plan (cumulative over its pin_collapse_times calls). */
@@ -85,7 +90,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d);
 size_t pin_footprint_bytes(const pin_plan_desc* d);
 
 /* Loads the linear density field delta(k) (Sec. 2.1.1, Eq. "deltal"), a
- * half-spectrum as described above, dtype PIN_C64 (interleaved float) or
+ * half-spectrum as described above (B of them back to back for a batch), dtype PIN_C64 (interleaved float) or
  * PIN_C128 (interleaved double, rounded to FP32 on the device), from host
  * memory (on_device = 0) or device memory (on_device = 1).  The data are
  * copied; the caller may reuse its buffer when the call returns (host input)

@@ -138,20 +138,23 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(co
   }
   __syncthreads();
   const int ncols = N * a.nhp;
-  const int ntiles = (ncols + TC - 1) / TC;  // the last tile may run past ncols (zero-filled)
+  const int tpr = (ncols + TC - 1) / TC;  // tiles per realisation; the last may run past ncols
+  const int ntiles = tpr * a.batch;        // realisation r owns rows [r N, r N + N)
   auto issue = [&](int tile) {
+    const int r = tile / tpr, t = tile % tpr;
     mbar_expect_tx(bar, N * TC * 8);
 #pragma unroll
     for (int b = 0; b < G::kBoxes; ++b)
-      tma_load_2d(smem_u32(s_st + b * G::kRows * TC), &a.tm, tile * TC, b * G::kRows, bar);
+      tma_load_2d(smem_u32(s_st + b * G::kRows * TC), &a.tm, t * TC, r * N + b * G::kRows, bar);
   };
   if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
   uint32_t parity = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     if (!stage_ready(bar, parity, a.err)) return;
     parity ^= 1;
-    const int col = tile * TC + c;
+    const int col = (tile % tpr) * TC + c;
     const bool ok = col < ncols;
+    const size_t rbase = (size_t)(tile / tpr) * N * ncols;
 #pragma unroll 1
     for (int f = 0; f < a.nout; ++f) {
       const float* mt = s_m + s_xm[f] * N + p;
@@ -166,10 +169,10 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(co
         }
       }
       fft_line<N, L>(v, p, c, s_x, s_tw);
-      float2* d = s_dst[f] + (ok ? col : 0);
+      float2* d = s_dst[f] + rbase + (ok ? col : 0);
 #pragma unroll
       for (int j = 0; j < E; ++j)
-        if (ok) d[fft_out_index<N>(p, j) * ncols] = v[j];
+        if (ok) d[(size_t)fft_out_index<N>(p, j) * ncols] = v[j];
       __syncthreads();
     }
   }
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
   __syncthreads();
   const int nhp = a.nhp, nout = a.nout;
   const int ktiles = (nhp + TC - 1) / TC;
-  const int ntiles = N * ktiles;
+  const int ntiles = N * a.batch * ktiles;  // x planes of all realisations, back to back
   auto issue = [&](int tile, int src) {
     const int x = tile / ktiles, kz0 = (tile % ktiles) * TC;
     mbar_expect_tx(bar, N * TC * 8);
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
   const int npairs = (a.nfields + 1) / 2;
   const int c = tid / P, p = tid % P;
   const int ln = c / 3, pair = c % 3;
-  const int nlines = N * N;
+  const int nlines = a.nlines;
   const int line = blockIdx.x * LINES + ln;
   const bool active = pair < npairs && line < nlines;
   const int fa = 2 * pair, fb = 2 * pair + 1;
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
         const int l = pt / N, z = pt % N;
         const int gl = blockIdx.x * LINES + l;
         valid[u] = pt < kPts && gl < nlines;
-        q[u] = gl * N + z;
+        q[u] = gl * N + z;  // < 2^31: checked at plan creation
         fm[u] = valid[u] ? a.fmax[q[u]] : 0.f;  // issued early: its latency hides under the math
 #pragma unroll
         for (int f = 0; f < 6; ++f) h[u][f] = valid[u] ? s_f[(l * 6 + f) * N + z] : 0.f;
@@ -475,7 +478,7 @@ static unsigned persistent_grid(K kernel, int threads, size_t smem, long ntiles)
 template <int N>
 static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
   using C = Cfg<N>;
-  const long ntiles = ((long)N * a.nhp + C::TC - 1) / C::TC;
+  const long ntiles = (((long)N * a.nhp + C::TC - 1) / C::TC) * a.batch;
   const unsigned grid = persistent_grid(k_pass_x<N, C::TC>, C::threads_xy, C::smem_xy, ntiles);
   k_pass_x<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
   return cudaGetLastError();
@@ -484,7 +487,7 @@ static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
 template <int N>
 static cudaError_t run_y(const ArgsY& a, cudaStream_t st) {
   using C = Cfg<N>;
-  const long ntiles = (long)N * ((a.nhp + C::TC - 1) / C::TC);
+  const long ntiles = (long)N * a.batch * ((a.nhp + C::TC - 1) / C::TC);
   const unsigned grid = persistent_grid(k_pass_y<N, C::TC>, C::threads_xy, C::smem_xy, ntiles);
   k_pass_y<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
   return cudaGetLastError();
@@ -493,7 +496,7 @@ static cudaError_t run_y(const ArgsY& a, cudaStream_t st) {
 template <int N>
 static cudaError_t run_z(const ArgsZ& a, bool dump, cudaStream_t st) {
   using C = Cfg<N>;
-  const long nlines = (long)N * N;
+  const long nlines = a.nlines;
   const unsigned grid = (unsigned)((nlines + C::LINES - 1) / C::LINES);
   if (dump) k_pass_z<N, C::LINES, true><<<grid, C::threads_z, C::smem_z, st>>>(a);
   else k_pass_z<N, C::LINES, false><<<grid, C::threads_z, C::smem_z, st>>>(a);
@@ -590,19 +593,19 @@ static cudaError_t encode(CUtensorMap* tm, int rank, const void* base, const cuu
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int n, int nhp) {
+cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int n, int nhp, int batch) {
   const PassShape sh = pass_shape(n);
   const int boxes = (n + 255) / 256;
-  const cuuint64_t dims[2] = {(cuuint64_t)n * nhp, (cuuint64_t)n};
+  const cuuint64_t dims[2] = {(cuuint64_t)n * nhp, (cuuint64_t)n * batch};
   const cuuint64_t strides[1] = {(cuuint64_t)n * nhp * 8};
   const cuuint32_t box[2] = {(cuuint32_t)sh.tc, (cuuint32_t)(n / boxes)};
   return encode(tm, 2, src, dims, strides, box);
 }
 
-cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int n, int nhp, size_t spec_elems) {
+cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int n, int nhp, size_t spec_elems, int batch) {
   const PassShape sh = pass_shape(n);
   const int boxes = (n + 255) / 256;
-  const cuuint64_t dims[4] = {(cuuint64_t)nhp, (cuuint64_t)n, (cuuint64_t)n, 3};
+  const cuuint64_t dims[4] = {(cuuint64_t)nhp, (cuuint64_t)n, (cuuint64_t)n * batch, 3};
   const cuuint64_t strides[3] = {(cuuint64_t)nhp * 8, (cuuint64_t)n * nhp * 8, (cuuint64_t)spec_elems * 8};
   const cuuint32_t box[4] = {(cuuint32_t)sh.tc, (cuuint32_t)(n / boxes), 1, 1};
   return encode(tm, 4, src3, dims, strides, box);

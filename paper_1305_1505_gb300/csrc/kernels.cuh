@@ -19,8 +19,8 @@ namespace pin {
 constexpr int kMaxFields = 6;
 
 // x pass: for each output f, dst[f] = IDFT_x(mult[xm[f]] * src).  The source
-// tiles arrive by TMA: tm is a 2D map over src, {N*nhp columns, N rows}, box
-// {tc, rows/boxes}.
+// tiles arrive by TMA: tm is a 2D map over src, {N*nhp columns, batch*N rows}
+// (realisations stacked along rows), box {tc, rows/boxes}.
 struct ArgsX {
   CUtensorMap tm;
   const float2* src;
@@ -30,6 +30,7 @@ struct ArgsX {
   const float* mult;  // [3][N] multipliers of this radius (W, kW, k^2W, each / N)
   const float2* tw;   // level-2 twiddles [E][P]
   int nhp;
+  int batch;          // realisations stacked back to back (same N, radii)
   int* err;           // set to 1 if a TMA wait gave up (bounded wait)
 };
 
@@ -37,7 +38,7 @@ struct ArgsX {
 // z factor mult[zm[f]](kz), times i when muli[f], is constant along a y line.
 // Outputs are processed in the given order; consecutive outputs with the same
 // source share one staged tile.  tm is a 4D map over the three source spectra
-// (stored back to back), {nhp, N, N, 3}, box {tc, rows/boxes, 1, 1}.
+// (stored back to back), {nhp, N, batch*N, 3}, box {tc, rows/boxes, 1, 1}.
 struct ArgsY {
   CUtensorMap tm;
   const float2* src[3];
@@ -50,6 +51,7 @@ struct ArgsY {
   const float* mult;
   const float2* tw;
   int nhp;
+  int batch;
   int* err;
 };
 
@@ -67,6 +69,7 @@ struct RedoEntry {
 struct ArgsZ {
   const float2* src[kMaxFields];
   int nfields;
+  int nlines;    // batch * N^2 lines along z
   const float2* tw;
   int nhp;
   // collapse mode
@@ -98,8 +101,8 @@ struct PassShape {
 // Tensor maps of the x and y passes (host; the encoder comes from the driver
 // entry point, so no driver library is linked).  spec_elems is the stride
 // between the spectra the y map spans.
-cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int n, int nhp);
-cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int n, int nhp, size_t spec_elems);
+cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int n, int nhp, int batch);
+cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int n, int nhp, size_t spec_elems, int batch);
 
 bool size_supported(int n);
 PassShape pass_shape(int n);

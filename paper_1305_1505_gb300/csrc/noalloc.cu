@@ -178,8 +178,8 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
   unsigned* redo_count = reinterpret_cast<unsigned*>(base + kOffRedoCount);
   int* err = reinterpret_cast<int*>(base + kOffErr);
   CUtensorMap tm_x, tm_y;
-  if (pin::make_tmap_x(&tm_x, phi0, n, nhp) != cudaSuccess ||
-      pin::make_tmap_y(&tm_y, U, n, nhp, spec) != cudaSuccess)
+  if (pin::make_tmap_x(&tm_x, phi0, n, nhp, 1) != cudaSuccess ||
+      pin::make_tmap_y(&tm_y, U, n, nhp, spec, 1) != cudaSuccess)
     return PIN_ECUDA;
   pin::RedoEntry* redo_list = reinterpret_cast<pin::RedoEntry*>(base + kOffRedo);
   const double dcorr = noalloc_dcorr();
@@ -209,6 +209,7 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
     ax.mult = m;
     ax.tw = tw;
     ax.nhp = nhp;
+    ax.batch = 1;
     ax.err = err;
     pin::ArgsY ay{};
     ay.tm = tm_y;
@@ -224,10 +225,12 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
     ay.mult = m;
     ay.tw = tw;
     ay.nhp = nhp;
+    ay.batch = 1;
     ay.err = err;
     pin::ArgsZ az{};
     for (int f = 0; f < 6; ++f) az.src[f] = V + f * spec;
     az.nfields = 6;
+    az.nlines = n * n;
     az.tw = tw;
     az.nhp = nhp;
     az.fmax = F_max;

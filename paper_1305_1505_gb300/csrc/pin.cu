@@ -25,6 +25,7 @@ using namespace pin;
 
 struct pin_plan_s {
   int n = 0, nhp = 0, nscales = 0, correction = 1, precision = 0;
+  int batch = 1;          // realisations sharing the grid and radii
   double box = 0.0;
   std::vector<double> radii;
   int device = 0;
@@ -32,6 +33,7 @@ struct pin_plan_s {
   bool own_stream = false;
   PassShape shape{};
   size_t spec_elems = 0;  // complex elements of one padded half-spectrum
+  size_t field_elems = 0; // batch * spec_elems: one field of every realisation
   float2* phi0 = nullptr;
   float2* U = nullptr;    // 3 spectra
   float2* V = nullptr;    // 6 spectra
@@ -111,20 +113,25 @@ bool validate(const pin_plan_desc* d, std::string* why) {
     if (!(d->radii[s] >= 0.0) || !std::isfinite(d->radii[s])) { *why = "radii must be finite and >= 0"; return false; }
   if (d->correction != PIN_CORR_NONE && d->correction != PIN_CORR_SPHERE) { *why = "bad correction mode"; return false; }
   if (d->precision != PIN_FP32_FALLBACK64) { *why = "bad precision mode"; return false; }
+  const long long b = d->batch <= 0 ? 1 : d->batch;
+  if (b > 4096) { *why = "batch must be in 1..4096"; return false; }
+  if (b * (long long)d->nx * d->nx * d->nx >= (1ll << 31)) { *why = "batch * N^3 must stay below 2^31"; return false; }
   return true;
 }
 
 // FP64 redo queue capacity: 1/64 of the grid (observed rate ~2e-4), at least 64 Ki.
-unsigned redo_capacity(int n) {
-  const size_t n3 = (size_t)n * n * n;
+unsigned redo_capacity(int n, int batch) {
+  const size_t n3 = (size_t)n * n * n * batch;
   return (unsigned)std::max<size_t>(65536, n3 / 64);
 }
 
-size_t footprint(int n, int nscales) {
-  const size_t spec = (size_t)n * n * padded_half(n);
-  const size_t n3 = (size_t)n * n * n;
+int batch_of(const pin_plan_desc* d) { return d->batch <= 0 ? 1 : d->batch; }
+
+size_t footprint(int n, int nscales, int batch) {
+  const size_t spec = (size_t)n * n * padded_half(n) * batch;
+  const size_t n3 = (size_t)n * n * n * batch;
   return spec * 8 * 10 + n3 * 8 + (size_t)(nscales + 1) * 3 * n * 4 + (size_t)n * 8 + 64 +
-         (size_t)redo_capacity(n) * sizeof(RedoEntry) + 16 + sizeof(int);
+         (size_t)redo_capacity(n, batch) * sizeof(RedoEntry) + 16 + sizeof(int);
 }
 
 // Per-axis multipliers for one radius: {W, k W, k^2 W} / n with
@@ -140,15 +147,16 @@ void fill_mult(float* out, int n, double box, double radius) {
   }
 }
 
-__global__ void k_load_phi0(const void* src, int dtype, int n, int nhp, double box, float2* phi0) {
+__global__ void k_load_phi0(const void* src, int dtype, int n, int nhp, double box, int batch,
+                            float2* phi0) {
   const int nh = n / 2 + 1;
-  const size_t total = (size_t)n * n * nhp;
+  const size_t total = (size_t)n * n * nhp * batch;
   const double kf = 2.0 * M_PI / box;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     const int iz = (int)(i % nhp);
     const size_t r = i / nhp;
-    const int iy = (int)(r % n), ix = (int)(r / n);
+    const int iy = (int)(r % n), ix = (int)((r / n) % n);  // r runs over realisations too
     float2 out = make_float2(0.f, 0.f);
     if (iz < nh) {
       const size_t j = r * nh + iz;
@@ -212,7 +220,7 @@ void release(pin_plan_t p) {
   p->graph = nullptr;
 }
 
-float2* spec(pin_plan_t p, float2* base, int f) { return base + (size_t)f * p->spec_elems; }
+float2* spec(pin_plan_t p, float2* base, int f) { return base + (size_t)f * p->field_elems; }
 
 // Filter-and-transform passes of one radius (mult set `ms`), ending in the
 // collapse update (dump == nullptr) or a dump of the six real components.
@@ -228,6 +236,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   ax.mult = mult;
   ax.tw = p->tw;
   ax.nhp = p->nhp;
+  ax.batch = p->batch;
   ax.err = p->err;
   PIN_CK(p, launch_x(p->n, ax, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 1], p->stream, cudaEventRecordExternal));
@@ -253,6 +262,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   ay.mult = mult;
   ay.tw = p->tw;
   ay.nhp = p->nhp;
+  ay.batch = p->batch;
   ay.err = p->err;
   PIN_CK(p, launch_y(p->n, ay, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 2], p->stream, cudaEventRecordExternal));
@@ -260,6 +270,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   ArgsZ az{};
   for (int f = 0; f < 6; ++f) az.src[f] = spec(p, p->V, f);
   az.nfields = 6;
+  az.nlines = p->n * p->n * p->batch;
   az.tw = p->tw;
   az.nhp = p->nhp;
   az.fmax = p->fmax;
@@ -284,7 +295,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
 }
 
 pin_status enqueue_collapse(pin_plan_t p) {
-  const size_t n3 = (size_t)p->n * p->n * p->n;
+  const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
   PIN_CK(p, cudaMemsetAsync(p->fmax, 0, n3 * sizeof(float), p->stream));
   PIN_CK(p, cudaMemsetAsync(p->idx, 0xFF, n3 * sizeof(int), p->stream));
   for (int s = 0; s < p->nscales; ++s) {
@@ -344,7 +355,7 @@ extern "C" {
 size_t pin_footprint_bytes(const pin_plan_desc* d) {
   std::string why;
   if (!validate(d, &why)) return 0;
-  return footprint(d->nx, d->nscales);
+  return footprint(d->nx, d->nscales, batch_of(d));
 }
 
 pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
@@ -361,10 +372,12 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   p->radii.assign(d->radii, d->radii + d->nscales);
   p->correction = d->correction;
   p->precision = d->precision;
+  p->batch = batch_of(d);
   p->shape = pass_shape(p->n);
   p->spec_elems = (size_t)p->n * p->n * p->nhp;
+  p->field_elems = p->spec_elems * p->batch;
   p->dcorr = 1.0 / delta_c_value() - 1.0 / x3_value();
-  p->redo_cap = redo_capacity(p->n);
+  p->redo_cap = redo_capacity(p->n, p->batch);
   auto bail = [&](pin_status s) {
     release(p);
     delete p;
@@ -378,16 +391,16 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
     if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PIN_ECUDA);
     p->own_stream = true;
   }
-  const size_t n3 = (size_t)p->n * p->n * p->n;
+  const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
   const size_t mult_elems = (size_t)(p->nscales + 1) * 3 * p->n;
-  if (cudaMalloc(&p->phi0, p->spec_elems * 8) != cudaSuccess ||
-      cudaMalloc(&p->U, 3 * p->spec_elems * 8) != cudaSuccess ||
-      cudaMalloc(&p->V, 6 * p->spec_elems * 8) != cudaSuccess ||
+  if (cudaMalloc(&p->phi0, p->field_elems * 8) != cudaSuccess ||
+      cudaMalloc(&p->U, 3 * p->field_elems * 8) != cudaSuccess ||
+      cudaMalloc(&p->V, 6 * p->field_elems * 8) != cudaSuccess ||
       cudaMalloc(&p->fmax, n3 * 4) != cudaSuccess || cudaMalloc(&p->idx, n3 * 4) != cudaSuccess ||
       cudaMalloc(&p->mult, mult_elems * 4) != cudaSuccess ||
       cudaMalloc(&p->tw, (size_t)p->n * 8) != cudaSuccess ||
       cudaMalloc(&p->counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMalloc(&p->redo_list, (size_t)redo_capacity(p->n) * sizeof(RedoEntry)) != cudaSuccess ||
+      cudaMalloc(&p->redo_list, (size_t)p->redo_cap * sizeof(RedoEntry)) != cudaSuccess ||
       cudaMalloc(&p->redo_count, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -409,8 +422,8 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
       cudaMemset(p->counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess)
     return bail(PIN_ECUDA);
-  if (make_tmap_x(&p->tm_x, p->phi0, p->n, p->nhp) != cudaSuccess ||
-      make_tmap_y(&p->tm_y, p->U, p->n, p->nhp, p->spec_elems) != cudaSuccess)
+  if (make_tmap_x(&p->tm_x, p->phi0, p->n, p->nhp, p->batch) != cudaSuccess ||
+      make_tmap_y(&p->tm_y, p->U, p->n, p->nhp, p->field_elems, p->batch) != cudaSuccess)
     return bail(PIN_ECUDA);
   *out = p;
   return PIN_OK;
@@ -422,17 +435,17 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
   if (!delta_k) return fail(p, PIN_EINVAL, "null delta_k");
   if (dtype != PIN_C64 && dtype != PIN_C128) return fail(p, PIN_EINVAL, "dtype must be PIN_C64 or PIN_C128");
   const size_t nh = (size_t)p->n / 2 + 1;
-  const size_t bytes = (size_t)p->n * p->n * nh * (dtype == PIN_C64 ? 8 : 16);
+  const size_t bytes = (size_t)p->n * p->n * nh * (dtype == PIN_C64 ? 8 : 16) * p->batch;
   const void* src = delta_k;
   if (!on_device) {
     // stage through the V workspace (6 spectra >= one C128 half-spectrum)
     PIN_CK(p, cudaMemcpyAsync(p->V, delta_k, bytes, cudaMemcpyHostToDevice, p->stream));
     src = p->V;
   }
-  const size_t total = p->spec_elems;
+  const size_t total = p->field_elems;
   const int threads = 256;
   const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, 152 * 64);
-  k_load_phi0<<<blocks, threads, 0, p->stream>>>(src, dtype, p->n, p->nhp, p->box, p->phi0);
+  k_load_phi0<<<blocks, threads, 0, p->stream>>>(src, dtype, p->n, p->nhp, p->box, p->batch, p->phi0);
   PIN_CK(p, cudaGetLastError());
   if (!on_device) PIN_CK(p, cudaStreamSynchronize(p->stream));
   p->ic_set = true;
@@ -447,7 +460,7 @@ pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, in
   st = ensure_graph(p);
   if (st != PIN_OK) return st;
   PIN_CK(p, cudaGraphLaunch(p->graph_exec, p->stream));
-  const size_t n3 = (size_t)p->n * p->n * p->n;
+  const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   PIN_CK(p, cudaMemcpyAsync(F_max, p->fmax, n3 * 4, kind, p->stream));
   PIN_CK(p, cudaMemcpyAsync(scale_idx, p->idx, n3 * 4, kind, p->stream));
@@ -461,6 +474,7 @@ pin_status pin_hessian(pin_plan_t p, int scale, float* out6, int on_device) {
   if (st != PIN_OK) return st;
   if (!out6) return fail(p, PIN_EINVAL, "null output");
   if (scale < 0 || scale >= p->nscales) return fail(p, PIN_EINVAL, "scale index out of range");
+  if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_hessian needs a plan with batch 1");
   if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
   const size_t n3 = (size_t)p->n * p->n * p->n;
   float* dev = out6;
@@ -483,6 +497,7 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   pin_status st = check_plan(p);
   if (st != PIN_OK) return st;
   if (!psi) return fail(p, PIN_EINVAL, "null output");
+  if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_displacements needs a plan with batch 1");
   if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
   const size_t n3 = (size_t)p->n * p->n * p->n;
   float* dev = psi;
@@ -499,6 +514,7 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   ax.mult = mult;
   ax.tw = p->tw;
   ax.nhp = p->nhp;
+  ax.batch = 1;
   ax.err = p->err;
   cudaError_t e = launch_x(p->n, ax, p->stream);
   // psi_x <- U1, psi_y <- U0 (k_y), psi_z <- U0 (z: k_z); all times i
@@ -519,6 +535,7 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   ay.mult = mult;
   ay.tw = p->tw;
   ay.nhp = p->nhp;
+  ay.batch = 1;
   ay.err = p->err;
   if (e == cudaSuccess) e = launch_y(p->n, ay, p->stream);
   ArgsZ az{};
@@ -527,6 +544,7 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
     az.out[f] = dev + (size_t)f * n3;
   }
   az.nfields = 3;
+  az.nlines = p->n * p->n;
   az.tw = p->tw;
   az.nhp = p->nhp;
   if (e == cudaSuccess) e = launch_z(p->n, az, true, p->stream);

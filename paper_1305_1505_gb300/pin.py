@@ -34,7 +34,8 @@ class pin_plan_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("box", ctypes.c_double), ("nscales", ctypes.c_int),
                 ("radii", ctypes.POINTER(ctypes.c_double)), ("correction", ctypes.c_int),
-                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("batch", ctypes.c_int)]
 
 
 class pin_stats(ctypes.Structure):
@@ -113,11 +114,11 @@ def _check(status, plan=None):
         raise PinError(status, msg)
 
 
-def make_desc(n, box, radii, correction=PIN_CORR_SPHERE, stream=None):
+def make_desc(n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1):
     r = np.ascontiguousarray(radii, dtype=np.float64)
     d = pin_plan_desc(n, n, n, float(box), int(r.size),
                       r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(correction),
-                      PIN_FP32_FALLBACK64, ctypes.c_void_p(stream) if stream else None)
+                      PIN_FP32_FALLBACK64, ctypes.c_void_p(stream) if stream else None, int(batch))
     d._radii_keepalive = r
     return d
 
@@ -207,15 +208,16 @@ def pin_destroy(plan):
 class Plan:
     """Owns one pin plan; methods take torch tensors (device or host)."""
 
-    def __init__(self, n, box, radii, correction=PIN_CORR_SPHERE, stream=None):
+    def __init__(self, n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("pin needs a CUDA device; none is available")
         self.n = int(n)
         self.box = float(box)
+        self.batch = int(batch)
         self.radii = np.ascontiguousarray(radii, dtype=np.float64)
         s = stream.cuda_stream if stream is not None else None
-        self._desc = make_desc(self.n, self.box, self.radii, correction, s)
+        self._desc = make_desc(self.n, self.box, self.radii, correction, s, self.batch)
         self.handle = pin_plan(self._desc)
 
     def __del__(self):
@@ -231,7 +233,8 @@ class Plan:
         self.__del__()
 
     def set_ic(self, delta_k):
-        """delta_k: (n, n, n//2+1) complex64/complex128 tensor or numpy array."""
+        """delta_k: (n, n, n//2+1) complex64/complex128 tensor or numpy array, or
+        (batch, n, n, n//2+1) for a batched plan."""
         import torch
         if isinstance(delta_k, np.ndarray):
             a = np.ascontiguousarray(delta_k)
@@ -254,10 +257,11 @@ class Plan:
         work is only enqueued on the plan's stream (call .sync() before use)."""
         import torch
         n = self.n
+        shape = (n, n, n) if self.batch == 1 else (self.batch, n, n, n)
         if fmax is None:
-            fmax = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+            fmax = torch.empty(shape, dtype=torch.float32, device="cuda")
         if idx is None:
-            idx = torch.empty((n, n, n), dtype=torch.int32, device=fmax.device)
+            idx = torch.empty(shape, dtype=torch.int32, device=fmax.device)
         if fmax.is_cuda != idx.is_cuda:
             raise ValueError("F_max and scale_idx must both be on the device or both on the host")
         if fmax.is_cuda:
