@@ -132,11 +132,11 @@ int pin_kernels_per_call(pin_plan_t p);
  * record CUDA events around each pass of each radius (on the plan's stream,
  * inside its graph); pin_pass_times() then waits for the plan's work and
  * returns, for the last completed call, the device time in milliseconds summed
- * over radii of the x pass (filter + transform), the y pass and the z pass
- * (c2r + eigenvalues + collapse + running max, with the FP64 redo of the
- * queued ill-conditioned particles): ms3[0..2]. */
+ * over radii of: ms4[0] the x pass (filter + transform), ms4[1] the y pass,
+ * ms4[2] the z pass (c2r + eigenvalues), ms4[3] the root pass (collapse time
+ * + running max) with the FP64 redo of the queued ill-conditioned particles. */
 pin_status pin_profile(pin_plan_t p, int enable);
-pin_status pin_pass_times(pin_plan_t p, double* ms3);
+pin_status pin_pass_times(pin_plan_t p, double* ms4);
 
 /* Largest grid side the no-allocation entry point below accepts. */
 #define PIN_NOALLOC_MAX_N 64

@@ -342,65 +342,112 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
       }
     }
     __syncthreads();
-    CollapseConsts<float> ccf{a.dcorr_f, a.correction};
-    // PIN_Z_ILP independent particles per iteration: the collapse arithmetic
-    // is a long dependent chain, and the transform leaves few warps per SM
+    // eigenvalues of every particle of the block's lines; the collapse time
+    // and the running maximum follow in k_roots, at a higher occupancy than
+    // the long transforms of this kernel allow
     constexpr int kPts = LINES * N;
-    constexpr int U = PIN_Z_ILP;
-    for (int base_pt = tid; base_pt < kPts; base_pt += U * nthreads) {
-      float h[U][6], lam[U][3], F[U], kap[U], rabs[U], fm[U];
-      int q[U];
-      bool valid[U];
+    const size_t total = (size_t)nlines * N;
+    for (int pt = tid; pt < kPts; pt += nthreads) {
+      const int l = pt / N, z = pt % N;
+      const int gl = blockIdx.x * LINES + l;
+      if (gl >= nlines) continue;
+      float h[6], lam[3];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int pt = base_pt + u * nthreads;
-        const int l = pt / N, z = pt % N;
-        const int gl = blockIdx.x * LINES + l;
-        valid[u] = pt < kPts && gl < nlines;
-        q[u] = gl * N + z;  // < 2^31: checked at plan creation
-        fm[u] = valid[u] ? a.fmax[q[u]] : 0.f;  // issued early: its latency hides under the math
+      for (int f = 0; f < 6; ++f) h[f] = s_f[(l * 6 + f) * N + z];
+      const float rabs = eig3<float>(h, lam);
+      const int q = gl * N + z;  // < 2^31: checked at plan creation
+      if (rabs > 1.f - a.tau_eig) {
+        atomicAdd(a.counters + 0, 1ull);
+        const unsigned slot = atomicAdd(a.redo_count, 1u);
+        if (slot < a.redo_cap) {
+          RedoEntry e;
+          e.q = q;
 #pragma unroll
-        for (int f = 0; f < 6; ++f) h[u][f] = valid[u] ? s_f[(l * 6 + f) * N + z] : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) rabs[u] = eig3<float>(h[u], lam[u]);
-      CollapseState<float> cs[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) collapse_main<float>(lam[u], ccf, cs[u]);
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (cs[u].need[0] || cs[u].need[1]) collapse_rare<float>(cs[u]);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        F[u] = cs[u].best + cs[u].corr;
-        kap[u] = cs[u].kappa;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (!valid[u]) continue;
-        const bool redo_eig = rabs[u] > 1.f - a.tau_eig;
-        const bool redo_root = kap[u] < a.tau_root;
-        if (redo_eig || redo_root) {
-          atomicAdd(a.counters + (redo_eig ? 0 : 1), 1ull);
-          const unsigned slot = atomicAdd(a.redo_count, 1u);
-          if (slot < a.redo_cap) {
-            RedoEntry e;
-            e.q = q[u];
-#pragma unroll
-            for (int f = 0; f < 6; ++f) e.h[f] = h[u][f];
-            e.pad = 0;
-            a.redo_list[slot] = e;
-            continue;  // the redo kernel updates this particle
-          }
-          atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
+          for (int f = 0; f < 6; ++f) e.h[f] = h[f];
+          e.kind = 0;
+          a.redo_list[slot] = e;
+          lam[0] = lam[1] = lam[2] = __int_as_float(0x7fc00000);  // NaN: skipped by k_roots
+        } else {
+          atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 eigenvalues
         }
-        if (F[u] > fm[u]) {
-          a.fmax[q[u]] = F[u];
-          a.idx[q[u]] = a.scale;
+      }
+      a.lam_out[q] = lam[0];
+      a.lam_out[total + q] = lam[1];
+      a.lam_out[2 * total + q] = lam[2];
+    }
+  }
+}
+
+// ------------------------------------------------------------- root pass --
+// Per particle: the collapse time F from its eigenvalues (collapse.cuh), and
+// the running maximum F_max with its radius index, updated in place.  Few
+// registers, so many warps hide the latency of the dependent root iteration;
+// PIN_Z_ILP particles per thread and iteration.
+__global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
+  constexpr int U = PIN_Z_ILP;
+  const int total = a.npart;
+  const float* L0 = a.lam_out;
+  const float* L1 = a.lam_out + total;
+  const float* L2 = a.lam_out + 2 * (size_t)total;
+  CollapseConsts<float> ccf{a.dcorr_f, a.correction};
+  const int stride = gridDim.x * blockDim.x;
+  for (int q0 = blockIdx.x * blockDim.x + threadIdx.x; q0 < total; q0 += U * stride) {
+    float lam[U][3], fm[U];
+    bool valid[U];
+    int q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      q[u] = q0 + u * stride;
+      const bool in = q[u] < total;
+      lam[u][0] = in ? __ldg(L0 + q[u]) : 0.f;
+      lam[u][1] = in ? __ldg(L1 + q[u]) : 0.f;
+      lam[u][2] = in ? __ldg(L2 + q[u]) : 0.f;
+      fm[u] = in ? a.fmax[q[u]] : 0.f;
+      valid[u] = in && !isnan(lam[u][0]);  // NaN: queued by the z pass
+      if (!valid[u]) lam[u][0] = lam[u][1] = lam[u][2] = 0.f;
+    }
+    CollapseState<float> cs[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) collapse_main<float>(lam[u], ccf, cs[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cs[u].need[0] || cs[u].need[1]) collapse_rare<float>(cs[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!valid[u]) continue;
+      const float F = cs[u].best + cs[u].corr;
+      if (cs[u].kappa < a.tau_root) {
+        atomicAdd(a.counters + 1, 1ull);
+        const unsigned slot = atomicAdd(a.redo_count, 1u);
+        if (slot < a.redo_cap) {
+          RedoEntry e;
+          e.q = q[u];
+          e.h[0] = lam[u][0];
+          e.h[1] = lam[u][1];
+          e.h[2] = lam[u][2];
+          e.h[3] = e.h[4] = e.h[5] = 0.f;
+          e.kind = 1;
+          a.redo_list[slot] = e;
+          continue;  // the redo kernel updates this particle
         }
+        atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
+      }
+      if (F > fm[u]) {
+        a.fmax[q[u]] = F;
+        a.idx[q[u]] = a.scale;
       }
     }
   }
+}
+
+cudaError_t launch_roots(const ArgsZ& a, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long need = ((long)a.npart + 255) / 256;
+  const unsigned grid = (unsigned)std::max<long>(1, std::min<long>(need, (long)sms * 8));
+  k_roots<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 // FP64 redo of the queued particles of one radius (grid-stride; each particle
@@ -414,7 +461,13 @@ __global__ void __launch_bounds__(128) k_redo64(ArgsZ a) {
     double h[6], lam[3], kap;
 #pragma unroll
     for (int f = 0; f < 6; ++f) h[f] = (double)e.h[f];
-    eig3<double>(h, lam);
+    if (e.kind == 0) {
+      eig3<double>(h, lam);
+    } else {
+      lam[0] = h[0];
+      lam[1] = h[1];
+      lam[2] = h[2];
+    }
     const float F = (float)collapse_from_eigs<double>(lam, ccd, kap);
     if (F > a.fmax[e.q]) {
       a.fmax[e.q] = F;

@@ -55,24 +55,30 @@ struct ArgsY {
   int* err;
 };
 
-// A particle whose FP32 collapse is ill-conditioned (near-degenerate
-// eigenvalue pair or near-tangent root): its grid index and the six FP32
-// Hessian components, finished in FP64 by the redo kernel.
+// A particle whose FP32 collapse is ill-conditioned, finished in FP64 by the
+// redo kernel: kind 0 (near-degenerate eigenvalue pair, queued by the z pass)
+// carries the six FP32 Hessian components; kind 1 (near-tangent or
+// unconverged root, queued by the root kernel) carries the three eigenvalues
+// in h[0..2].
 struct RedoEntry {
   int q;
   float h[6];
-  int pad;
+  int kind;
 };
 
 // z pass: c2r of each field (its z factor already applied by the y pass),
-// then either the collapse update or a dump of the real fields.
+// then either the eigenvalues of every particle (lam_out, [3][nlines*N];
+// NaN for particles queued for the FP64 redo) or a dump of the real fields.
 struct ArgsZ {
   const float2* src[kMaxFields];
   int nfields;
   int nlines;    // batch * N^2 lines along z
+  int npart;     // batch * N^3 particles
   const float2* tw;
   int nhp;
-  // collapse mode
+  // eigenvalue mode
+  float* lam_out;
+  // root and redo kernels
   float* fmax;
   int* idx;
   int scale;
@@ -110,7 +116,9 @@ cudaError_t prepare_kernels(int n);  // sets shared-memory attributes (once per 
 cudaError_t launch_x(int n, const ArgsX& a, cudaStream_t st);
 cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st);
 cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st);
-// FP64 redo of the particles the z pass queued (after it, same stream).
+// Collapse time and running maximum from the eigenvalues the z pass wrote
+// (after it, same stream), then the FP64 redo of every queued particle.
+cudaError_t launch_roots(const ArgsZ& a, cudaStream_t st);
 cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st);
 cudaError_t upload_constant_twiddles();  // per device
 

@@ -53,7 +53,7 @@ struct pin_plan_s {
   uint64_t calls = 0;
   double dcorr = 0.0;
   bool profile = false;             // graph carries per-pass event records
-  std::vector<cudaEvent_t> events;  // 4 per radius: before x, after x, y, z
+  std::vector<cudaEvent_t> events;  // 5 per radius: before x, after x, y, z, roots+redo
   std::string last_error;
 };
 
@@ -227,7 +227,7 @@ float2* spec(pin_plan_t p, float2* base, int f) { return base + (size_t)f * p->f
 pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   const float* mult = p->mult + (size_t)ms * 3 * p->n;
   const bool rec = p->profile && dump == nullptr && !p->events.empty();
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 0], p->stream, cudaEventRecordExternal));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 0], p->stream, cudaEventRecordExternal));
   ArgsX ax{};
   ax.tm = p->tm_x;
   ax.src = p->phi0;
@@ -239,7 +239,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   ax.batch = p->batch;
   ax.err = p->err;
   PIN_CK(p, launch_x(p->n, ax, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 1], p->stream, cudaEventRecordExternal));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 1], p->stream, cudaEventRecordExternal));
 
   // y pass, outputs grouped by source so that each staged tile serves them in
   // a row: V[xx] <- U2; V[xy] <- U1 (k_y), V[xz] <- U1 (z: k_z);
@@ -265,12 +265,14 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   ay.batch = p->batch;
   ay.err = p->err;
   PIN_CK(p, launch_y(p->n, ay, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 2], p->stream, cudaEventRecordExternal));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 2], p->stream, cudaEventRecordExternal));
 
   ArgsZ az{};
   for (int f = 0; f < 6; ++f) az.src[f] = spec(p, p->V, f);
   az.nfields = 6;
   az.nlines = p->n * p->n * p->batch;
+  az.npart = az.nlines * p->n;
+  az.lam_out = reinterpret_cast<float*>(p->U);  // the x-pass spectra are free by now
   az.tw = p->tw;
   az.nhp = p->nhp;
   az.fmax = p->fmax;
@@ -289,8 +291,12 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
     for (int f = 0; f < 6; ++f) az.out[f] = dump[f];
   if (!dump) PIN_CK(p, cudaMemsetAsync(p->redo_count, 0, sizeof(unsigned), p->stream));
   PIN_CK(p, launch_z(p->n, az, dump != nullptr, p->stream));
-  if (!dump) PIN_CK(p, launch_redo(az, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[4 * scale + 3], p->stream, cudaEventRecordExternal));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 3], p->stream, cudaEventRecordExternal));
+  if (!dump) {
+    PIN_CK(p, launch_roots(az, p->stream));
+    PIN_CK(p, launch_redo(az, p->stream));
+  }
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 4], p->stream, cudaEventRecordExternal));
   return PIN_OK;
 }
 
@@ -591,7 +597,7 @@ pin_status pin_get_stats(pin_plan_t p, pin_stats* out) {
   return PIN_OK;
 }
 
-int pin_kernels_per_call(pin_plan_t p) { return p ? 4 * p->nscales : 0; }
+int pin_kernels_per_call(pin_plan_t p) { return p ? 5 * p->nscales : 0; }
 
 pin_status pin_profile(pin_plan_t p, int enable) {
   pin_status st = check_plan(p);
@@ -600,7 +606,7 @@ pin_status pin_profile(pin_plan_t p, int enable) {
   if (want == p->profile) return PIN_OK;
   PIN_CK(p, cudaStreamSynchronize(p->stream));
   if (want && p->events.empty()) {
-    p->events.resize(4 * (size_t)p->nscales, nullptr);
+    p->events.resize(5 * (size_t)p->nscales, nullptr);
     for (auto& e : p->events) PIN_CK(p, cudaEventCreate(&e));
   }
   p->profile = want;
@@ -612,18 +618,18 @@ pin_status pin_profile(pin_plan_t p, int enable) {
   return PIN_OK;
 }
 
-pin_status pin_pass_times(pin_plan_t p, double* ms3) {
+pin_status pin_pass_times(pin_plan_t p, double* ms4) {
   pin_status st = check_plan(p);
   if (st != PIN_OK) return st;
-  if (!ms3) return fail(p, PIN_EINVAL, "null output");
+  if (!ms4) return fail(p, PIN_EINVAL, "null output");
   if (!p->profile || p->events.empty() || p->calls == 0) return fail(p, PIN_ESTATE, "profiling is off or nothing ran");
   PIN_CK(p, cudaStreamSynchronize(p->stream));
-  ms3[0] = ms3[1] = ms3[2] = 0.0;
+  ms4[0] = ms4[1] = ms4[2] = ms4[3] = 0.0;
   for (int s = 0; s < p->nscales; ++s)
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
       float ms = 0.f;
-      PIN_CK(p, cudaEventElapsedTime(&ms, p->events[4 * s + k], p->events[4 * s + k + 1]));
-      ms3[k] += ms;
+      PIN_CK(p, cudaEventElapsedTime(&ms, p->events[5 * s + k], p->events[5 * s + k + 1]));
+      ms4[k] += ms;
     }
   return PIN_OK;
 }

@@ -173,7 +173,8 @@ def pin_profile(plan, enable):
 
 
 def pin_pass_times(plan):
-    ms = (ctypes.c_double * 3)()
+    """[x, y, z, roots] device milliseconds of the last call, summed over radii."""
+    ms = (ctypes.c_double * 4)()
     _check(load().pin_pass_times(plan, ms), plan)
     return list(ms)
 
