@@ -40,12 +40,32 @@ namespace pin {
 //  - division: the two-ulp fast form.
 // On the host (unit tests) the same formulas run with the C++ library
 // standing in for the hardware approximations.
+#ifdef __CUDA_ARCH__
+// single-instruction approximations (PTX sqrt/lg2/ex2 .approx): relative error
+// a few ulp; sqrt(0) = 0, lg2(0) = -inf, ex2(-inf) = 0
+__device__ __forceinline__ float ptx_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ptx_lg2(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ptx_ex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+#endif
+
 template <typename T> struct M;
 template <> struct M<float> {
-  // x * rsqrt(x): two instructions, ~2 ulp, no special-case branches (x >= 0)
+  // approximate square root of x >= 0 (a few ulp, no special-case branches)
   __host__ __device__ __forceinline__ static float sqrt_(float x) {
 #ifdef __CUDA_ARCH__
-    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+    return ptx_sqrt(x);
 #else
     return std::sqrt(x);
 #endif
@@ -67,7 +87,7 @@ template <> struct M<float> {
     poly = fmaf(poly, ax, 0.0889789874f);
     poly = fmaf(poly, ax, -0.2145988016f);
     poly = fmaf(poly, ax, 1.5707963050f);
-    const float r = sqrt_(1.0f - ax) * poly;
+    const float r = sqrt_(fmaxf(1.0f - ax, 0.0f)) * poly;
     return x < 0.0f ? 3.14159265358979f - r : r;
   }
   __host__ __device__ __forceinline__ static void sincos_(float x, float* sn, float* cs) {
@@ -92,17 +112,17 @@ template <> struct M<float> {
     return std::exp(x);
 #endif
   }
-  // approximate sqrt / cbrt of x >= 0 (relative error ~1e-7 / ~1e-6): bounds only
+  // approximate sqrt / cbrt of max(x, 0) (relative error ~1e-7 / ~1e-6): bounds only
   __host__ __device__ __forceinline__ static float sqrt_approx(float x) {
 #ifdef __CUDA_ARCH__
-    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+    return ptx_sqrt(fmaxf(x, 0.0f));
 #else
     return x > 0.0f ? std::sqrt(x) : 0.0f;
 #endif
   }
   __host__ __device__ __forceinline__ static float cbrt_approx(float x) {
 #ifdef __CUDA_ARCH__
-    return x > 0.0f ? exp2f(__log2f(x) * (1.0f / 3.0f)) : 0.0f;
+    return ptx_ex2(ptx_lg2(fmaxf(x, 0.0f)) * (1.0f / 3.0f));
 #else
     return x > 0.0f ? std::cbrt(x) : 0.0f;
 #endif
@@ -111,7 +131,7 @@ template <> struct M<float> {
     if (x == 0.0f) return 0.0f;
     const float ax = fabsf(x);
 #ifdef __CUDA_ARCH__
-    float u = exp2f(__log2f(ax) * (1.0f / 3.0f));
+    float u = ptx_ex2(ptx_lg2(ax) * (1.0f / 3.0f));
 #else
     float u = std::exp2(std::log2(ax) * (1.0f / 3.0f));
 #endif
@@ -206,13 +226,16 @@ __host__ __device__ __forceinline__ T largest_root_iter(T c1, T c2, T c3, T& kap
   const bool none = !right && c3 <= T(0);  // single root, and it is not positive
   T x = right ? up : T(0);
   T step = T(0);
+  // Halley: x -= g g' / (g'^2 - g g''/2).  The denominator is floored at a
+  // tiny positive value instead of tested: a degenerate step leaves a large
+  // last step, which sends the particle to the FP64 redo below.
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     const T g = ((x - c1) * x - c2) * x - c3;
     const T dg = (T(3) * x - T(2) * c1) * x - c2;
-    const T d2 = T(6) * x - T(2) * c1;
-    const T den = T(2) * dg * dg - g * d2;
-    step = den != T(0) ? F::div_(T(2) * g * dg, den != T(0) ? den : T(1)) : T(0);
+    const T d2h = T(3) * x - c1;
+    const T den = dg * dg - g * d2h;
+    step = F::div_(g * dg, den > T(1e-30) ? den : T(1e-30));
     x = x - step;
   }
   kappa = root_kappa<T>(c1, c2, x);

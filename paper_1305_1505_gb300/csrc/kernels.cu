@@ -485,7 +485,11 @@ cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st) {
 
 template <int N> struct Cfg {
   static constexpr int E = Shape<N>::E, P = Shape<N>::P;
-  static constexpr int TC = P >= 8 ? 16 : (P == 4 ? 32 : 64);
+  // columns per x/y tile (a TMA box row is TC x 8 bytes)
+#ifndef PIN_TC_LONG
+#define PIN_TC_LONG 16
+#endif
+  static constexpr int TC = P >= 16 ? PIN_TC_LONG : (P >= 8 ? 16 : (P == 4 ? 32 : 64));
   static constexpr int LINES = 64 / P;
   // staged tile + exchange + twiddles + multipliers + alignment slack
   static constexpr size_t smem_xy = (size_t)N * TC * 8 + (size_t)XLayoutCols<E, P, TC>::kSize * 8 +
