@@ -277,7 +277,10 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
   using L = XLayoutLines<E, P, NC>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* s_x = reinterpret_cast<float2*>(smem_raw);
-  constexpr int kXBytes = L::kSize * 8, kFBytes = LINES * 6 * N * 4;
+  // field lines padded by P/2 floats so that the pair-columns of a warp
+  // (each P floats wide) start on different banks
+  constexpr int kFS = N + (P >= 2 ? P / 2 : 1);
+  constexpr int kXBytes = L::kSize * 8, kFBytes = LINES * 6 * kFS * 4;
   constexpr int kBufBytes = kXBytes > kFBytes ? kXBytes : kFBytes;
   float2* s_tw = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem_raw) + kBufBytes);
   float* s_f = reinterpret_cast<float*>(smem_raw);
@@ -337,8 +340,8 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
 #pragma unroll
       for (int j = 0; j < E; ++j) {
         const int z = fft_out_index<N>(p, j);
-        s_f[(ln * 6 + fa) * N + z] = v[j].x;
-        s_f[(ln * 6 + fb) * N + z] = v[j].y;
+        s_f[(ln * 6 + fa) * kFS + z] = v[j].x;
+        s_f[(ln * 6 + fb) * kFS + z] = v[j].y;
       }
     }
     __syncthreads();
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
       if (gl >= nlines) continue;
       float h[6], lam[3];
 #pragma unroll
-      for (int f = 0; f < 6; ++f) h[f] = s_f[(l * 6 + f) * N + z];
+      for (int f = 0; f < 6; ++f) h[f] = s_f[(l * 6 + f) * kFS + z];
       const float rabs = eig3<float>(h, lam);
       const int q = gl * N + z;  // < 2^31: checked at plan creation
       if (rabs > 1.f - a.tau_eig) {
@@ -495,7 +498,7 @@ template <int N> struct Cfg {
   static constexpr size_t smem_xy = (size_t)N * TC * 8 + (size_t)XLayoutCols<E, P, TC>::kSize * 8 +
                                     (size_t)E * P * 8 + (size_t)3 * N * 4 + 128;
   static constexpr size_t xz = (size_t)XLayoutLines<E, P, 3 * LINES>::kSize * 8;
-  static constexpr size_t fz = (size_t)LINES * 6 * N * 4;
+  static constexpr size_t fz = (size_t)LINES * 6 * (N + (P >= 2 ? P / 2 : 1)) * 4;
   static constexpr size_t smem_z = (xz > fz ? xz : fz) + (size_t)E * P * 8;
   static constexpr int threads_xy = TC * P;
   static constexpr int threads_z = 3 * LINES * P;
