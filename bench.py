@@ -190,7 +190,7 @@ def run_ours(args):
     radii = ic.log_radii(w["r_min"], w["r_max"], S)
     stream = torch.cuda.Stream()
     d32 = ic.delta_k(n, w["box"], w["seed"] + 1000 * rank if ws > 1 else w["seed"], dtype=np.complex64)
-    plan = pin.Plan(n, w["box"], radii, stream=stream)
+    plan = pin.Plan(n, w["box"], radii, stream=stream, velocities=args.velocities)
     dk = torch.from_numpy(d32).cuda()
     plan.set_ic(dk)
     F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
@@ -269,7 +269,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(_config(w), velocities=bool(args.velocities)),
             "roofline": {"bound": "hbm", "kernel": ("k_pass_" if names[dom] != "roots" else "k_") + names[dom],
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
@@ -378,6 +379,8 @@ def main():
     ap.add_argument("--grid", type=int, default=0,
                     help="grid side for profiling captures (box = 4 Mpc/h per cell); default 768")
     ap.add_argument("--nscales", type=int, default=0, help="number of radii; default 40")
+    ap.add_argument("--velocities", action="store_true",
+                    help="also keep v_max (the displacement smoothed on R_max): 9 fields per radius")
     ap.add_argument("--workload", default="paper", choices=["paper", "ensemble"],
                     help="paper: 768^3 x 40 (the metric); ensemble: 64 x 128^3 batched vs sequential")
     args = ap.parse_args()

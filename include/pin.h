@@ -70,6 +70,9 @@ typedef struct {
                             are then B consecutive copies of the single-realisation
                             layout; one launch per pass covers all of them.  B * N^3 must
                             stay below 2^31.  pin_hessian and pin_displacements need B = 1. */
+  int velocities;        /* 1: also keep, per particle, the Zel'dovich displacement of the
+                            field smoothed at R_max (the velocity of Sec. 2.1.1, see
+                            pin_velocities); costs three more spectra per radius.  0: off. */
 } pin_plan_desc;
 
 /* Runtime counters of a plan (cumulative over its pin_collapse_times calls). */
@@ -107,6 +110,16 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
  * returns (use pin_sync or the stream).  on_device = 0: host pointers; the
  * call returns when the results are in host memory. */
 pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, int on_device);
+
+/* v_max of Sec. 2.1.1: for each particle, the first derivative of the peculiar
+ * potential smoothed on R_max, as the linear (Zel'dovich) displacement
+ * psi_R(k) = i k W(kR) delta(k)/k^2 at the radius where F_max was reached
+ * (zero where the particle never collapses), from the last
+ * pin_collapse_times call of a plan created with velocities = 1.  Output
+ * psi_max = [3][B][N^3] floats in Mpc/h; the peculiar velocity follows by the
+ * linear factor a H f(a) of the caller's cosmology (D = 1 at z = 0).  Same
+ * on_device semantics as pin_collapse_times. */
+pin_status pin_velocities(pin_plan_t p, float* psi_max, int on_device);
 
 /* The six real components of the deformation tensor phi_ij(q) at radius
  * index `scale` (the a1-a2 steps alone), out6 = [6][N^3] floats in the order

@@ -37,6 +37,7 @@ def lib():
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_hessian_point.restype = ctypes.c_double
         L.or_displacement.argtypes = [_dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.or_displacement_r.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
         L.or_hessian_points.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp]
         L.or_eig3.argtypes = [_dp, _dp]
@@ -52,7 +53,7 @@ def lib():
         L.or_collapse_slope.argtypes = [_dp]
         L.or_collapse_slope.restype = ctypes.c_double
         L.or_collapse_times.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
-                                        ctypes.c_int, _dp, _ip, _dp, _dp, _ip, _dp]
+                                        ctypes.c_int, _dp, _ip, _dp, _dp, _ip, _dp, _dp]
         L.or_collapse_times_sampled.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                                 _dp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_longlong), _dp, _ip, _dp,
@@ -95,12 +96,12 @@ def hessian(delta_half, box, radius):
     return out, mi.value
 
 
-def displacement(delta_half, box):
-    """(3, n, n, n) FP64 Zel'dovich displacement psi = i k delta / k^2."""
+def displacement(delta_half, box, radius=0.0):
+    """(3, n, n, n) FP64 Zel'dovich displacement psi = i k W(kR) delta / k^2."""
     d = _c128(delta_half)
     n = d.shape[0]
     out = np.empty((3, n, n, n), dtype=np.float64)
-    rc = lib().or_displacement(_p(d.view(np.float64)), n, box, _p(out))
+    rc = lib().or_displacement_r(_p(d.view(np.float64)), n, box, radius, _p(out))
     if rc:
         raise ValueError("or_displacement failed: %d" % rc)
     return out
@@ -168,9 +169,10 @@ def collapse_slope(lam):
     return lib().or_collapse_slope(_p(lam))
 
 
-def collapse_times(delta_half, box, radii, correction=1, keep_all=False):
-    """Returns dict with fmax, idx (n^3), f2/idx2 (runner-up), slope, and
-    f_all (S, n^3) when keep_all."""
+def collapse_times(delta_half, box, radii, correction=1, keep_all=False, velocities=False):
+    """Returns dict with fmax, idx (n^3), f2/idx2 (runner-up), slope, f_all
+    (S, n^3) when keep_all, and vmax (3, n^3: the smoothed displacement at the
+    radius of F_max) when velocities."""
     d = _c128(delta_half)
     n = d.shape[0]
     r = np.ascontiguousarray(radii, dtype=np.float64)
@@ -182,14 +184,17 @@ def collapse_times(delta_half, box, radii, correction=1, keep_all=False):
     idx2 = np.empty(n3, dtype=np.int32)
     slope = np.empty(n3)
     f_all = np.empty((S, n3)) if keep_all else None
+    vmax = np.empty((3, n3)) if velocities else None
     rc = lib().or_collapse_times(_p(d.view(np.float64)), n, box, S, _p(r), correction,
                                  _p(fmax), _p(idx, ctypes.c_int), _p(f_all), _p(f2),
-                                 _p(idx2, ctypes.c_int), _p(slope))
+                                 _p(idx2, ctypes.c_int), _p(slope), _p(vmax))
     if rc:
         raise ValueError("or_collapse_times failed: %d" % rc)
     out = dict(fmax=fmax, idx=idx, f2=f2, idx2=idx2, slope=slope)
     if keep_all:
         out["f_all"] = f_all
+    if velocities:
+        out["vmax"] = vmax
     return out
 
 

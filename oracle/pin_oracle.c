@@ -298,12 +298,14 @@ int or_hessian_points(const double* delta_half_ri, int n, double box, double rad
   return 0;
 }
 
-/* Zel'dovich displacement of the unsmoothed field (Sec. 2.1.2: particles
- * and halos are displaced with the ZA, first-order LPT): x = q + psi with
- * psi = -grad phi and del^2 phi = delta, i.e. psi_i(k) = i k_i delta(k) / k^2,
- * so that delta = -div psi.  A mode whose k_i sits on the Nyquist index is
- * zeroed for component i (the odd multiplier breaks Hermitian symmetry). */
-int or_displacement(const double* delta_half_ri, int n, double box, double* out3) {
+/* Zel'dovich displacement of the field smoothed on radius R (Sec. 2.1.2:
+ * particles and halos are displaced with the ZA, first-order LPT; Sec. 2.1.1:
+ * v_max comes from the first derivative of the potential smoothed on R_max):
+ * x = q + psi with psi = -grad phi and del^2 phi = delta, i.e.
+ * psi_i(k) = i k_i W(kR) delta(k) / k^2, so that delta = -div psi for R = 0.
+ * A mode whose k_i sits on the Nyquist index is zeroed for component i (the
+ * odd multiplier breaks Hermitian symmetry). */
+int or_displacement_r(const double* delta_half_ri, int n, double box, double radius, double* out3) {
   if (n < 2 || (n & 1)) return -1;
   const double complex* half = (const double complex*)delta_half_ri;
   const int nh = n / 2 + 1;
@@ -324,7 +326,7 @@ int or_displacement(const double* delta_half_ri, int n, double box, double* out3
           double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
           double complex d = mirrored ? conj(half[src]) : half[src];
           double complex t = 0.0;
-          if (k2 > 0.0 && s[c] != -n / 2) t = I * k[c] / k2 * d;
+          if (k2 > 0.0 && s[c] != -n / 2) t = I * k[c] / k2 * exp(-0.5 * k2 * radius * radius) * d;
           full[((size_t)ix * n + iy) * n + iz] = t;
         }
       }
@@ -334,6 +336,10 @@ int or_displacement(const double* delta_half_ri, int n, double box, double* out3
   }
   free(full);
   return 0;
+}
+
+int or_displacement(const double* delta_half_ri, int n, double box, double* out3) {
+  return or_displacement_r(delta_half_ri, n, box, 0.0, out3);
 }
 
 /* ------------------------------------------------------- eigenvalues -- */
@@ -511,11 +517,14 @@ double or_collapse_slope(const double* lam) {
 
 int or_collapse_times(const double* delta_half_ri, int n, double box, int nscales,
                       const double* radii, int correction, double* fmax, int* idx,
-                      double* f_all, double* f2, int* idx2, double* slope) {
+                      double* f_all, double* f2, int* idx2, double* slope, double* vmax) {
   if (n < 2 || (n & 1) || nscales < 1) return -1;
   const size_t n3 = (size_t)n * n * n;
   double* h = malloc(sizeof(double) * 6 * n3);
-  if (!h) return -2;
+  double* psi = vmax ? malloc(sizeof(double) * 3 * n3) : NULL;
+  if (!h || (vmax && !psi)) { free(h); free(psi); return -2; }
+  if (vmax)
+    for (size_t q = 0; q < 3 * n3; ++q) vmax[q] = 0.0;
   for (size_t q = 0; q < n3; ++q) {
     fmax[q] = 0.0;
     idx[q] = -1;
@@ -524,7 +533,8 @@ int or_collapse_times(const double* delta_half_ri, int n, double box, int nscale
   }
   for (int s = 0; s < nscales; ++s) {
     int rc = or_hessian(delta_half_ri, n, box, radii[s], h, NULL);
-    if (rc) { free(h); return rc; }
+    if (!rc && vmax) rc = or_displacement_r(delta_half_ri, n, box, radii[s], psi);
+    if (rc) { free(h); free(psi); return rc; }
 #pragma omp parallel for schedule(static)
     for (long long q = 0; q < (long long)n3; ++q) {
       double h6[6];
@@ -536,6 +546,8 @@ int or_collapse_times(const double* delta_half_ri, int n, double box, int nscale
         if (f2) { f2[q] = fmax[q]; idx2[q] = idx[q]; }
         fmax[q] = F;
         idx[q] = s;
+        if (vmax)
+          for (int c = 0; c < 3; ++c) vmax[c * n3 + q] = psi[c * n3 + q];
         if (slope) slope[q] = or_collapse_slope(lam);
       } else if (f2 && F > f2[q]) {
         f2[q] = F;
@@ -544,6 +556,7 @@ int or_collapse_times(const double* delta_half_ri, int n, double box, int nscale
     }
   }
   free(h);
+  free(psi);
   return 0;
 }
 

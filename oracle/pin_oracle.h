@@ -19,6 +19,7 @@ double or_hessian_point(const double* delta_half_ri, int n, double box, double r
 int or_hessian_points(const double* delta_half_ri, int n, double box, double radius, int npts,
                       const long long* q_list, double* out);
 int or_displacement(const double* delta_half_ri, int n, double box, double* out3);
+int or_displacement_r(const double* delta_half_ri, int n, double box, double radius, double* out3);
 void or_eig3(const double* h6, double* lam);
 void or_axis_coeffs(const double* lam, int i, double* c);
 double or_first_root(const double* c);
@@ -29,7 +30,7 @@ double or_collapse_point(const double* h6, int correction, double* lam_out);
 double or_collapse_slope(const double* lam);
 int or_collapse_times(const double* delta_half_ri, int n, double box, int nscales,
                       const double* radii, int correction, double* fmax, int* idx,
-                      double* f_all, double* f2, int* idx2, double* slope);
+                      double* f_all, double* f2, int* idx2, double* slope, double* vmax);
 int or_collapse_times_sampled(const double* delta_half_ri, int n, double box, int nscales,
                               const double* radii, int correction, int npts,
                               const long long* q_list, double* fmax, int* idx, double* f2,

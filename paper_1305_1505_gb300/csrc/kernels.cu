@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(co
 // Lines along y: a tile is TC consecutive kz of one x plane; element
 // (ky, kz) of plane x sits at (x*N + ky)*nhp + kz.  Columns past nhp are
 // zero-filled by the tensor map and not stored.
-template <int N, int TC>
+template <int N, int TC, bool DUAL>
 __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(const __grid_constant__ ArgsY a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
   using L = XLayoutCols<E, P, TC>;
@@ -194,7 +194,9 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
   float* s_m = reinterpret_cast<float*>(s_tw + E * P);
   __shared__ __align__(8) unsigned long long s_bar;
   __shared__ float2* s_dst[kMaxFields];
+  __shared__ float2* s_dst2[kMaxFields];
   __shared__ int s_sel[kMaxFields], s_ym[kMaxFields], s_zm[kMaxFields], s_mi[kMaxFields];
+  __shared__ int s_zm2[kMaxFields], s_mi2[kMaxFields];
   const int tid = threadIdx.x, c = tid % TC, p = tid / TC;
   const uint32_t bar = smem_u32(&s_bar);
   for (int i = tid; i < E * P; i += TC * P) s_tw[i] = a.tw[i];
@@ -205,6 +207,9 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
     s_ym[tid] = a.ym[tid];
     s_zm[tid] = a.zm[tid];
     s_mi[tid] = a.muli[tid];
+    s_dst2[tid] = a.dst2[tid];
+    s_zm2[tid] = a.zm2[tid];
+    s_mi2[tid] = a.muli2[tid];
   }
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -261,6 +266,18 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
         if (mi) w = cmuli(w);
         if (ok) d[(size_t)fft_out_index<N>(p, j) * nhp] = w;
       }
+      if (DUAL && s_dst2[o] != nullptr) {
+        // the same transform with another z factor (displacement components)
+        const float zf2 = (ok && kz <= N / 2) ? s_m[s_zm2[o] * N + kz] : 0.f;
+        const bool mi2 = s_mi2[o] != 0;
+        float2* d2 = s_dst2[o] + base;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          float2 w = cscale(v[j], zf2);
+          if (mi2) w = cmuli(w);
+          if (ok) d2[(size_t)fft_out_index<N>(p, j) * nhp] = w;
+        }
+      }
       __syncthreads();
     }
   }
@@ -270,17 +287,20 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
 // Lines along z: line index l = x*N + y, the half line src[f][l*nhp + kz],
 // kz in [0, N/2], is contiguous.  Fields are paired (A + iB) into one complex
 // length-N transform whose real and imaginary parts are the two real lines.
-template <int N, int LINES, bool DUMP>
-__global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pass_z(ArgsZ a) {
+// NP pairs per line: 3 (the six Hessian components) or 5 (plus the three
+// smoothed displacement components, kept for the velocity at R_max).
+template <int N, int LINES, bool DUMP, int NP>
+__global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_pass_z(ArgsZ a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
-  constexpr int NC = 3 * LINES;  // at most three pairs per line
+  constexpr int NC = NP * LINES;  // pair-columns of the block
+  constexpr int NF = 2 * NP;      // field slots per line
   using L = XLayoutLines<E, P, NC>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* s_x = reinterpret_cast<float2*>(smem_raw);
   // field lines padded by P/2 floats so that the pair-columns of a warp
   // (each P floats wide) start on different banks
   constexpr int kFS = N + (P >= 2 ? P / 2 : 1);
-  constexpr int kXBytes = L::kSize * 8, kFBytes = LINES * 6 * kFS * 4;
+  constexpr int kXBytes = L::kSize * 8, kFBytes = LINES * NF * kFS * 4;
   constexpr int kBufBytes = kXBytes > kFBytes ? kXBytes : kFBytes;
   float2* s_tw = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem_raw) + kBufBytes);
   float* s_f = reinterpret_cast<float*>(smem_raw);
@@ -291,7 +311,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
 
   const int npairs = (a.nfields + 1) / 2;
   const int c = tid / P, p = tid % P;
-  const int ln = c / 3, pair = c % 3;
+  const int ln = c / NP, pair = c % NP;
   const int nlines = a.nlines;
   const int line = blockIdx.x * LINES + ln;
   const bool active = pair < npairs && line < nlines;
@@ -340,8 +360,8 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
 #pragma unroll
       for (int j = 0; j < E; ++j) {
         const int z = fft_out_index<N>(p, j);
-        s_f[(ln * 6 + fa) * kFS + z] = v[j].x;
-        s_f[(ln * 6 + fb) * kFS + z] = v[j].y;
+        s_f[(ln * NF + fa) * kFS + z] = v[j].x;
+        s_f[(ln * NF + fb) * kFS + z] = v[j].y;
       }
     }
     __syncthreads();
@@ -356,7 +376,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
       if (gl >= nlines) continue;
       float h[6], lam[3];
 #pragma unroll
-      for (int f = 0; f < 6; ++f) h[f] = s_f[(l * 6 + f) * kFS + z];
+      for (int f = 0; f < 6; ++f) h[f] = s_f[(l * NF + f) * kFS + z];
       const float rabs = eig3<float>(h, lam);
       const int q = gl * N + z;  // < 2^31: checked at plan creation
       if (rabs > 1.f - a.tau_eig) {
@@ -377,6 +397,12 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
       a.lam_out[q] = lam[0];
       a.lam_out[total + q] = lam[1];
       a.lam_out[2 * total + q] = lam[2];
+      if constexpr (NP == 5) {
+        // smoothed displacement of this radius, copied to the state by k_roots
+        // when F_max moves here
+#pragma unroll
+        for (int cpt = 0; cpt < 3; ++cpt) a.psi_out[cpt * total + q] = s_f[(l * NF + 6 + cpt) * kFS + z];
+      }
     }
   }
 }
@@ -386,6 +412,7 @@ __global__ void __launch_bounds__(3 * LINES * Shape<N>::P, MinBlocks<N>::z) k_pa
 // the running maximum F_max with its radius index, updated in place.  Few
 // registers, so many warps hide the latency of the dependent root iteration;
 // PIN_Z_ILP particles per thread and iteration.
+template <bool VEL>
 __global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
   constexpr int U = PIN_Z_ILP;
   const int total = a.npart;
@@ -438,6 +465,11 @@ __global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
       if (F > fm[u]) {
         a.fmax[q[u]] = F;
         a.idx[q[u]] = a.scale;
+        if constexpr (VEL) {
+#pragma unroll
+          for (int cpt = 0; cpt < 3; ++cpt)
+            a.vstate[(size_t)cpt * total + q[u]] = a.psi_out[(size_t)cpt * total + q[u]];
+        }
       }
     }
   }
@@ -449,7 +481,8 @@ cudaError_t launch_roots(const ArgsZ& a, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long need = ((long)a.npart + 255) / 256;
   const unsigned grid = (unsigned)std::max<long>(1, std::min<long>(need, (long)sms * 8));
-  k_roots<<<grid, 256, 0, st>>>(a);
+  if (a.vstate) k_roots<true><<<grid, 256, 0, st>>>(a);
+  else k_roots<false><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -475,6 +508,11 @@ __global__ void __launch_bounds__(128) k_redo64(ArgsZ a) {
     if (F > a.fmax[e.q]) {
       a.fmax[e.q] = F;
       a.idx[e.q] = a.scale;
+      if (a.vstate) {
+        const size_t total = (size_t)a.npart;
+#pragma unroll
+        for (int cpt = 0; cpt < 3; ++cpt) a.vstate[cpt * total + e.q] = a.psi_out[cpt * total + e.q];
+      }
     }
   }
 }
@@ -502,6 +540,12 @@ template <int N> struct Cfg {
   static constexpr size_t smem_z = (xz > fz ? xz : fz) + (size_t)E * P * 8;
   static constexpr int threads_xy = TC * P;
   static constexpr int threads_z = 3 * LINES * P;
+  // with the displacement fields: five pairs per line, half as many lines
+  static constexpr int LINES_V = LINES >= 2 ? LINES / 2 : 1;
+  static constexpr size_t xzv = (size_t)XLayoutLines<E, P, 5 * LINES_V>::kSize * 8;
+  static constexpr size_t fzv = (size_t)LINES_V * 10 * (N + (P >= 2 ? P / 2 : 1)) * 4;
+  static constexpr size_t smem_zv = (xzv > fzv ? xzv : fzv) + (size_t)E * P * 8;
+  static constexpr int threads_zv = 5 * LINES_V * P;
 };
 
 template <int N>
@@ -510,11 +554,15 @@ static cudaError_t set_attrs() {
   cudaError_t e;
   e = cudaFuncSetAttribute(k_pass_x<N, C::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pass_y<N, C::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
+  e = cudaFuncSetAttribute(k_pass_y<N, C::TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
+  e = cudaFuncSetAttribute(k_pass_y<N, C::TC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_pass_z<N, C::LINES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
+  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES_V, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_zv);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_pass_z<N, C::LINES, true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
 }
 
 template <int N>
@@ -548,8 +596,15 @@ template <int N>
 static cudaError_t run_y(const ArgsY& a, cudaStream_t st) {
   using C = Cfg<N>;
   const long ntiles = (long)N * a.batch * ((a.nhp + C::TC - 1) / C::TC);
-  const unsigned grid = persistent_grid(k_pass_y<N, C::TC>, C::threads_xy, C::smem_xy, ntiles);
-  k_pass_y<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
+  bool dual = false;
+  for (int o = 0; o < a.nout; ++o) dual = dual || a.dst2[o] != nullptr;
+  if (dual) {
+    const unsigned grid = persistent_grid(k_pass_y<N, C::TC, true>, C::threads_xy, C::smem_xy, ntiles);
+    k_pass_y<N, C::TC, true><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
+  } else {
+    const unsigned grid = persistent_grid(k_pass_y<N, C::TC, false>, C::threads_xy, C::smem_xy, ntiles);
+    k_pass_y<N, C::TC, false><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -557,9 +612,14 @@ template <int N>
 static cudaError_t run_z(const ArgsZ& a, bool dump, cudaStream_t st) {
   using C = Cfg<N>;
   const long nlines = a.nlines;
+  if (!dump && a.nfields > 6) {
+    const unsigned grid = (unsigned)((nlines + C::LINES_V - 1) / C::LINES_V);
+    k_pass_z<N, C::LINES_V, false, 5><<<grid, C::threads_zv, C::smem_zv, st>>>(a);
+    return cudaGetLastError();
+  }
   const unsigned grid = (unsigned)((nlines + C::LINES - 1) / C::LINES);
-  if (dump) k_pass_z<N, C::LINES, true><<<grid, C::threads_z, C::smem_z, st>>>(a);
-  else k_pass_z<N, C::LINES, false><<<grid, C::threads_z, C::smem_z, st>>>(a);
+  if (dump) k_pass_z<N, C::LINES, true, 3><<<grid, C::threads_z, C::smem_z, st>>>(a);
+  else k_pass_z<N, C::LINES, false, 3><<<grid, C::threads_z, C::smem_z, st>>>(a);
   return cudaGetLastError();
 }
 

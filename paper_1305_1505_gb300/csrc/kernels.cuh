@@ -16,7 +16,7 @@
 
 namespace pin {
 
-constexpr int kMaxFields = 6;
+constexpr int kMaxFields = 9;
 
 // x pass: for each output f, dst[f] = IDFT_x(mult[xm[f]] * src).  The source
 // tiles arrive by TMA: tm is a 2D map over src, {N*nhp columns, batch*N rows}
@@ -47,6 +47,10 @@ struct ArgsY {
   int ym[kMaxFields];
   int zm[kMaxFields];
   int muli[kMaxFields];
+  // optional second store of the same transform with its own z factor
+  float2* dst2[kMaxFields];
+  int zm2[kMaxFields];
+  int muli2[kMaxFields];
   int nout;
   const float* mult;
   const float2* tw;
@@ -76,8 +80,10 @@ struct ArgsZ {
   int npart;     // batch * N^3 particles
   const float2* tw;
   int nhp;
-  // eigenvalue mode
+  // eigenvalue mode (nfields 6), plus the displacement components (nfields 9)
   float* lam_out;
+  float* psi_out;   // [3][npart] smoothed displacement of this radius
+  float* vstate;    // [3][npart] displacement at R_max, or null
   // root and redo kernels
   float* fmax;
   int* idx;

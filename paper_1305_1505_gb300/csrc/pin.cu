@@ -26,6 +26,7 @@ using namespace pin;
 struct pin_plan_s {
   int n = 0, nhp = 0, nscales = 0, correction = 1, precision = 0;
   int batch = 1;          // realisations sharing the grid and radii
+  bool velocities = false; // keep the smoothed displacement at R_max (v_max)
   double box = 0.0;
   std::vector<double> radii;
   int device = 0;
@@ -36,7 +37,9 @@ struct pin_plan_s {
   size_t field_elems = 0; // batch * spec_elems: one field of every realisation
   float2* phi0 = nullptr;
   float2* U = nullptr;    // 3 spectra
-  float2* V = nullptr;    // 6 spectra
+  float2* V = nullptr;    // 6 spectra (9 with velocities)
+  float* psi = nullptr;   // [3][npart] displacement of the current radius (velocities)
+  float* vstate = nullptr;  // [3][npart] displacement at R_max (velocities)
   float* fmax = nullptr;
   int* idx = nullptr;
   float* mult = nullptr;  // (nscales + 1) x 3 x n; the last set has R = 0
@@ -113,6 +116,7 @@ bool validate(const pin_plan_desc* d, std::string* why) {
     if (!(d->radii[s] >= 0.0) || !std::isfinite(d->radii[s])) { *why = "radii must be finite and >= 0"; return false; }
   if (d->correction != PIN_CORR_NONE && d->correction != PIN_CORR_SPHERE) { *why = "bad correction mode"; return false; }
   if (d->precision != PIN_FP32_FALLBACK64) { *why = "bad precision mode"; return false; }
+  if (d->velocities != 0 && d->velocities != 1) { *why = "velocities must be 0 or 1"; return false; }
   const long long b = d->batch <= 0 ? 1 : d->batch;
   if (b > 4096) { *why = "batch must be in 1..4096"; return false; }
   if (b * (long long)d->nx * d->nx * d->nx >= (1ll << 31)) { *why = "batch * N^3 must stay below 2^31"; return false; }
@@ -127,10 +131,11 @@ unsigned redo_capacity(int n, int batch) {
 
 int batch_of(const pin_plan_desc* d) { return d->batch <= 0 ? 1 : d->batch; }
 
-size_t footprint(int n, int nscales, int batch) {
+size_t footprint(int n, int nscales, int batch, bool velocities) {
   const size_t spec = (size_t)n * n * padded_half(n) * batch;
   const size_t n3 = (size_t)n * n * n * batch;
-  return spec * 8 * 10 + n3 * 8 + (size_t)(nscales + 1) * 3 * n * 4 + (size_t)n * 8 + 64 +
+  return spec * 8 * (velocities ? 13 : 10) + n3 * 8 + (velocities ? n3 * 24 : 0) +
+         (size_t)(nscales + 1) * 3 * n * 4 + (size_t)n * 8 + 64 +
          (size_t)redo_capacity(n, batch) * sizeof(RedoEntry) + 16 + sizeof(int);
 }
 
@@ -205,6 +210,8 @@ void release(pin_plan_t p) {
   cudaFree(p->phi0);
   cudaFree(p->U);
   cudaFree(p->V);
+  cudaFree(p->psi);
+  cudaFree(p->vstate);
   cudaFree(p->fmax);
   cudaFree(p->idx);
   cudaFree(p->mult);
@@ -258,6 +265,19 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
     ay.zm[o] = zm[o];
     ay.muli[o] = 0;
   }
+  if (p->velocities && !dump) {
+    // smoothed displacement psi = i k W Phi0 shares the y transforms of
+    // xz (psi_x: z factor W), zz (psi_z: z factor k W) and yz (psi_y: z factor W)
+    ay.dst2[2] = spec(p, p->V, 6);
+    ay.zm2[2] = 0;
+    ay.muli2[2] = 1;
+    ay.dst2[4] = spec(p, p->V, 8);
+    ay.zm2[4] = 1;
+    ay.muli2[4] = 1;
+    ay.dst2[5] = spec(p, p->V, 7);
+    ay.zm2[5] = 0;
+    ay.muli2[5] = 1;
+  }
   ay.nout = 6;
   ay.mult = mult;
   ay.tw = p->tw;
@@ -268,8 +288,11 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 2], p->stream, cudaEventRecordExternal));
 
   ArgsZ az{};
-  for (int f = 0; f < 6; ++f) az.src[f] = spec(p, p->V, f);
-  az.nfields = 6;
+  const int nf = (p->velocities && !dump) ? 9 : 6;
+  for (int f = 0; f < nf; ++f) az.src[f] = spec(p, p->V, f);
+  az.nfields = nf;
+  az.psi_out = p->psi;
+  az.vstate = (p->velocities && !dump) ? p->vstate : nullptr;
   az.nlines = p->n * p->n * p->batch;
   az.npart = az.nlines * p->n;
   az.lam_out = reinterpret_cast<float*>(p->U);  // the x-pass spectra are free by now
@@ -304,6 +327,7 @@ pin_status enqueue_collapse(pin_plan_t p) {
   const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
   PIN_CK(p, cudaMemsetAsync(p->fmax, 0, n3 * sizeof(float), p->stream));
   PIN_CK(p, cudaMemsetAsync(p->idx, 0xFF, n3 * sizeof(int), p->stream));
+  if (p->velocities) PIN_CK(p, cudaMemsetAsync(p->vstate, 0, 3 * n3 * sizeof(float), p->stream));
   for (int s = 0; s < p->nscales; ++s) {
     pin_status st = enqueue_radius(p, s, s, nullptr);
     if (st != PIN_OK) return st;
@@ -361,7 +385,7 @@ extern "C" {
 size_t pin_footprint_bytes(const pin_plan_desc* d) {
   std::string why;
   if (!validate(d, &why)) return 0;
-  return footprint(d->nx, d->nscales, batch_of(d));
+  return footprint(d->nx, d->nscales, batch_of(d), d->velocities != 0);
 }
 
 pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
@@ -379,6 +403,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   p->correction = d->correction;
   p->precision = d->precision;
   p->batch = batch_of(d);
+  p->velocities = d->velocities != 0;
   p->shape = pass_shape(p->n);
   p->spec_elems = (size_t)p->n * p->n * p->nhp;
   p->field_elems = p->spec_elems * p->batch;
@@ -401,7 +426,9 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   const size_t mult_elems = (size_t)(p->nscales + 1) * 3 * p->n;
   if (cudaMalloc(&p->phi0, p->field_elems * 8) != cudaSuccess ||
       cudaMalloc(&p->U, 3 * p->field_elems * 8) != cudaSuccess ||
-      cudaMalloc(&p->V, 6 * p->field_elems * 8) != cudaSuccess ||
+      cudaMalloc(&p->V, (p->velocities ? 9 : 6) * p->field_elems * 8) != cudaSuccess ||
+      (p->velocities && (cudaMalloc(&p->psi, 3 * n3 * 4) != cudaSuccess ||
+                         cudaMalloc(&p->vstate, 3 * n3 * 4) != cudaSuccess)) ||
       cudaMalloc(&p->fmax, n3 * 4) != cudaSuccess || cudaMalloc(&p->idx, n3 * 4) != cudaSuccess ||
       cudaMalloc(&p->mult, mult_elems * 4) != cudaSuccess ||
       cudaMalloc(&p->tw, (size_t)p->n * 8) != cudaSuccess ||
@@ -471,6 +498,19 @@ pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, in
   PIN_CK(p, cudaMemcpyAsync(F_max, p->fmax, n3 * 4, kind, p->stream));
   PIN_CK(p, cudaMemcpyAsync(scale_idx, p->idx, n3 * 4, kind, p->stream));
   p->calls++;
+  if (!on_device) return finish_host(p);
+  return PIN_OK;
+}
+
+pin_status pin_velocities(pin_plan_t p, float* psi_max, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!psi_max) return fail(p, PIN_EINVAL, "null output");
+  if (!p->velocities) return fail(p, PIN_EINVAL, "the plan was created without velocities");
+  if (p->calls == 0) return fail(p, PIN_ESTATE, "pin_collapse_times has not been called");
+  const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
+  PIN_CK(p, cudaMemcpyAsync(psi_max, p->vstate, 3 * n3 * 4,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
   if (!on_device) return finish_host(p);
   return PIN_OK;
 }

@@ -35,7 +35,7 @@ class pin_plan_desc(ctypes.Structure):
                 ("box", ctypes.c_double), ("nscales", ctypes.c_int),
                 ("radii", ctypes.POINTER(ctypes.c_double)), ("correction", ctypes.c_int),
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("batch", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("velocities", ctypes.c_int)]
 
 
 class pin_stats(ctypes.Structure):
@@ -46,7 +46,7 @@ class pin_stats(ctypes.Structure):
 # every symbol include/pin.h declares
 EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_hessian",
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
-           "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc",
+           "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
            "pin_strerror", "pin_last_error", "pin_destroy")
 
 _lib = None
@@ -71,6 +71,8 @@ def load(path=None):
     L.pin_set_ic.restype = ctypes.c_int
     L.pin_collapse_times.argtypes = [P, P, P, ctypes.c_int]
     L.pin_collapse_times.restype = ctypes.c_int
+    L.pin_velocities.argtypes = [P, P, ctypes.c_int]
+    L.pin_velocities.restype = ctypes.c_int
     L.pin_hessian.argtypes = [P, ctypes.c_int, P, ctypes.c_int]
     L.pin_hessian.restype = ctypes.c_int
     L.pin_displacements.argtypes = [P, P, ctypes.c_int]
@@ -114,11 +116,12 @@ def _check(status, plan=None):
         raise PinError(status, msg)
 
 
-def make_desc(n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1):
+def make_desc(n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1, velocities=False):
     r = np.ascontiguousarray(radii, dtype=np.float64)
     d = pin_plan_desc(n, n, n, float(box), int(r.size),
                       r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(correction),
-                      PIN_FP32_FALLBACK64, ctypes.c_void_p(stream) if stream else None, int(batch))
+                      PIN_FP32_FALLBACK64, ctypes.c_void_p(stream) if stream else None, int(batch),
+                      1 if velocities else 0)
     d._radii_keepalive = r
     return d
 
@@ -143,6 +146,10 @@ def pin_set_ic(plan, delta_k_ptr, dtype, on_device):
 def pin_collapse_times(plan, fmax_ptr, idx_ptr, on_device):
     _check(load().pin_collapse_times(plan, ctypes.c_void_p(fmax_ptr), ctypes.c_void_p(idx_ptr),
                                      int(on_device)), plan)
+
+
+def pin_velocities(plan, out_ptr, on_device):
+    _check(load().pin_velocities(plan, ctypes.c_void_p(out_ptr), int(on_device)), plan)
 
 
 def pin_hessian(plan, scale, out_ptr, on_device):
@@ -209,7 +216,8 @@ def pin_destroy(plan):
 class Plan:
     """Owns one pin plan; methods take torch tensors (device or host)."""
 
-    def __init__(self, n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1):
+    def __init__(self, n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1,
+                 velocities=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("pin needs a CUDA device; none is available")
@@ -218,7 +226,7 @@ class Plan:
         self.batch = int(batch)
         self.radii = np.ascontiguousarray(radii, dtype=np.float64)
         s = stream.cuda_stream if stream is not None else None
-        self._desc = make_desc(self.n, self.box, self.radii, correction, s, self.batch)
+        self._desc = make_desc(self.n, self.box, self.radii, correction, s, self.batch, velocities)
         self.handle = pin_plan(self._desc)
 
     def __del__(self):
@@ -271,6 +279,17 @@ class Plan:
         if sync and fmax.is_cuda:
             self.sync()
         return fmax, idx
+
+    def velocities(self):
+        """(3, [batch,] n, n, n) displacement at R_max of the last collapse_times."""
+        import torch
+        n = self.n
+        shape = (3, n, n, n) if self.batch == 1 else (3, self.batch, n, n, n)
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        pin_velocities(self.handle, out.data_ptr(), 1)
+        self.sync()
+        return out
 
     def hessian(self, scale):
         import torch

@@ -417,3 +417,38 @@ def test_multi_point_direct_sum_matches_fft_path():
     got = oracle.hessian_points(d, box, radius, q)
     ref = h.reshape(6, -1)[:, q].T
     assert np.abs(got - ref).max() < 1e-12 * np.abs(h).max()
+
+
+@pytest.mark.parametrize("radius", [0.0, 3.0])
+def test_smoothed_displacement_single_mode(radius):
+    """psi_R = i k W(kR) delta / k^2: one mode gives the unsmoothed closed form
+    times exp(-k^2 R^2 / 2)."""
+    n, box = 8, 40.0
+    d = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    amp = 0.4 + 0.9j
+    d[1, 2, 3] = amp
+    psi = oracle.displacement(d, box, radius)
+    s = [1, 2, 3]
+    kf = 2 * np.pi / box
+    k = kf * np.array(s, dtype=float)
+    k2 = k @ k
+    q = np.indices((n, n, n))
+    phase = 2 * np.pi * (s[0] * q[0] + s[1] * q[1] + s[2] * q[2]) / n
+    wave = -2 * np.imag(amp * np.exp(1j * phase)) / n ** 3 * np.exp(-0.5 * k2 * radius ** 2)
+    for c in range(3):
+        assert np.abs(psi[c] - k[c] / k2 * wave).max() < 1e-15 + 1e-12 * np.abs(wave).max()
+
+
+def test_vmax_is_displacement_at_the_argmax_radius():
+    n, box = 8, 50.0
+    d = _field(n, box, 23)
+    radii = ic.log_radii(box / n, 12.0, 4)
+    out = oracle.collapse_times(d, box, radii, velocities=True)
+    v = out["vmax"].reshape(3, -1)
+    for q in (0, 100, 300, 511):
+        s = out["idx"][q]
+        if s < 0:
+            assert np.all(v[:, q] == 0)
+        else:
+            ref = oracle.displacement(d, box, radii[s]).reshape(3, -1)[:, q]
+            assert np.allclose(v[:, q], ref, rtol=0, atol=1e-15)
