@@ -125,22 +125,37 @@ template <int N> struct DFT {
 };
 
 // Per-size decomposition N = E * P of a line (E register slots per thread,
-// P threads per line, P divides E so that level 2 hands each thread E/P
-// whole length-P transforms).
-template <int N> struct Shape;
-template <> struct Shape<8>    { static constexpr int E = 8,  P = 1; };
-template <> struct Shape<16>   { static constexpr int E = 16, P = 1; };
-template <> struct Shape<32>   { static constexpr int E = 8,  P = 4; };
-template <> struct Shape<48>   { static constexpr int E = 12, P = 4; };
-template <> struct Shape<64>   { static constexpr int E = 8,  P = 8; };
-template <> struct Shape<96>   { static constexpr int E = 24, P = 4; };
-template <> struct Shape<128>  { static constexpr int E = 16, P = 8; };
-template <> struct Shape<192>  { static constexpr int E = 24, P = 8; };
-template <> struct Shape<256>  { static constexpr int E = 16, P = 16; };
-template <> struct Shape<384>  { static constexpr int E = 48, P = 8; };
-template <> struct Shape<512>  { static constexpr int E = 32, P = 16; };
-template <> struct Shape<768>  { static constexpr int E = 48, P = 16; };
-template <> struct Shape<1024> { static constexpr int E = 64, P = 16; };
+// P threads per line).  Two levels (P2 == 1): P divides E, so that level 2
+// hands each thread E/P whole length-P transforms.  Three levels (P2 > 1,
+// P = P1 * P2): the length-P transforms are themselves split into a length-P2
+// stage and a length-P1 stage with a second exchange, so that E, and with it
+// the registers a thread holds, stays small (P1 and P2 divide E).
+template <int N> struct ShapeBase;
+template <> struct ShapeBase<8>    { static constexpr int E = 8,  P1 = 1, P2 = 1; };
+template <> struct ShapeBase<16>   { static constexpr int E = 16, P1 = 1, P2 = 1; };
+template <> struct ShapeBase<32>   { static constexpr int E = 8,  P1 = 4, P2 = 1; };
+template <> struct ShapeBase<48>   { static constexpr int E = 12, P1 = 4, P2 = 1; };
+template <> struct ShapeBase<64>   { static constexpr int E = 8,  P1 = 8, P2 = 1; };
+template <> struct ShapeBase<96>   { static constexpr int E = 24, P1 = 4, P2 = 1; };
+template <> struct ShapeBase<128>  { static constexpr int E = 16, P1 = 8, P2 = 1; };
+template <> struct ShapeBase<192>  { static constexpr int E = 24, P1 = 8, P2 = 1; };
+template <> struct ShapeBase<256>  { static constexpr int E = 16, P1 = 16, P2 = 1; };
+template <> struct ShapeBase<384>  { static constexpr int E = 48, P1 = 8, P2 = 1; };
+template <> struct ShapeBase<512>  { static constexpr int E = 32, P1 = 16, P2 = 1; };
+#ifndef PIN_768_TWO_LEVEL
+template <> struct ShapeBase<768>  { static constexpr int E = 24, P1 = 4, P2 = 8; };
+#else
+template <> struct ShapeBase<768>  { static constexpr int E = 48, P1 = 16, P2 = 1; };
+#endif
+template <int N> struct Shape : ShapeBase<N> {
+  static constexpr int E = ShapeBase<N>::E, P1 = ShapeBase<N>::P1, P2 = ShapeBase<N>::P2;
+  static constexpr int P = P1 * P2;
+  // twiddles: w_N^{p k1} ([k1][p], E*P = N entries), then for three levels
+  // w_P^{p1 k2a} ([k2a][p1], P entries)
+  static constexpr int kTw = E * P + (P2 > 1 ? P : 0);
+  static_assert(E * P == N, "shape must cover the line");
+  static_assert(E % P1 == 0 && E % P2 == 0, "stage lengths must divide E");
+};
 
 // Shared-memory layouts for the level-1 -> level-2 exchange of one tile of
 // lines.  Index of value (k1, p) of line c.
@@ -149,19 +164,41 @@ template <> struct Shape<1024> { static constexpr int E = 64, P = 16; };
 //  - Contiguous lines (pass along z): consecutive lanes are consecutive p of
 //    one line, layout [c][k1][p] with the p extent padded to P+1 so that the
 //    level-2 reads (stride P+1) do not collide on a bank.
-template <int E, int P, int TC>
+// at(k1, p, c): exchange after level 1; at2(k1, k2a, p1, c): second exchange
+// of the three-level form (P = P1 P2).
+template <int E, int P, int TC, int P1 = P>
 struct XLayoutCols {
+  static constexpr int P2 = P / P1;
   static constexpr int kSize = E * P * TC;
   __device__ __forceinline__ static int at(int k1, int p, int c) { return (k1 * P + p) * TC + c; }
+  __device__ __forceinline__ static int at2(int k1, int k2a, int p1, int c) {
+    return ((k1 * P2 + k2a) * P1 + p1) * TC + c;
+  }
 };
-template <int E, int P, int NC>
+template <int E, int P, int NC, int P1 = P>
 struct XLayoutLines {
-  // per-line stride padded to P (mod 16) float2, so that the 32/P lines of a
-  // warp (each 2P banks wide) tile the 32 banks
+  static constexpr int P2 = P / P1;
+  // two levels: per-line stride padded to P (mod 16) float2, so that the 32/P
+  // lines of a warp (each 2P banks wide) tile the 32 banks
   static constexpr int kLine0 = E * (P + 1);
-  static constexpr int kLine = P >= 16 ? kLine0 : kLine0 + ((P - kLine0 % 16) % 16 + 16) % 16;
+  static constexpr int kLine2 = P >= 16 ? kLine0 : kLine0 + ((P - kLine0 % 16) % 16 + 16) % 16;
+  // three levels (one line per warp, lanes p = p1 + P1 q): rows of the first
+  // exchange are S1 >= P float2 with S1 = P1 (mod 16), so lanes (q, p1) of a
+  // level-2 read spread over the banks; the second exchange is [k2a][k1][p1]
+  // with a row of S2 = 1 (mod 16) float2 per k2a, so both its writes (lanes
+  // (q, p1)) and its level-3 reads (lanes (k1, k2a)) spread too.
+  static constexpr int S1 = P + ((P1 - P % 16) % 16 + 16) % 16;
+  static constexpr int S2 = E * P1 + ((1 - (E * P1) % 16) % 16 + 16) % 16;
+  static constexpr int kLine3 = (E * S1 > P2 * S2) ? E * S1 : P2 * S2;
+  static constexpr int kLine = P2 > 1 ? kLine3 : kLine2;
   static constexpr int kSize = NC * kLine;
-  __device__ __forceinline__ static int at(int k1, int p, int c) { return c * kLine + k1 * (P + 1) + p; }
+  __device__ __forceinline__ static int at(int k1, int p, int c) {
+    if constexpr (P2 > 1) return c * kLine + k1 * S1 + p;
+    else return c * kLine + k1 * (P + 1) + p;
+  }
+  __device__ __forceinline__ static int at2(int k1, int k2a, int p1, int c) {
+    return c * kLine + k2a * S2 + k1 * P1 + p1;
+  }
 };
 
 // Level-2 twiddles w_N^{p k1}, laid out [k1][p] in shared memory.
@@ -169,16 +206,60 @@ template <int E, int P>
 __device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { return s_tw[k1 * P + p]; }
 
 // Inverse FFT of one line held as v[t] = x[p + P t] by thread p of the line.
-// On return v[i * P + k2] = X[(p + P i) + E k2] for i in [0, E/P), k2 in [0, P)
-// (for P == 1: v[k] = X[k]).  All threads of the block must call it; it
-// synchronises once inside and leaves the exchange buffer in use (callers
-// synchronise before writing s_x again).
+// Two levels: on return v[i * P + k2] = X[(p + P i) + E k2] for i in [0, E/P),
+// k2 in [0, P) (for P == 1: v[k] = X[k]).  Three levels (P = P1 P2, with
+// p = p1 + P1 q): X[k1 + E (k2a + P2 k2b)] = sum_p1 w_P1^{p1 k2b} w_P^{p1 k2a}
+// sum_p2 w_P2^{p2 k2a} w_N^{p k1} Y_p[k1], Y_p the level-1 DFT of thread p;
+// on return v[m P1 + k2b] holds the pair (k1, k2a) = divmod(p + P m, P2).
+// fft_out_index gives the frequency of each slot.  All threads of the block
+// must call it; it synchronises once (twice more for three levels) and leaves
+// the exchange buffer in use (callers synchronise before writing s_x again).
 template <int N, class Layout>
 __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c, float2* s_x,
                                          const float2* s_tw) {
-  constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  constexpr int E = Shape<N>::E, P = Shape<N>::P, P1 = Shape<N>::P1, P2 = Shape<N>::P2;
   DFT<E>::run(v);
-  if constexpr (P > 1) {
+  if constexpr (P2 > 1) {
+    // level 1 done; twiddle w_N^{p k1} and first exchange
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) {
+      float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P>(s_tw, k1, p));
+      s_x[Layout::at(k1, p, c)] = z;
+    }
+    __syncthreads();
+    // level 2: for k1 = q + P2 i, the length-P2 DFT over p2 of Z[k1][p1 + P1 p2],
+    // then the twiddle w_P^{p1 k2a}
+    const int p1 = p % P1, q = p / P1;
+    const float2* s_twb = s_tw + E * P;
+#pragma unroll
+    for (int i = 0; i < E / P2; ++i) {
+      float2 t[P2];
+#pragma unroll
+      for (int j = 0; j < P2; ++j) t[j] = s_x[Layout::at(q + P2 * i, p1 + P1 * j, c)];
+      DFT<P2>::run(t);
+#pragma unroll
+      for (int k2a = 0; k2a < P2; ++k2a)
+        v[i * P2 + k2a] = (k2a == 0) ? t[k2a] : cmul(t[k2a], s_twb[k2a * P1 + p1]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < E / P2; ++i)
+#pragma unroll
+      for (int k2a = 0; k2a < P2; ++k2a) s_x[Layout::at2(q + P2 * i, k2a, p1, c)] = v[i * P2 + k2a];
+    __syncthreads();
+    // level 3: pairs (k1, k2a) = divmod(p + P m, P2), the length-P1 DFT over p1
+#pragma unroll
+    for (int m = 0; m < E / P1; ++m) {
+      const int pi = p + P * m;
+      const int k1 = pi / P2, k2a = pi % P2;
+      float2 t[P1];
+#pragma unroll
+      for (int r = 0; r < P1; ++r) t[r] = s_x[Layout::at2(k1, k2a, r, c)];
+      DFT<P1>::run(t);
+#pragma unroll
+      for (int k2b = 0; k2b < P1; ++k2b) v[m * P1 + k2b] = t[k2b];
+    }
+  } else if constexpr (P > 1) {
 #pragma unroll
     for (int k1 = 0; k1 < E; ++k1) {
       float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P>(s_tw, k1, p));
@@ -202,8 +283,12 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c,
 // Output frequency of register slot j after fft_line.
 template <int N>
 __device__ __forceinline__ int fft_out_index(int p, int j) {
-  constexpr int E = Shape<N>::E, P = Shape<N>::P;
-  if constexpr (P == 1) {
+  constexpr int E = Shape<N>::E, P = Shape<N>::P, P1 = Shape<N>::P1, P2 = Shape<N>::P2;
+  if constexpr (P2 > 1) {
+    const int m = j / P1, k2b = j % P1;
+    const int pi = p + P * m;
+    return pi / P2 + E * (pi % P2 + P2 * k2b);
+  } else if constexpr (P == 1) {
     (void)p;
     return j;
   } else {

@@ -100,8 +100,14 @@ template <int N> struct Stage {
 #ifndef PIN_Z_ILP
 #define PIN_Z_ILP 2
 #endif
+#ifndef PIN_Z_MINB3
+#define PIN_Z_MINB3 4
+#endif
+// Three-level lines hold half the registers per thread: the z pass is sized
+// for more resident blocks.
 template <int N> struct MinBlocks {
-  static constexpr int xy = N >= 384 ? PIN_XY_MINB : 1, z = N >= 384 ? PIN_Z_MINB : 1;
+  static constexpr int xy = N >= 384 ? PIN_XY_MINB : 1;
+  static constexpr int z = Shape<N>::P2 > 1 ? PIN_Z_MINB3 : (N >= 384 ? PIN_Z_MINB : 1);
 };
 
 // ---------------------------------------------------------------- x pass --
@@ -112,21 +118,21 @@ template <int N> struct MinBlocks {
 // the current one into registers.
 template <int N, int TC>
 __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(const __grid_constant__ ArgsX a) {
-  constexpr int E = Shape<N>::E, P = Shape<N>::P;
-  using L = XLayoutCols<E, P, TC>;
+  constexpr int E = Shape<N>::E, P = Shape<N>::P, NTW = Shape<N>::kTw;
+  using L = XLayoutCols<E, P, TC, Shape<N>::P1>;
   using G = Stage<N>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // staged tile [N][TC]; TMA destinations start on a 128-byte boundary
   float2* s_st = reinterpret_cast<float2*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
   float2* s_x = s_st + N * TC;
   float2* s_tw = s_x + L::kSize;
-  float* s_m = reinterpret_cast<float*>(s_tw + E * P);  // [3][N] multipliers
+  float* s_m = reinterpret_cast<float*>(s_tw + NTW);  // [3][N] multipliers
   __shared__ __align__(8) unsigned long long s_bar;
   __shared__ float2* s_dst[3];
   __shared__ int s_xm[3];
   const int tid = threadIdx.x, c = tid % TC, p = tid / TC;
   const uint32_t bar = smem_u32(&s_bar);
-  for (int i = tid; i < E * P; i += TC * P) s_tw[i] = a.tw[i];
+  for (int i = tid; i < NTW; i += TC * P) s_tw[i] = a.tw[i];
   for (int i = tid; i < 3 * N; i += TC * P) s_m[i] = a.mult[i];
   if (tid < 3) {
     s_dst[tid] = a.dst[tid];
@@ -184,14 +190,14 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(co
 // zero-filled by the tensor map and not stored.
 template <int N, int TC, bool DUAL>
 __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(const __grid_constant__ ArgsY a) {
-  constexpr int E = Shape<N>::E, P = Shape<N>::P;
-  using L = XLayoutCols<E, P, TC>;
+  constexpr int E = Shape<N>::E, P = Shape<N>::P, NTW = Shape<N>::kTw;
+  using L = XLayoutCols<E, P, TC, Shape<N>::P1>;
   using G = Stage<N>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* s_st = reinterpret_cast<float2*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
   float2* s_x = s_st + N * TC;
   float2* s_tw = s_x + L::kSize;
-  float* s_m = reinterpret_cast<float*>(s_tw + E * P);
+  float* s_m = reinterpret_cast<float*>(s_tw + NTW);
   __shared__ __align__(8) unsigned long long s_bar;
   __shared__ float2* s_dst[kMaxFields];
   __shared__ float2* s_dst2[kMaxFields];
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
   __shared__ int s_zm2[kMaxFields], s_mi2[kMaxFields];
   const int tid = threadIdx.x, c = tid % TC, p = tid / TC;
   const uint32_t bar = smem_u32(&s_bar);
-  for (int i = tid; i < E * P; i += TC * P) s_tw[i] = a.tw[i];
+  for (int i = tid; i < NTW; i += TC * P) s_tw[i] = a.tw[i];
   for (int i = tid; i < 3 * N; i += TC * P) s_m[i] = a.mult[i];
   if (tid < kMaxFields) {
     s_dst[tid] = a.dst[tid];
@@ -291,10 +297,10 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
 // smoothed displacement components, kept for the velocity at R_max).
 template <int N, int LINES, bool DUMP, int NP>
 __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_pass_z(ArgsZ a) {
-  constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  constexpr int E = Shape<N>::E, P = Shape<N>::P, NTW = Shape<N>::kTw;
   constexpr int NC = NP * LINES;  // pair-columns of the block
   constexpr int NF = 2 * NP;      // field slots per line
-  using L = XLayoutLines<E, P, NC>;
+  using L = XLayoutLines<E, P, NC, Shape<N>::P1>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* s_x = reinterpret_cast<float2*>(smem_raw);
   // field lines padded by P/2 floats so that the pair-columns of a warp
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
   float* s_f = reinterpret_cast<float*>(smem_raw);
   const int nthreads = NC * P;
   const int tid = threadIdx.x;
-  for (int i = tid; i < E * P; i += nthreads) s_tw[i] = a.tw[i];
+  for (int i = tid; i < NTW; i += nthreads) s_tw[i] = a.tw[i];
   __syncthreads();
 
   const int npairs = (a.nfields + 1) / 2;
@@ -525,26 +531,26 @@ cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st) {
 // -------------------------------------------------------------- dispatch --
 
 template <int N> struct Cfg {
-  static constexpr int E = Shape<N>::E, P = Shape<N>::P;
+  static constexpr int E = Shape<N>::E, P = Shape<N>::P, P1 = Shape<N>::P1, NTW = Shape<N>::kTw;
   // columns per x/y tile (a TMA box row is TC x 8 bytes)
 #ifndef PIN_TC_LONG
 #define PIN_TC_LONG 16
 #endif
   static constexpr int TC = P >= 16 ? PIN_TC_LONG : (P >= 8 ? 16 : (P == 4 ? 32 : 64));
-  static constexpr int LINES = 64 / P;
+  static constexpr int LINES = P >= 64 ? 1 : 64 / P;
   // staged tile + exchange + twiddles + multipliers + alignment slack
-  static constexpr size_t smem_xy = (size_t)N * TC * 8 + (size_t)XLayoutCols<E, P, TC>::kSize * 8 +
-                                    (size_t)E * P * 8 + (size_t)3 * N * 4 + 128;
-  static constexpr size_t xz = (size_t)XLayoutLines<E, P, 3 * LINES>::kSize * 8;
+  static constexpr size_t smem_xy = (size_t)N * TC * 8 + (size_t)XLayoutCols<E, P, TC, P1>::kSize * 8 +
+                                    (size_t)NTW * 8 + (size_t)3 * N * 4 + 128;
+  static constexpr size_t xz = (size_t)XLayoutLines<E, P, 3 * LINES, P1>::kSize * 8;
   static constexpr size_t fz = (size_t)LINES * 6 * (N + (P >= 2 ? P / 2 : 1)) * 4;
-  static constexpr size_t smem_z = (xz > fz ? xz : fz) + (size_t)E * P * 8;
+  static constexpr size_t smem_z = (xz > fz ? xz : fz) + (size_t)NTW * 8;
   static constexpr int threads_xy = TC * P;
   static constexpr int threads_z = 3 * LINES * P;
   // with the displacement fields: five pairs per line, half as many lines
   static constexpr int LINES_V = LINES >= 2 ? LINES / 2 : 1;
-  static constexpr size_t xzv = (size_t)XLayoutLines<E, P, 5 * LINES_V>::kSize * 8;
+  static constexpr size_t xzv = (size_t)XLayoutLines<E, P, 5 * LINES_V, P1>::kSize * 8;
   static constexpr size_t fzv = (size_t)LINES_V * 10 * (N + (P >= 2 ? P / 2 : 1)) * 4;
-  static constexpr size_t smem_zv = (xzv > fzv ? xzv : fzv) + (size_t)E * P * 8;
+  static constexpr size_t smem_zv = (xzv > fzv ? xzv : fzv) + (size_t)NTW * 8;
   static constexpr int threads_zv = 5 * LINES_V * P;
 };
 
@@ -568,7 +574,8 @@ static cudaError_t set_attrs() {
 template <int N>
 static PassShape shape_of() {
   using C = Cfg<N>;
-  return PassShape{C::E, C::P, C::TC, C::LINES, C::smem_xy, C::smem_z, C::threads_xy, C::threads_z};
+  return PassShape{C::E, C::P, Shape<N>::P1, Shape<N>::P2, C::TC, C::LINES, C::smem_xy, C::smem_z,
+                   C::threads_xy, C::threads_z};
 }
 
 // Persistent grid: as many blocks as fit on the device at once, at most one

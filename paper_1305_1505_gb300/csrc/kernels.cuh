@@ -28,7 +28,7 @@ struct ArgsX {
   int xm[3];
   int nout;
   const float* mult;  // [3][N] multipliers of this radius (W, kW, k^2W, each / N)
-  const float2* tw;   // level-2 twiddles [E][P]
+  const float2* tw;   // twiddles: w_N^{p k1} [E][P], then w_P^{p1 k2a} [P2][P1] for three levels
   int nhp;
   int batch;          // realisations stacked back to back (same N, radii)
   int* err;           // set to 1 if a TMA wait gave up (bounded wait)
@@ -103,6 +103,7 @@ struct ArgsZ {
 
 struct PassShape {
   int E, P;
+  int P1, P2;     // P = P1 * P2; P2 > 1: three-level line transform
   int tc;         // columns per block, x/y passes
   int lines;      // lines per block, z pass
   size_t smem_xy; // dynamic shared bytes, x/y passes

@@ -431,7 +431,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
                          cudaMalloc(&p->vstate, 3 * n3 * 4) != cudaSuccess)) ||
       cudaMalloc(&p->fmax, n3 * 4) != cudaSuccess || cudaMalloc(&p->idx, n3 * 4) != cudaSuccess ||
       cudaMalloc(&p->mult, mult_elems * 4) != cudaSuccess ||
-      cudaMalloc(&p->tw, (size_t)p->n * 8) != cudaSuccess ||
+      cudaMalloc(&p->tw, ((size_t)p->n + p->shape.P) * 8) != cudaSuccess ||
       cudaMalloc(&p->counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&p->redo_list, (size_t)p->redo_cap * sizeof(RedoEntry)) != cudaSuccess ||
       cudaMalloc(&p->redo_count, sizeof(unsigned)) != cudaSuccess ||
@@ -442,14 +442,21 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   std::vector<float> mult(mult_elems);
   for (int s = 0; s < p->nscales; ++s) fill_mult(mult.data() + (size_t)s * 3 * p->n, p->n, p->box, p->radii[s]);
   fill_mult(mult.data() + (size_t)p->nscales * 3 * p->n, p->n, p->box, 0.0);
-  // level-2 twiddles w_N^{p k1} in [k1][p] order
-  const int E = p->shape.E, P = p->shape.P;
-  std::vector<float2> tw((size_t)p->n);
+  // twiddles w_N^{p k1} in [k1][p] order; for a three-level line (P = P1 P2)
+  // then w_P^{p1 k2a} in [k2a][p1] order
+  const int E = p->shape.E, P = p->shape.P, P1 = p->shape.P1, P2 = p->shape.P2;
+  std::vector<float2> tw((size_t)p->n + (P2 > 1 ? P : 0));
   for (int k1 = 0; k1 < E; ++k1)
     for (int q = 0; q < P; ++q) {
       const double ang = 2.0 * M_PI * (double)((long)q * k1 % p->n) / p->n;
       tw[(size_t)k1 * P + q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
+  if (P2 > 1)
+    for (int k2a = 0; k2a < P2; ++k2a)
+      for (int q1 = 0; q1 < P1; ++q1) {
+        const double ang = 2.0 * M_PI * (double)(q1 * k2a % P) / P;
+        tw[(size_t)p->n + k2a * P1 + q1] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+      }
   if (cudaMemcpy(p->mult, mult.data(), mult_elems * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(p->counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
