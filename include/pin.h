@@ -138,7 +138,9 @@ pin_status pin_sync(pin_plan_t p, int64_t timeout_ns);
 
 pin_status pin_get_stats(pin_plan_t p, pin_stats* out);
 
-/* Number of kernels one pin_collapse_times call launches (for accounting). */
+/* Number of kernels one pin_collapse_times call launches (for accounting):
+ * per radius the x, y and z passes, the root pass unless the z pass of this
+ * grid size computes the collapse times itself (N = 768), and the FP64 redo. */
 int pin_kernels_per_call(pin_plan_t p);
 
 /* Measurement hooks.  pin_profile(p, 1) makes later pin_collapse_times calls
@@ -146,8 +148,10 @@ int pin_kernels_per_call(pin_plan_t p);
  * inside its graph); pin_pass_times() then waits for the plan's work and
  * returns, for the last completed call, the device time in milliseconds summed
  * over radii of: ms4[0] the x pass (filter + transform), ms4[1] the y pass,
- * ms4[2] the z pass (c2r + eigenvalues), ms4[3] the root pass (collapse time
- * + running max) with the FP64 redo of the queued ill-conditioned particles. */
+ * ms4[2] the z pass (c2r + eigenvalues; at N = 768 also the collapse time and
+ * running max), ms4[3] the root pass (collapse time + running max, where it
+ * is a kernel of its own) with the FP64 redo of the queued ill-conditioned
+ * particles. */
 pin_status pin_profile(pin_plan_t p, int enable);
 pin_status pin_pass_times(pin_plan_t p, double* ms4);
 

@@ -212,6 +212,9 @@ __host__ __device__ __forceinline__ T root_kappa(T c1, T c2, T x) {
 //    region; it is positive only if g(0) = -c3 < 0, and the iteration starts at 0.
 // Four iterations reach ~1e-6 relative in FP32 on the coefficient ranges of
 // smoothed Gaussian fields; near-tangent roots are flagged by kappa and redone.
+#ifndef PIN_HALLEY_ITERS
+#define PIN_HALLEY_ITERS 4
+#endif
 template <typename T>
 __host__ __device__ __forceinline__ T largest_root_iter(T c1, T c2, T c3, T& kappa) {
   using F = M<T>;
@@ -230,7 +233,7 @@ __host__ __device__ __forceinline__ T largest_root_iter(T c1, T c2, T c3, T& kap
   // tiny positive value instead of tested: a degenerate step leaves a large
   // last step, which sends the particle to the FP64 redo below.
 #pragma unroll
-  for (int it = 0; it < 4; ++it) {
+  for (int it = 0; it < PIN_HALLEY_ITERS; ++it) {
     const T g = ((x - c1) * x - c2) * x - c3;
     const T dg = (T(3) * x - T(2) * c1) * x - c2;
     const T d2h = T(3) * x - c1;

@@ -140,7 +140,11 @@ template <> struct ShapeBase<96>   { static constexpr int E = 24, P1 = 4, P2 = 1
 template <> struct ShapeBase<128>  { static constexpr int E = 16, P1 = 8, P2 = 1; };
 template <> struct ShapeBase<192>  { static constexpr int E = 24, P1 = 8, P2 = 1; };
 template <> struct ShapeBase<256>  { static constexpr int E = 16, P1 = 16, P2 = 1; };
+#ifndef PIN_384_TWO_LEVEL
+template <> struct ShapeBase<384>  { static constexpr int E = 24, P1 = 4, P2 = 4; };
+#else
 template <> struct ShapeBase<384>  { static constexpr int E = 48, P1 = 8, P2 = 1; };
+#endif
 template <> struct ShapeBase<512>  { static constexpr int E = 32, P1 = 16, P2 = 1; };
 #ifndef PIN_768_TWO_LEVEL
 template <> struct ShapeBase<768>  { static constexpr int E = 24, P1 = 4, P2 = 8; };

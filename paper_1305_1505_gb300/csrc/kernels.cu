@@ -106,7 +106,9 @@ template <int N> struct Stage {
 // Three-level lines hold half the registers per thread: the z pass is sized
 // for more resident blocks.
 template <int N> struct MinBlocks {
-  static constexpr int xy = N >= 384 ? PIN_XY_MINB : 1;
+  // three-level x/y blocks (16 columns x P threads) are sized for 512
+  // resident threads per SM
+  static constexpr int xy = Shape<N>::P2 > 1 ? 32 / Shape<N>::P : (N >= 384 ? PIN_XY_MINB : 1);
   static constexpr int z = Shape<N>::P2 > 1 ? PIN_Z_MINB3 : (N >= 384 ? PIN_Z_MINB : 1);
 };
 
@@ -289,13 +291,25 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
   }
 }
 
+// Stride (floats) of one real field line in the z pass's shared buffer, padded
+// so that the stores of the transform outputs spread over the banks: two-level
+// lines write runs of P consecutive z per pair-column (offset P/2), three-level
+// lines write z = k1 + E (k2a + P2 k2b) (offset 2, so that the two
+// pair-columns of a 16-thread-line warp land on disjoint banks).
+template <int N> __host__ __device__ constexpr int field_stride() {
+  return Shape<N>::P2 > 1 ? N + 2 : N + (Shape<N>::P >= 2 ? Shape<N>::P / 2 : 1);
+}
+
 // ---------------------------------------------------------------- z pass --
 // Lines along z: line index l = x*N + y, the half line src[f][l*nhp + kz],
 // kz in [0, N/2], is contiguous.  Fields are paired (A + iB) into one complex
 // length-N transform whose real and imaginary parts are the two real lines.
 // NP pairs per line: 3 (the six Hessian components) or 5 (plus the three
 // smoothed displacement components, kept for the velocity at R_max).
-template <int N, int LINES, bool DUMP, int NP>
+// FUSE: the collapse time and the running maximum of every particle follow
+// its eigenvalues in this kernel (no eigenvalue round trip through memory);
+// otherwise the eigenvalues go to lam_out for k_roots.
+template <int N, int LINES, bool DUMP, int NP, bool FUSE>
 __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_pass_z(ArgsZ a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P, NTW = Shape<N>::kTw;
   constexpr int NC = NP * LINES;  // pair-columns of the block
@@ -303,9 +317,7 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
   using L = XLayoutLines<E, P, NC, Shape<N>::P1>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* s_x = reinterpret_cast<float2*>(smem_raw);
-  // field lines padded by P/2 floats so that the pair-columns of a warp
-  // (each P floats wide) start on different banks
-  constexpr int kFS = N + (P >= 2 ? P / 2 : 1);
+  constexpr int kFS = field_stride<N>();
   constexpr int kXBytes = L::kSize * 8, kFBytes = LINES * NF * kFS * 4;
   constexpr int kBufBytes = kXBytes > kFBytes ? kXBytes : kFBytes;
   float2* s_tw = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem_raw) + kBufBytes);
@@ -371,43 +383,134 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
       }
     }
     __syncthreads();
-    // eigenvalues of every particle of the block's lines; the collapse time
-    // and the running maximum follow in k_roots, at a higher occupancy than
-    // the long transforms of this kernel allow
     constexpr int kPts = LINES * N;
     const size_t total = (size_t)nlines * N;
-    for (int pt = tid; pt < kPts; pt += nthreads) {
-      const int l = pt / N, z = pt % N;
-      const int gl = blockIdx.x * LINES + l;
-      if (gl >= nlines) continue;
-      float h[6], lam[3];
+    if constexpr (FUSE) {
+      // eigenvalues, collapse time and running maximum, PIN_Z_ILP particles
+      // per thread and iteration
+      constexpr int U = PIN_Z_ILP;
+      const CollapseConsts<float> ccf{a.dcorr_f, a.correction};
+      for (int pt0 = tid; pt0 < kPts; pt0 += U * nthreads) {
+        float lam[U][3], fm[U];
+        bool valid[U];
+        int q[U];
 #pragma unroll
-      for (int f = 0; f < 6; ++f) h[f] = s_f[(l * NF + f) * kFS + z];
-      const float rabs = eig3<float>(h, lam);
-      const int q = gl * N + z;  // < 2^31: checked at plan creation
-      if (rabs > 1.f - a.tau_eig) {
-        atomicAdd(a.counters + 0, 1ull);
-        const unsigned slot = atomicAdd(a.redo_count, 1u);
-        if (slot < a.redo_cap) {
-          RedoEntry e;
-          e.q = q;
+        for (int u = 0; u < U; ++u) {
+          const int pt = pt0 + u * nthreads;
+          const int l = pt / N, z = pt % N;
+          const int gl = blockIdx.x * LINES + l;
+          valid[u] = pt < kPts && gl < nlines;
+          q[u] = gl * N + z;  // < 2^31: checked at plan creation
+          fm[u] = 0.f;
+          lam[u][0] = lam[u][1] = lam[u][2] = 0.f;
+          if (valid[u]) {
+            float h[6];
 #pragma unroll
-          for (int f = 0; f < 6; ++f) e.h[f] = h[f];
-          e.kind = 0;
-          a.redo_list[slot] = e;
-          lam[0] = lam[1] = lam[2] = __int_as_float(0x7fc00000);  // NaN: skipped by k_roots
-        } else {
-          atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 eigenvalues
+            for (int f = 0; f < 6; ++f) h[f] = s_f[(l * NF + f) * kFS + z];
+            const float rabs = eig3<float>(h, lam[u]);
+            fm[u] = a.fmax[q[u]];
+            if (rabs > 1.f - a.tau_eig) {
+              atomicAdd(a.counters + 0, 1ull);
+              const unsigned slot = atomicAdd(a.redo_count, 1u);
+              if (slot < a.redo_cap) {
+                RedoEntry e;
+                e.q = q[u];
+#pragma unroll
+                for (int f = 0; f < 6; ++f) e.h[f] = h[f];
+                e.kind = 0;
+                a.redo_list[slot] = e;
+                if constexpr (NP == 5) {
+#pragma unroll
+                  for (int cpt = 0; cpt < 3; ++cpt)
+                    a.psi_out[cpt * total + q[u]] = s_f[(l * NF + 6 + cpt) * kFS + z];
+                }
+                valid[u] = false;  // the redo kernel updates this particle
+                lam[u][0] = lam[u][1] = lam[u][2] = 0.f;
+              } else {
+                atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 eigenvalues
+              }
+            }
+          }
+        }
+        CollapseState<float> cs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) collapse_main<float>(lam[u], ccf, cs[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (cs[u].need[0] || cs[u].need[1]) collapse_rare<float>(cs[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (!valid[u]) continue;
+          const int pt = pt0 + u * nthreads;
+          const int l = pt / N, z = pt % N;
+          const float F = cs[u].best + cs[u].corr;
+          if (cs[u].kappa < a.tau_root) {
+            atomicAdd(a.counters + 1, 1ull);
+            const unsigned slot = atomicAdd(a.redo_count, 1u);
+            if (slot < a.redo_cap) {
+              RedoEntry e;
+              e.q = q[u];
+              e.h[0] = lam[u][0];
+              e.h[1] = lam[u][1];
+              e.h[2] = lam[u][2];
+              e.h[3] = e.h[4] = e.h[5] = 0.f;
+              e.kind = 1;
+              a.redo_list[slot] = e;
+              if constexpr (NP == 5) {
+#pragma unroll
+                for (int cpt = 0; cpt < 3; ++cpt)
+                  a.psi_out[cpt * total + q[u]] = s_f[(l * NF + 6 + cpt) * kFS + z];
+              }
+              continue;
+            }
+            atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
+          }
+          if (F > fm[u]) {
+            a.fmax[q[u]] = F;
+            a.idx[q[u]] = a.scale;
+            if constexpr (NP == 5) {
+#pragma unroll
+              for (int cpt = 0; cpt < 3; ++cpt) a.vstate[cpt * total + q[u]] = s_f[(l * NF + 6 + cpt) * kFS + z];
+            }
+          }
         }
       }
-      a.lam_out[q] = lam[0];
-      a.lam_out[total + q] = lam[1];
-      a.lam_out[2 * total + q] = lam[2];
-      if constexpr (NP == 5) {
-        // smoothed displacement of this radius, copied to the state by k_roots
-        // when F_max moves here
+    } else {
+      // eigenvalues of every particle of the block's lines; the collapse time
+      // and the running maximum follow in k_roots
+      for (int pt = tid; pt < kPts; pt += nthreads) {
+        const int l = pt / N, z = pt % N;
+        const int gl = blockIdx.x * LINES + l;
+        if (gl >= nlines) continue;
+        float h[6], lam[3];
 #pragma unroll
-        for (int cpt = 0; cpt < 3; ++cpt) a.psi_out[cpt * total + q] = s_f[(l * NF + 6 + cpt) * kFS + z];
+        for (int f = 0; f < 6; ++f) h[f] = s_f[(l * NF + f) * kFS + z];
+        const float rabs = eig3<float>(h, lam);
+        const int q = gl * N + z;  // < 2^31: checked at plan creation
+        if (rabs > 1.f - a.tau_eig) {
+          atomicAdd(a.counters + 0, 1ull);
+          const unsigned slot = atomicAdd(a.redo_count, 1u);
+          if (slot < a.redo_cap) {
+            RedoEntry e;
+            e.q = q;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) e.h[f] = h[f];
+            e.kind = 0;
+            a.redo_list[slot] = e;
+            lam[0] = lam[1] = lam[2] = __int_as_float(0x7fc00000);  // NaN: skipped by k_roots
+          } else {
+            atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 eigenvalues
+          }
+        }
+        a.lam_out[q] = lam[0];
+        a.lam_out[total + q] = lam[1];
+        a.lam_out[2 * total + q] = lam[2];
+        if constexpr (NP == 5) {
+          // smoothed displacement of this radius, copied to the state by k_roots
+          // when F_max moves here
+#pragma unroll
+          for (int cpt = 0; cpt < 3; ++cpt) a.psi_out[cpt * total + q] = s_f[(l * NF + 6 + cpt) * kFS + z];
+        }
       }
     }
   }
@@ -538,18 +641,25 @@ template <int N> struct Cfg {
 #endif
   static constexpr int TC = P >= 16 ? PIN_TC_LONG : (P >= 8 ? 16 : (P == 4 ? 32 : 64));
   static constexpr int LINES = P >= 64 ? 1 : 64 / P;
+  // the root solve runs inside the z pass where its transform leaves the
+  // registers for it (three-level lines)
+#ifndef PIN_Z_FUSE
+  static constexpr bool FUSE = Shape<N>::P2 > 1;
+#else
+  static constexpr bool FUSE = PIN_Z_FUSE != 0;
+#endif
   // staged tile + exchange + twiddles + multipliers + alignment slack
   static constexpr size_t smem_xy = (size_t)N * TC * 8 + (size_t)XLayoutCols<E, P, TC, P1>::kSize * 8 +
                                     (size_t)NTW * 8 + (size_t)3 * N * 4 + 128;
   static constexpr size_t xz = (size_t)XLayoutLines<E, P, 3 * LINES, P1>::kSize * 8;
-  static constexpr size_t fz = (size_t)LINES * 6 * (N + (P >= 2 ? P / 2 : 1)) * 4;
+  static constexpr size_t fz = (size_t)LINES * 6 * field_stride<N>() * 4;
   static constexpr size_t smem_z = (xz > fz ? xz : fz) + (size_t)NTW * 8;
   static constexpr int threads_xy = TC * P;
   static constexpr int threads_z = 3 * LINES * P;
   // with the displacement fields: five pairs per line, half as many lines
   static constexpr int LINES_V = LINES >= 2 ? LINES / 2 : 1;
   static constexpr size_t xzv = (size_t)XLayoutLines<E, P, 5 * LINES_V, P1>::kSize * 8;
-  static constexpr size_t fzv = (size_t)LINES_V * 10 * (N + (P >= 2 ? P / 2 : 1)) * 4;
+  static constexpr size_t fzv = (size_t)LINES_V * 10 * field_stride<N>() * 4;
   static constexpr size_t smem_zv = (xzv > fzv ? xzv : fzv) + (size_t)NTW * 8;
   static constexpr int threads_zv = 5 * LINES_V * P;
 };
@@ -564,11 +674,14 @@ static cudaError_t set_attrs() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_pass_y<N, C::TC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
+  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES, false, 3, C::FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)C::smem_z);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES_V, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_zv);
+  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES_V, false, 5, C::FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)C::smem_zv);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_pass_z<N, C::LINES, true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
+  return cudaFuncSetAttribute(k_pass_z<N, C::LINES, true, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)C::smem_z);
 }
 
 template <int N>
@@ -621,16 +734,25 @@ static cudaError_t run_z(const ArgsZ& a, bool dump, cudaStream_t st) {
   const long nlines = a.nlines;
   if (!dump && a.nfields > 6) {
     const unsigned grid = (unsigned)((nlines + C::LINES_V - 1) / C::LINES_V);
-    k_pass_z<N, C::LINES_V, false, 5><<<grid, C::threads_zv, C::smem_zv, st>>>(a);
+    k_pass_z<N, C::LINES_V, false, 5, C::FUSE><<<grid, C::threads_zv, C::smem_zv, st>>>(a);
     return cudaGetLastError();
   }
   const unsigned grid = (unsigned)((nlines + C::LINES - 1) / C::LINES);
-  if (dump) k_pass_z<N, C::LINES, true, 3><<<grid, C::threads_z, C::smem_z, st>>>(a);
-  else k_pass_z<N, C::LINES, false, 3><<<grid, C::threads_z, C::smem_z, st>>>(a);
+  if (dump) k_pass_z<N, C::LINES, true, 3, false><<<grid, C::threads_z, C::smem_z, st>>>(a);
+  else k_pass_z<N, C::LINES, false, 3, C::FUSE><<<grid, C::threads_z, C::smem_z, st>>>(a);
   return cudaGetLastError();
 }
 
 #define PIN_SIZES(X) X(8) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
+
+bool z_fuses_roots(int n) {
+  switch (n) {
+#define CASE(N) case N: return Cfg<N>::FUSE;
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return false;
+  }
+}
 
 bool size_supported(int n) {
   switch (n) {

@@ -72,7 +72,8 @@ struct RedoEntry {
 
 // z pass: c2r of each field (its z factor already applied by the y pass),
 // then either the eigenvalues of every particle (lam_out, [3][nlines*N];
-// NaN for particles queued for the FP64 redo) or a dump of the real fields.
+// NaN for particles queued for the FP64 redo), or, where z_fuses_roots, the
+// collapse times and running maximum directly, or a dump of the real fields.
 struct ArgsZ {
   const float2* src[kMaxFields];
   int nfields;
@@ -123,6 +124,9 @@ cudaError_t prepare_kernels(int n);  // sets shared-memory attributes (once per 
 cudaError_t launch_x(int n, const ArgsX& a, cudaStream_t st);
 cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st);
 cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st);
+// True when the z pass of size n also computes the collapse times and the
+// running maximum (launch_roots is then not called for that size).
+bool z_fuses_roots(int n);
 // Collapse time and running maximum from the eigenvalues the z pass wrote
 // (after it, same stream), then the FP64 redo of every queued particle.
 cudaError_t launch_roots(const ArgsZ& a, cudaStream_t st);

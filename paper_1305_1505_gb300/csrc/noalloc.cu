@@ -249,7 +249,8 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
     az.redo_cap = (unsigned)kRedoCap;
     if (pin::launch_x(n, ax, cs) != cudaSuccess || pin::launch_y(n, ay, cs) != cudaSuccess ||
         cudaMemsetAsync(redo_count, 0, sizeof(unsigned), cs) != cudaSuccess ||
-        pin::launch_z(n, az, false, cs) != cudaSuccess || pin::launch_roots(az, cs) != cudaSuccess ||
+        pin::launch_z(n, az, false, cs) != cudaSuccess ||
+        (!pin::z_fuses_roots(n) && pin::launch_roots(az, cs) != cudaSuccess) ||
         pin::launch_redo(az, cs) != cudaSuccess)
       return PIN_ECUDA;
   }

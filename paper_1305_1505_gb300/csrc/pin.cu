@@ -316,7 +316,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   PIN_CK(p, launch_z(p->n, az, dump != nullptr, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 3], p->stream, cudaEventRecordExternal));
   if (!dump) {
-    PIN_CK(p, launch_roots(az, p->stream));
+    if (!z_fuses_roots(p->n)) PIN_CK(p, launch_roots(az, p->stream));
     PIN_CK(p, launch_redo(az, p->stream));
   }
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 4], p->stream, cudaEventRecordExternal));
@@ -644,7 +644,10 @@ pin_status pin_get_stats(pin_plan_t p, pin_stats* out) {
   return PIN_OK;
 }
 
-int pin_kernels_per_call(pin_plan_t p) { return p ? 5 * p->nscales : 0; }
+int pin_kernels_per_call(pin_plan_t p) {
+  if (!p) return 0;
+  return (z_fuses_roots(p->n) ? 4 : 5) * p->nscales;  // x, y, z, [roots,] redo per radius
+}
 
 pin_status pin_profile(pin_plan_t p, int enable) {
   pin_status st = check_plan(p);

@@ -1,5 +1,6 @@
 """The 768^3 x 40-radius workload of the benchmark, in its launch
-configuration, checked where the oracle can follow it:
+configuration, and the 384^3 grid with the same 4 Mpc/h cells (the other
+three-level transform size), checked where the oracle can follow them:
  - the deformation tensor at sampled grid points against the oracle's direct
    sum over every mode (one radius), and the trace rule over the whole grid;
  - F_max and the scale index at 1e5 sampled particles against the oracle's
@@ -14,24 +15,26 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-N, BOX, SEED, S = 768, 3072.0, 3, 40
+SEED, S = 3, 40
 
 
-@pytest.fixture(scope="module")
-def run():
+@pytest.fixture(scope="module", params=[384, 768])
+def run(request):
     import torch
     from paper_1305_1505_gb300 import pin
+    n = request.param
+    box = 4.0 * n
     radii = ic.log_radii(4.0, 120.0, S)
-    d32 = ic.delta_k(N, BOX, SEED, dtype=np.complex64)
-    plan = pin.Plan(N, BOX, radii)
+    d32 = ic.delta_k(n, box, SEED, dtype=np.complex64)
+    plan = pin.Plan(n, box, radii)
     plan.set_ic(torch.from_numpy(d32).cuda())
     F, I = plan.collapse_times()
-    yield plan, d32, radii, F, I
+    yield n, box, plan, d32, radii, F, I
     plan.close()
 
 
 def test_hessian_points_against_direct_sum(run):
-    plan, d32, radii, _, _ = run
+    N, BOX, plan, d32, radii, _, _ = run
     rng = np.random.default_rng(7)
     q = rng.integers(0, N ** 3, size=6)
     s = 30  # R = 8.6 Mpc/h: the field still has structure on the grid scale
@@ -46,7 +49,7 @@ def test_hessian_points_against_direct_sum(run):
 
 def test_collapse_sampled_particles(run):
     import torch
-    plan, _, radii, F, I = run
+    N, _, plan, _, radii, F, I = run
     rng = np.random.default_rng(8)
     q = np.unique(rng.integers(0, N ** 3, size=100_000))
     qt = torch.as_tensor(q, device="cuda")
@@ -57,6 +60,6 @@ def test_collapse_sampled_particles(run):
     Fg = F.reshape(-1)[qt].cpu().numpy()
     Ig = I.reshape(-1)[qt].cpu().numpy()
     bad, rep = parity.classify(Fg, Ig, orc["fmax"], orc["idx"], orc["f2"], orc["idx2"])
-    print("768^3 sampled:", rep, plan.stats())
+    print("%d^3 sampled:" % N, rep, plan.stats())
     assert rep["f_bad"] == 0 and rep["idx_bad"] == 0, rep
     assert rep["idx_mismatch"] <= max(1, 1e-4 * q.size), rep
