@@ -314,7 +314,8 @@ def run_ours(args):
     if rank == 0:
         cb = cpu_baseline(S) if ws == 1 and not args.no_cpu else None
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": METRIC if n == WORKLOAD["n"] else METRIC.replace("768^3", "%d^3" % n),
+            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(_config(w), velocities=bool(args.velocities)),

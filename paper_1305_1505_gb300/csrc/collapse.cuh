@@ -212,9 +212,6 @@ __host__ __device__ __forceinline__ T root_kappa(T c1, T c2, T x) {
 //    region; it is positive only if g(0) = -c3 < 0, and the iteration starts at 0.
 // Four iterations reach ~1e-6 relative in FP32 on the coefficient ranges of
 // smoothed Gaussian fields; near-tangent roots are flagged by kappa and redone.
-#ifndef PIN_HALLEY_ITERS
-#define PIN_HALLEY_ITERS 4
-#endif
 template <typename T>
 __host__ __device__ __forceinline__ T largest_root_iter(T c1, T c2, T c3, T& kappa) {
   using F = M<T>;
@@ -233,7 +230,7 @@ __host__ __device__ __forceinline__ T largest_root_iter(T c1, T c2, T c3, T& kap
   // tiny positive value instead of tested: a degenerate step leaves a large
   // last step, which sends the particle to the FP64 redo below.
 #pragma unroll
-  for (int it = 0; it < PIN_HALLEY_ITERS; ++it) {
+  for (int it = 0; it < 4; ++it) {
     const T g = ((x - c1) * x - c2) * x - c3;
     const T dg = (T(3) * x - T(2) * c1) * x - c2;
     const T d2h = T(3) * x - c1;
@@ -303,17 +300,16 @@ struct CollapseConsts {
 // g(T) > 0 and g stays positive beyond T, i.e. g' has no real root, or the
 // right critical point F* = (c1 + sqrt(c1^2 + 3 c2))/3 lies at or below T, or
 // g(F*) > 0 (g is increasing beyond F*).  Exact up to rounding, and far
-// cheaper than solving the cubic.
+// cheaper than solving the cubic.  Every term is evaluated (no early exits),
+// so that the particles of a warp do not diverge on it.
 template <typename T>
 __host__ __device__ __forceinline__ bool no_root_from(T c1, T c2, T c3, T t) {
   using F = M<T>;
   const T gt = ((t - c1) * t - c2) * t - c3;
-  if (!(gt > T(0))) return false;
   const T d = c1 * c1 + T(3) * c2;
-  if (d < T(0)) return true;
   const T fs = (c1 + F::sqrt_approx(d)) * (T(1) / T(3));
-  if (fs <= t) return true;
-  return ((fs - c1) * fs - c2) * fs - c3 > T(0);
+  const T gs = ((fs - c1) * fs - c2) * fs - c3;
+  return (gt > T(0)) & ((d < T(0)) | (fs <= t) | (gs > T(0)));
 }
 
 // Coefficients (c1, c2, c3) of a_i(D) = c1 D + c2 D^2 + c3 D^3 for axis i.

@@ -234,7 +234,9 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c,
     // level 2: for k1 = q + P2 i, the length-P2 DFT over p2 of Z[k1][p1 + P1 p2],
     // then the twiddle w_P^{p1 k2a}
     const int p1 = p % P1, q = p / P1;
-    const float2* s_twb = s_tw + E * P;
+    float2 twb[P2];  // w_P^{p1 k2a}: the same for every k1 of this thread
+#pragma unroll
+    for (int k2a = 1; k2a < P2; ++k2a) twb[k2a] = s_tw[E * P + k2a * P1 + p1];
 #pragma unroll
     for (int i = 0; i < E / P2; ++i) {
       float2 t[P2];
@@ -242,8 +244,7 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c,
       for (int j = 0; j < P2; ++j) t[j] = s_x[Layout::at(q + P2 * i, p1 + P1 * j, c)];
       DFT<P2>::run(t);
 #pragma unroll
-      for (int k2a = 0; k2a < P2; ++k2a)
-        v[i * P2 + k2a] = (k2a == 0) ? t[k2a] : cmul(t[k2a], s_twb[k2a * P1 + p1]);
+      for (int k2a = 0; k2a < P2; ++k2a) v[i * P2 + k2a] = (k2a == 0) ? t[k2a] : cmul(t[k2a], twb[k2a]);
     }
     __syncthreads();
 #pragma unroll

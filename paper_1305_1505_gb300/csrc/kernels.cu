@@ -344,14 +344,19 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
 #pragma unroll
     for (int t = 0; t < E; ++t) {
       const int n = p + P * t;
-      const int m = n <= N / 2 ? n : N - n;
+      // slot t holds n in [P t, P t + P): wholly below N/2, wholly above, or
+      // straddling it; the first two are decided at compile time
+      const bool below = P * t + P - 1 < N / 2, above = P * t > N / 2;
+      const int m = below ? n : (above ? N - n : (n <= N / 2 ? n : N - n));
+      const bool conj = !below && (above || n > N / 2);
+      const bool real = below ? (t == 0 && p == 0) : (!above && (n == N / 2 || n == 0));
       float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
       if (active) xa = __ldg(A + m);
       if (hasb) xb = __ldg(B + m);
-      if (n == 0 || n == N / 2) {
+      if (real) {
         xa.y = 0.f;
         xb.y = 0.f;
-      } else if (n > N / 2) {
+      } else if (conj) {
         xa = cconj(xa);
         xb = cconj(xb);
       }

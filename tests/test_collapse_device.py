@@ -61,3 +61,41 @@ def test_device_collapse_and_eigen_vs_oracle(lib):
     hmax = np.abs(h).max(axis=1)
     eerr = np.abs(e32 - ref_eig).max(axis=1) / hmax
     assert np.percentile(eerr, 99.9) < 1e-5
+
+
+def _special_eigenvalues(rng):
+    """Structured and scaled eigenvalue triples (sorted, largest first):
+    spheres, one- and two-axis cases, zero and sign-mixed triples, exact
+    diagonal ties, roots crossing zero (lam0 -> 0+ with the others negative),
+    and random triples over six decades of amplitude."""
+    rows = []
+    for t in (-2.0, -0.3, 0.0, 1e-4, 0.2, 1.0, 3.0):
+        rows += [(t, t, t), (t, 0.0, 0.0), (t, t, 0.0), (t, 0.0, -t), (t, -t, -t), (0.0, 0.0, t)]
+    for eps in (1e-7, 1e-6, 1e-5, 1e-4, 1e-3):
+        for a, b in rng.uniform(0.01, 0.4, size=(200, 2)):
+            rows.append((eps, -min(a, b), -max(a, b)))
+    for amp in (1e-3, 1e-2, 0.1, 1.0, 10.0, 100.0):
+        x = rng.normal(size=(2000, 3)) * amp
+        rows += [tuple(r) for r in x]
+        a = rng.normal(size=(500, 2)) * amp
+        rows += [(u, u, v) for u, v in a] + [(u, v, v) for u, v in a]
+    lam = -np.sort(-np.array(rows, dtype=np.float64), axis=1)
+    return lam
+
+
+def test_device_collapse_special_cases(lib):
+    lam = _special_eigenvalues(np.random.default_rng(11))
+    h = np.zeros((lam.shape[0], 6))
+    h[:, :3] = lam
+    ref = np.array([oracle.collapse_F(l, c) for l in lam for c in (1,)])
+    F32, kap, _ = _eval(lib, lam, h, 1, 1)
+    assert np.all(np.isfinite(kap)) and np.all(np.isfinite(F32))
+    scale = np.abs(lam).max(axis=1)
+    ok = kap >= 1e-3
+    err = np.abs(F32 - ref)
+    bad = np.nonzero(ok & (err > 1e-4 * np.abs(ref) + 1e-6 * scale))[0]
+    assert bad.size == 0, (bad[:5], lam[bad[:5]], F32[bad[:5]], ref[bad[:5]])
+    # particles that never collapse get exactly 0
+    assert np.all(F32[ref == 0.0][kap[ref == 0.0] >= 1e-3] == 0.0)
+    # what goes to the FP64 redo stays rare
+    assert (~ok).mean() < 0.02

@@ -82,3 +82,38 @@ def test_eigen_fp64_and_fp32(lib):
             if use_float and 1 - r < 2e-4:
                 continue  # near-degenerate: the kernel redoes these in FP64
             assert np.abs(lam - ref).max() <= tol * np.abs(h).max(), (h, lam, ref)
+
+
+def _structured(rng):
+    """Spheres, one- and two-axis triples, zeros, sign mixes, exact ties, a
+    root crossing zero (lam0 -> 0+ with the others negative), and random
+    triples over six decades of amplitude."""
+    rows = []
+    for t in (-2.0, -0.3, 0.0, 1e-4, 0.2, 1.0, 3.0):
+        rows += [(t, t, t), (t, 0.0, 0.0), (t, t, 0.0), (t, 0.0, -t), (t, -t, -t), (0.0, 0.0, t)]
+    for eps in (1e-7, 1e-6, 1e-5, 1e-4, 1e-3):
+        for a, b in rng.uniform(0.01, 0.4, size=(40, 2)):
+            rows.append((eps, -min(a, b), -max(a, b)))
+    for amp in (1e-3, 1e-2, 0.1, 1.0, 10.0, 100.0):
+        rows += [tuple(r) for r in rng.normal(size=(300, 3)) * amp]
+        rows += [(u, u, v) for u, v in rng.normal(size=(60, 2)) * amp]
+        rows += [(u, v, v) for u, v in rng.normal(size=(60, 2)) * amp]
+    return -np.sort(-np.array(rows, dtype=np.float64), axis=1)
+
+
+def test_collapse_fp32_structured(lib):
+    lam_all = _structured(np.random.default_rng(12))
+    flagged = 0
+    for lam in lam_all:
+        g, kap = _F(lib, lam, 1, 1)
+        o = oracle.collapse_F(lam, 1)
+        scale = np.abs(lam).max()
+        assert np.isfinite(kap), (lam, g, kap)
+        if kap >= 1e-3:
+            assert np.isfinite(g) and abs(g - o) <= 1e-4 * abs(o) + 1e-6 * scale, (lam, g, o, kap)
+        else:
+            assert np.isfinite(g), (lam, g, kap)
+            flagged += 1
+        if o == 0.0 and kap >= 1e-3:
+            assert g == 0.0, (lam, g)
+    assert flagged <= 0.02 * len(lam_all)
