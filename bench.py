@@ -123,7 +123,12 @@ def algorithmic_bytes(n, fused, velocities):
 # dram__bytes_write.sum), from an ncu capture of bench.py, valid only while
 # the kernel sources hash to the recorded value; otherwise reported as null.
 TRAFFIC_SOURCES = ["kernels.cu", "kernels.cuh", "fft.cuh", "collapse.cuh", "pin.cu"]
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # profiles/launch_list_768x40.md: dram bytes and warp instructions of the
+    # fused z pass per launch, 768^3 x 40
+    ("k_pass_z", 768, False): {"sources": "b8091d6d40822834", "bytes_per_launch": 16.707e9,
+                               "warp_inst_per_launch": 6.945e9},
+}
 
 
 def sources_digest():
@@ -135,11 +140,46 @@ def sources_digest():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel, n, nscales, velocities):
+def measured_record(kernel, n, velocities):
     rec = MEASURED_TRAFFIC.get((kernel, n, bool(velocities)))
     if rec is None or rec["sources"] != sources_digest():
         return None
-    return rec["bytes_per_launch"]
+    return rec
+
+
+def measured_traffic(kernel, n, nscales, velocities):
+    rec = measured_record(kernel, n, velocities)
+    return None if rec is None else rec["bytes_per_launch"]
+
+
+# Issue roof of the SMs: 152 SMs x 4 warp schedulers x 1 warp instruction per
+# cycle at the sampled maximum SM clock (2070 MHz on GB300).
+SMS, SCHEDULERS = 152, 4
+
+
+def roofline(pass_name, ms_per_launch, n, velocities, fused, hbm_achieved, hbm_peak, peak_kind, clocks, passes):
+    """Roofline object of the dominant kernel.  HBM-bound passes report
+    algorithmic GB/s against the measured copy bandwidth.  The fused z pass
+    is bound by instruction issue: when its warp-instruction count per launch
+    was measured on the current kernel sources (MEASURED_TRAFFIC), it reports
+    warp instructions per second against the issue roof (SMS x SCHEDULERS x
+    the sampled maximum SM clock), with its HBM fraction alongside."""
+    kname = ("k_pass_" if pass_name in "xyz" else "k_") + pass_name
+    rec = measured_record(kname, n, velocities)
+    traffic = None if rec is None else rec["bytes_per_launch"]
+    hbm = {"bound": "hbm", "kernel": kname, "achieved": hbm_achieved, "peak": hbm_peak,
+           "peak_kind": peak_kind, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+           "traffic": traffic, "passes": passes}
+    if rec is None or not fused or kname != "k_pass_z" or not rec.get("warp_inst_per_launch"):
+        return hbm
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = SMS * SCHEDULERS * mhz * 1e6 / 1e9
+    achieved = rec["warp_inst_per_launch"] / (ms_per_launch / 1e3) / 1e9
+    return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+            "peak_kind": "derived: %d SMs x %d schedulers x 1 warp instruction/cycle x %.0f MHz"
+                         % (SMS, SCHEDULERS, mhz),
+            "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": traffic,
+            "hbm_frac": hbm_achieved / hbm_peak, "hbm_peak_kind": peak_kind, "passes": passes}
 
 
 def _dist():
@@ -312,6 +352,7 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     if rank == 0:
+        clocks = clk.summary()
         cb = cpu_baseline(S) if ws == 1 and not args.no_cpu else None
         line = {
             "metric": METRIC if n == WORKLOAD["n"] else METRIC.replace("768^3", "%d^3" % n),
@@ -319,16 +360,13 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(_config(w), velocities=bool(args.velocities)),
-            "roofline": {"bound": "hbm", "kernel": ("k_pass_" if names[dom] in "xyz" else "k_") + names[dom],
-                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
-                         "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": measured_traffic(names[dom], n, S, bool(args.velocities)),
-                         "passes": passes},
+            "roofline": roofline(names[dom], per_launch_ms[dom], n, bool(args.velocities), fused,
+                                 achieved, peak, peak_kind, clocks, passes),
             "cpu_baseline": cb,
             "e2e": None if args.no_e2e else {"value": updates * ws / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(d32.nbytes), "d2h_bytes_per_step": int(8 * n ** 3)},
             "gpu_launches": int(args.steps * pin.pin_kernels_per_call(plan.handle)),
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "fp64_redo": {"eig": stats["eig_fp64_redo"], "root": stats["root_fp64_redo"],
                           "particle_scales": int(stats["collapse_calls"]) * updates},
         }
