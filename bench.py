@@ -455,6 +455,90 @@ def run_ensemble(args):
     return 0
 
 
+# bytes each particle costs the fragmentation front end: four radix passes
+# (histogram key read 4 B each; scatter: pass 0 reads F 4 B and writes key +
+# index 8 B, passes 1-2 read and write 8 B, pass 3 reads 8 B and writes the
+# index 4 B) and the neighbour count (F read 4 B, count write 1 B)
+FRAGMENT_BYTES = 4 * 4 + (4 + 8) + 2 * (8 + 8) + (8 + 4) + (4 + 1)
+
+
+def run_fragment(args):
+    """Fragmentation front end (Sec. 2.1.2) on the 768^3 x 40 workload: one
+    pin_collapse_times (untimed), then pin_fragment_order timed on the device
+    (order and neighbour counts, device outputs), end to end with host
+    outputs, and the oracle on a 128^3 block of the same F_max field."""
+    import torch
+    from paper_1305_1505_gb300 import ic, pin
+    w = dict(WORKLOAD)
+    if args.grid:
+        w["n"], w["box"] = args.grid, 4.0 * args.grid
+    n = w["n"]
+    radii = ic.log_radii(w["r_min"], w["r_max"], w["nscales"])
+    stream = torch.cuda.Stream()
+    plan = pin.Plan(n, w["box"], radii, stream=stream)
+    plan.set_ic(torch.from_numpy(ic.delta_k(n, w["box"], w["seed"], dtype=np.complex64)).cuda())
+    F, _ = plan.collapse_times()
+    order = torch.empty(n ** 3, dtype=torch.int32, device="cuda")
+    nb = torch.empty((n, n, n), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        pin.pin_fragment_order(plan.handle, order.data_ptr(), nb.data_ptr(), 1)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    e2e = None
+    if not args.no_e2e:
+        ho = torch.empty(n ** 3, dtype=torch.int32).pin_memory()
+        hn = torch.empty((n, n, n), dtype=torch.uint8).pin_memory()
+        pin.pin_fragment_order(plan.handle, ho.data_ptr(), hn.data_ptr(), 0)
+        reps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            pin.pin_fragment_order(plan.handle, ho.data_ptr(), hn.data_ptr(), 0)
+        te = (time.perf_counter() - t0) / reps
+        e2e = {"value": n ** 3 / te, "unit": "particles/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int(5 * n ** 3)}
+    cb = None
+    if not args.no_cpu:
+        import oracle
+        m = min(128, n)
+        block = F[:m, :m, :m].contiguous().cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.fragment_order(block)
+        tc = time.perf_counter() - t0
+        cb = {"value": m ** 3 / tc, "unit": "particles/s", "cores": 1, "kind": "oracle",
+              "sample": "%d^3 block of the same F_max field (numpy lexsort + rolls), %.1f s" % (m, tc)}
+    peak, peak_kind = _peaks()
+    achieved = FRAGMENT_BYTES * n ** 3 / t / 1e9
+    line = {"metric": "fragmentation order (particles/s) at %d^3" % n, "value": n ** 3 / t,
+            "unit": "particles/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "F_max of the %d^3 x %d collapse workload, seed %d" % (n, w["nscales"], w["seed"]),
+                       "l2": "inputs larger than L2 (F_max %.1f GB, sort buffers %.1f GB)"
+                             % (4 * n ** 3 / 1e9, 16 * n ** 3 / 1e9)},
+            "roofline": {"bound": "hbm", "kernel": "fragment_order (4 radix passes + neighbour count)",
+                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "alg_bytes_per_particle": FRAGMENT_BYTES},
+            "cpu_baseline": cb, "e2e": e2e,
+            "gpu_launches": int(args.steps * 21), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,11 +552,14 @@ def main():
     ap.add_argument("--nscales", type=int, default=0, help="number of radii; default 40")
     ap.add_argument("--velocities", action="store_true",
                     help="also keep v_max (the displacement smoothed on R_max): 9 fields per radius")
-    ap.add_argument("--workload", default="paper", choices=["paper", "ensemble"],
-                    help="paper: 768^3 x 40 (the metric); ensemble: 64 x 128^3 batched vs sequential")
+    ap.add_argument("--workload", default="paper", choices=["paper", "ensemble", "fragment"],
+                    help="paper: 768^3 x 40 (the metric); ensemble: 64 x 128^3 batched vs sequential; "
+                         "fragment: the fragmentation front end on the 768^3 F_max field")
     args = ap.parse_args()
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "fragment":
+        return run_fragment(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -121,6 +121,22 @@ pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, in
  * on_device semantics as pin_collapse_times. */
 pin_status pin_velocities(pin_plan_t p, float* psi_max, int on_device);
 
+/* Fragmentation front end (Sec. 2.1.2): the fragmentation considers the
+ * particles in descending F_max (an effectively chronological order) and,
+ * for each, the halos its six neighbours belong to.  From the F_max of the
+ * plan's last pin_collapse_times call (batch 1 only):
+ *   order[i]     (N^3 int32) the particle index q of the i-th particle in
+ *                descending F_max; equal F_max in ascending q (a reading: the
+ *                paper gives no tie rule), so order is a permutation of [0, N^3);
+ *   n_before[q]  (N^3 uint8) how many of the six periodic neighbours of q
+ *                (q +- 1 along x, y and z) come before q in that order; 0 marks
+ *                a peak of the F_max field (a new halo, case (i)).
+ * Either output may be NULL (skipped), not both.  Runs on the plan's stream
+ * and uses the y-pass spectra as scratch (they are rebuilt by the next
+ * pin_collapse_times).  Same on_device semantics as pin_collapse_times.
+ * PIN_ESTATE before the first pin_collapse_times, PIN_EINVAL for batch > 1. */
+pin_status pin_fragment_order(pin_plan_t p, int32_t* order, uint8_t* n_before, int on_device);
+
 /* The six real components of the deformation tensor phi_ij(q) at radius
  * index `scale` (the a1-a2 steps alone), out6 = [6][N^3] floats in the order
  * xx, yy, zz, xy, xz, yz.  Same on_device semantics as pin_collapse_times. */

@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and
 by bench.py's cpu_baseline / reference leg.  The product path never imports
-it.  Everything here is argument marshalling around oracle/pin_oracle.c.
+it.  Everything here is argument marshalling around oracle/pin_oracle.c,
+except fragment_order (Sec. 2.1.2), a few lines of numpy.
 """
 import ctypes
 import os
@@ -223,3 +224,26 @@ def collapse_from_hessians(h6s, correction=1):
     lib().or_collapse_from_hessians(_p(h), S, m, correction, _p(fmax), _p(idx, ctypes.c_int),
                                     _p(f2), _p(idx2, ctypes.c_int))
     return dict(fmax=fmax, idx=idx, f2=f2, idx2=idx2)
+
+
+def fragment_order(F_max):
+    """Fragmentation front end (Sec. 2.1.2) on an (n, n, n) F_max field.
+    The particles are considered in descending F_max; equal values in
+    ascending particle index q = (x n + y) n + z (a reading: the paper states
+    no tie rule).  Returns (order, n_before): order[i] is the q of the i-th
+    particle considered; n_before[q] counts the six periodic neighbours of q
+    (+-1 along each axis) whose rank in that order is below q's.  numpy's
+    lexsort and roll serve as the sort and the shifts."""
+    F = np.asarray(F_max, dtype=np.float64)
+    n = F.shape[0]
+    flat = F.ravel()
+    q = np.arange(flat.size)
+    order = np.lexsort((q, -flat))  # last key is the primary one
+    rank = np.empty(flat.size, dtype=np.int64)
+    rank[order] = q
+    R = rank.reshape(F.shape)
+    n_before = np.zeros(F.shape, dtype=np.int64)
+    for axis in range(3):
+        for shift in (1, -1):
+            n_before += np.roll(R, shift, axis=axis) < R
+    return order, n_before

@@ -268,22 +268,33 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
       const float zf = (ok && kz <= N / 2) ? s_m[s_zm[o] * N + kz] : 0.f;
       const bool mi = s_mi[o] != 0;
       float2* d = s_dst[o] + base;
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        float2 w = cscale(v[j], zf);
-        if (mi) w = cmuli(w);
-        if (ok) d[(size_t)fft_out_index<N>(p, j) * nhp] = w;
-      }
-      if (DUAL && s_dst2[o] != nullptr) {
-        // the same transform with another z factor (displacement components)
-        const float zf2 = (ok && kz <= N / 2) ? s_m[s_zm2[o] * N + kz] : 0.f;
+      if constexpr (DUAL) {
+        // outputs with a second store: the same transform with another z
+        // factor (displacement components), both stores per register slot so
+        // that each slot dies after its two stores
+        float2* d2 = s_dst2[o];
+        const bool two = ok && d2 != nullptr;
+        const float zf2 = (two && kz <= N / 2) ? s_m[s_zm2[o] * N + kz] : 0.f;
         const bool mi2 = s_mi2[o] != 0;
-        float2* d2 = s_dst2[o] + base;
+        d2 = two ? d2 + base : nullptr;
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-          float2 w = cscale(v[j], zf2);
-          if (mi2) w = cmuli(w);
-          if (ok) d2[(size_t)fft_out_index<N>(p, j) * nhp] = w;
+          const size_t off = (size_t)fft_out_index<N>(p, j) * nhp;
+          float2 w = cscale(v[j], zf);
+          if (mi) w = cmuli(w);
+          if (ok) d[off] = w;
+          if (two) {
+            float2 w2 = cscale(v[j], zf2);
+            if (mi2) w2 = cmuli(w2);
+            d2[off] = w2;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          float2 w = cscale(v[j], zf);
+          if (mi) w = cmuli(w);
+          if (ok) d[(size_t)fft_out_index<N>(p, j) * nhp] = w;
         }
       }
       __syncthreads();

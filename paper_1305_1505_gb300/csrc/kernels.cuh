@@ -12,6 +12,7 @@
 #pragma once
 #include <cuda.h>  // CUtensorMap (the encoder itself is fetched from the driver at run time)
 #include <cstddef>
+#include <cstdint>
 #include <cuda_runtime.h>
 
 namespace pin {
@@ -132,5 +133,14 @@ bool z_fuses_roots(int n);
 cudaError_t launch_roots(const ArgsZ& a, cudaStream_t st);
 cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st);
 cudaError_t upload_constant_twiddles();  // per device
+
+// Fragmentation front end (fragment.cu): the particles of one N^3 grid in
+// descending F_max (ties: ascending index) into `order`, and the number of
+// their six periodic neighbours that precede them into `n_before`; either
+// output may be null.  `scratch` holds fragment_scratch_bytes(N^3) bytes.
+size_t fragment_scratch_bytes(long n3);
+cudaError_t fragment_order(const float* fmax, int n, void* scratch, int32_t* order, uint8_t* n_before,
+                           cudaStream_t st);
+int fragment_kernels(bool order, bool counts);  // launches of one fragment_order call
 
 }  // namespace pin

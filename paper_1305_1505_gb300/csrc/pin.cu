@@ -522,6 +522,37 @@ pin_status pin_velocities(pin_plan_t p, float* psi_max, int on_device) {
   return PIN_OK;
 }
 
+pin_status pin_fragment_order(pin_plan_t p, int32_t* order, uint8_t* n_before, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!order && !n_before) return fail(p, PIN_EINVAL, "both outputs are null");
+  if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_fragment_order needs a plan with batch 1");
+  if (p->calls == 0) return fail(p, PIN_ESTATE, "pin_collapse_times has not been called");
+  const long n3 = (long)p->n * p->n * p->n;
+  // the y-pass spectra are free once the radius loop is done: sort scratch,
+  // and (for host outputs) the device copies of the results after it
+  const size_t need = fragment_scratch_bytes(n3);
+  const size_t have = (size_t)(p->velocities ? 9 : 6) * p->field_elems * sizeof(float2);
+  const size_t tail = (need + 255) & ~(size_t)255;
+  if (tail + (size_t)n3 > have) return fail(p, PIN_ECUDA, "fragment scratch does not fit the plan's workspace");
+  char* scratch = reinterpret_cast<char*>(p->V);
+  int32_t* order_dev = order;
+  uint8_t* nb_dev = n_before;
+  if (!on_device) {
+    // the last radix pass reads keys and values A and writes only values:
+    // the second value array is free for the order
+    if (order) order_dev = reinterpret_cast<int32_t*>(scratch + (size_t)3 * n3 * 4);
+    if (n_before) nb_dev = reinterpret_cast<uint8_t*>(scratch + tail);
+  }
+  PIN_CK(p, fragment_order(p->fmax, p->n, scratch, order_dev, nb_dev, p->stream));
+  if (!on_device) {
+    if (order) PIN_CK(p, cudaMemcpyAsync(order, order_dev, (size_t)n3 * 4, cudaMemcpyDeviceToHost, p->stream));
+    if (n_before) PIN_CK(p, cudaMemcpyAsync(n_before, nb_dev, (size_t)n3, cudaMemcpyDeviceToHost, p->stream));
+    return finish_host(p);
+  }
+  return PIN_OK;
+}
+
 pin_status pin_hessian(pin_plan_t p, int scale, float* out6, int on_device) {
   pin_status st = check_plan(p);
   if (st != PIN_OK) return st;

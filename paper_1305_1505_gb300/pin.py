@@ -47,7 +47,7 @@ class pin_stats(ctypes.Structure):
 EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_hessian",
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
-           "pin_strerror", "pin_last_error", "pin_destroy")
+           "pin_fragment_order", "pin_strerror", "pin_last_error", "pin_destroy")
 
 _lib = None
 
@@ -73,6 +73,8 @@ def load(path=None):
     L.pin_collapse_times.restype = ctypes.c_int
     L.pin_velocities.argtypes = [P, P, ctypes.c_int]
     L.pin_velocities.restype = ctypes.c_int
+    L.pin_fragment_order.argtypes = [P, P, P, ctypes.c_int]
+    L.pin_fragment_order.restype = ctypes.c_int
     L.pin_hessian.argtypes = [P, ctypes.c_int, P, ctypes.c_int]
     L.pin_hessian.restype = ctypes.c_int
     L.pin_displacements.argtypes = [P, P, ctypes.c_int]
@@ -150,6 +152,12 @@ def pin_collapse_times(plan, fmax_ptr, idx_ptr, on_device):
 
 def pin_velocities(plan, out_ptr, on_device):
     _check(load().pin_velocities(plan, ctypes.c_void_p(out_ptr), int(on_device)), plan)
+
+
+def pin_fragment_order(plan, order_ptr, n_before_ptr, on_device):
+    _check(load().pin_fragment_order(plan, ctypes.c_void_p(order_ptr) if order_ptr else None,
+                                     ctypes.c_void_p(n_before_ptr) if n_before_ptr else None,
+                                     int(on_device)), plan)
 
 
 def pin_hessian(plan, scale, out_ptr, on_device):
@@ -290,6 +298,21 @@ class Plan:
         pin_velocities(self.handle, out.data_ptr(), 1)
         self.sync()
         return out
+
+    def fragment_order(self, order=True, n_before=True):
+        """(order, n_before) of the last collapse_times (Sec. 2.1.2): the
+        particle indices in descending F_max (ties by index) as an (n^3,)
+        int32 tensor, and per particle the number of its six neighbours that
+        precede it, (n, n, n) uint8; either may be skipped (None)."""
+        import torch
+        n = self.n
+        o = torch.empty((n ** 3,), dtype=torch.int32, device="cuda") if order else None
+        c = torch.empty((n, n, n), dtype=torch.uint8, device="cuda") if n_before else None
+        torch.cuda.current_stream().synchronize()
+        pin_fragment_order(self.handle, o.data_ptr() if o is not None else 0,
+                           c.data_ptr() if c is not None else 0, 1)
+        self.sync()
+        return o, c
 
     def hessian(self, scale):
         import torch

@@ -63,3 +63,30 @@ def test_collapse_sampled_particles(run):
     print("%d^3 sampled:" % N, rep, plan.stats())
     assert rep["f_bad"] == 0 and rep["idx_bad"] == 0, rep
     assert rep["idx_mismatch"] <= max(1, 1e-4 * q.size), rep
+
+
+def test_fragment_order_full_grid(run):
+    """At the benchmark size the order is checked by the properties that
+    define it (the oracle's sort of 4.5e8 values is not run here): a
+    permutation, F_max non-increasing along it, equal values in ascending
+    index, each neighbour pair counted once, and n_before at 1e5 sampled
+    particles recomputed from F_max."""
+    import torch
+    N, _, plan, _, _, F, _ = run
+    order, nb = plan.fragment_order()
+    f = F.reshape(-1)
+    o = order.long()
+    assert int(torch.bincount(o, minlength=N ** 3).ne(1).sum()) == 0
+    fo = f[o]
+    assert bool((fo[1:] <= fo[:-1]).all())
+    eq = fo[1:] == fo[:-1]
+    assert bool((o[1:][eq] > o[:-1][eq]).all())
+    assert int(nb.long().sum()) == 3 * N ** 3
+    rng = np.random.default_rng(9)
+    q = torch.as_tensor(rng.integers(0, N ** 3, size=100_000), device="cuda")
+    x, y, z = q // (N * N), (q // N) % N, q % N
+    cnt = torch.zeros_like(q)
+    for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+        r = (((x + dx) % N) * N + (y + dy) % N) * N + (z + dz) % N
+        cnt += ((f[r] > f[q]) | ((f[r] == f[q]) & (r < q))).long()
+    assert bool((nb.reshape(-1)[q].long() == cnt).all())

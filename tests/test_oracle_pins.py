@@ -452,3 +452,55 @@ def test_vmax_is_displacement_at_the_argmax_radius():
         else:
             ref = oracle.displacement(d, box, radii[s]).reshape(3, -1)[:, q]
             assert np.allclose(v[:, q], ref, rtol=0, atol=1e-15)
+
+
+# ---- fragmentation front end (Sec. 2.1.2): order and neighbours before ----
+
+def _brute_fragment(F):
+    """Straight from the definitions: sort the (F, q) pairs by a key, and
+    count for each particle the neighbours whose pair comes first by direct
+    comparison (larger F, or equal F and smaller index)."""
+    n = F.shape[0]
+    flat = [float(v) for v in F.ravel()]
+    order = sorted(range(n ** 3), key=lambda q: (-flat[q], q))
+    nb = np.zeros((n, n, n), dtype=np.int64)
+    for x in range(n):
+        for y in range(n):
+            for z in range(n):
+                q = (x * n + y) * n + z
+                for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    r = (((x + dx) % n) * n + (y + dy) % n) * n + (z + dz) % n
+                    if flat[r] > flat[q] or (flat[r] == flat[q] and r < q):
+                        nb[x, y, z] += 1
+    return np.array(order), nb
+
+
+@pytest.mark.parametrize("n,levels", [(3, 0), (4, 5), (5, 3), (6, 0)])
+def test_fragment_order_brute_force(n, levels):
+    rng = np.random.default_rng(40 + n)
+    F = rng.random((n, n, n)).astype(np.float32)
+    if levels:  # many exact ties, including zeros (particles that never collapse)
+        F = np.floor(F * levels).astype(np.float32) / levels
+    order, nb = oracle.fragment_order(F)
+    border, bnb = _brute_fragment(F)
+    assert np.array_equal(order, border)
+    assert np.array_equal(nb, bnb)
+
+
+def test_fragment_order_invariants():
+    rng = np.random.default_rng(7)
+    n = 8
+    F = np.maximum(rng.normal(size=(n, n, n)), 0).astype(np.float32)  # about half never collapse
+    order, nb = oracle.fragment_order(F)
+    assert np.array_equal(np.sort(order), np.arange(n ** 3))  # a permutation
+    f = F.ravel()[order]
+    assert np.all(np.diff(f) <= 0)  # descending F
+    ties = np.nonzero(np.diff(f) == 0)[0]
+    assert np.all(order[ties] < order[ties + 1])  # equal F: ascending index
+    # each of the 3 n^3 neighbour pairs is counted by exactly one of its two ends
+    assert nb.sum() == 3 * n ** 3
+    assert nb.ravel()[order[0]] == 0 and nb.ravel()[order[-1]] == 6
+    # all-equal field: the order is the index order, and q counts its smaller-index neighbours
+    o2, nb2 = oracle.fragment_order(np.zeros((4, 4, 4), dtype=np.float32))
+    assert np.array_equal(o2, np.arange(64))
+    assert nb2[0, 0, 0] == 0 and nb2[3, 3, 3] == 6 and nb2[1, 1, 1] == 3
