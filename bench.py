@@ -539,6 +539,85 @@ def run_fragment(args):
     return 0
 
 
+# bytes per particle of one pin_displacements_2lpt call (H ~ N^3/2 complex =
+# 4 B per particle per spectrum): the unsmoothed Hessian passes (x 4 spectra,
+# y 9, z reads 6 and writes the 4-byte source S), the forward transform of S
+# (z reads S and writes a spectrum, y and x read and write one each), Phi2
+# (read and write one), and the gradient passes (x 3 spectra, y 5, z reads 3
+# and writes 12 bytes)
+LPT2_BYTES = 16 + 36 + 28 + 8 + 8 + 8 + 8 + 12 + 20 + 24
+
+
+def run_2lpt(args):
+    """Second-order LPT displacement of the unsmoothed 768^3 field, timed on
+    the device (output in device memory) and end to end (host output)."""
+    import torch
+    from paper_1305_1505_gb300 import ic, pin
+    w = dict(WORKLOAD)
+    if args.grid:
+        w["n"], w["box"] = args.grid, 4.0 * args.grid
+    n = w["n"]
+    stream = torch.cuda.Stream()
+    plan = pin.Plan(n, w["box"], [w["r_max"]], stream=stream)
+    d32 = ic.delta_k(n, w["box"], w["seed"], dtype=np.complex64)
+    plan.set_ic(torch.from_numpy(d32).cuda())
+    out = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        pin.pin_displacements_2lpt(plan.handle, out.data_ptr(), 1)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    e2e = None
+    if not args.no_e2e:
+        hd = torch.from_numpy(d32).pin_memory()
+        ho = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
+        reps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)
+            pin.pin_displacements_2lpt(plan.handle, ho.data_ptr(), 0)
+        te = (time.perf_counter() - t0) / reps
+        e2e = {"value": n ** 3 / te, "unit": "particles/s", "h2d_bytes_per_step": int(d32.nbytes),
+               "d2h_bytes_per_step": int(12 * n ** 3)}
+    cb = None
+    if not args.no_cpu:
+        import oracle
+        m = min(128, n)
+        dm = ic.delta_k(m, 4.0 * m, w["seed"])
+        t0 = time.perf_counter()
+        oracle.displacement_2lpt(dm, 4.0 * m)
+        tc = time.perf_counter() - t0
+        cb = {"value": m ** 3 / tc, "unit": "particles/s", "cores": os.cpu_count(), "kind": "oracle",
+              "sample": "%d^3 grid with the same 4 Mpc/h cells, FP64, %.1f s" % (m, tc)}
+    peak, peak_kind = _peaks()
+    achieved = LPT2_BYTES * n ** 3 / t / 1e9
+    line = {"metric": "2LPT displacement (particles/s) at %d^3" % n, "value": n ** 3 / t,
+            "unit": "particles/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d^3 grid, box %g Mpc/h, seed %d, unsmoothed" % (n, w["box"], w["seed"]),
+                       "l2": "inputs larger than L2 (spectra %.1f GB each)" % (8 * n * n * (n // 2 + 1) / 1e9)},
+            "roofline": {"bound": "hbm", "kernel": "2LPT passes (11 kernels)", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "alg_bytes_per_particle": LPT2_BYTES},
+            "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(args.steps * 11), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -552,14 +631,17 @@ def main():
     ap.add_argument("--nscales", type=int, default=0, help="number of radii; default 40")
     ap.add_argument("--velocities", action="store_true",
                     help="also keep v_max (the displacement smoothed on R_max): 9 fields per radius")
-    ap.add_argument("--workload", default="paper", choices=["paper", "ensemble", "fragment"],
+    ap.add_argument("--workload", default="paper", choices=["paper", "ensemble", "fragment", "2lpt"],
                     help="paper: 768^3 x 40 (the metric); ensemble: 64 x 128^3 batched vs sequential; "
-                         "fragment: the fragmentation front end on the 768^3 F_max field")
+                         "fragment: the fragmentation front end on the 768^3 F_max field; "
+                         "2lpt: the second-order displacement of the 768^3 field")
     args = ap.parse_args()
     if args.workload == "ensemble":
         return run_ensemble(args)
     if args.workload == "fragment":
         return run_fragment(args)
+    if args.workload == "2lpt":
+        return run_2lpt(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

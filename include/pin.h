@@ -121,6 +121,21 @@ pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, in
  * on_device semantics as pin_collapse_times. */
 pin_status pin_velocities(pin_plan_t p, float* psi_max, int on_device);
 
+/* Second-order LPT displacement of the unsmoothed field, for halo positions
+ * beyond the Zel'dovich approximation (Sec. 4 names 2LPT as the next step for
+ * them; the formula is the standard one of second-order Lagrangian
+ * perturbation theory).  With phi_ij the deformation tensor at R = 0 (the
+ * Hessian of pin_hessian, unsmoothed) and its second invariant
+ *   S(q) = sum_{i<j} (phi_ii phi_jj - phi_ij^2),
+ *   psi2(k) = (3/7) i k S(k) / k^2,
+ * so that div psi2 = -(3/7) S and, with D2 = -(3/7) D^2, the position is
+ * x = q + D psi + D^2 psi2 (psi from pin_displacements).  Output
+ * psi2 = [3][N^3] floats in Mpc/h (odd-order Nyquist modes zeroed as for
+ * psi).  Uses the plan's spectra as scratch (batch 1 only; any collapse state
+ * is kept, the next pin_collapse_times rebuilds the spectra).  Same on_device
+ * semantics as pin_collapse_times. */
+pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device);
+
 /* Fragmentation front end (Sec. 2.1.2): the fragmentation considers the
  * particles in descending F_max (an effectively chronological order) and,
  * for each, the halos its six neighbours belong to.  From the F_max of the

@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and
 by bench.py's cpu_baseline / reference leg.  The product path never imports
 it.  Everything here is argument marshalling around oracle/pin_oracle.c,
-except fragment_order (Sec. 2.1.2), a few lines of numpy.
+except fragment_order (Sec. 2.1.2) and the 2LPT source and its transform in
+displacement_2lpt, a few lines of numpy.
 """
 import ctypes
 import os
@@ -247,3 +248,17 @@ def fragment_order(F_max):
         for shift in (1, -1):
             n_before += np.roll(R, shift, axis=axis) < R
     return order, n_before
+
+
+def displacement_2lpt(delta_half, box):
+    """Second-order LPT displacement of the unsmoothed field (the standard
+    second-order Lagrangian perturbation theory result): with phi_ij the
+    deformation tensor at R = 0, S = sum_{i<j} (phi_ii phi_jj - phi_ij^2) and
+    psi2(k) = (3/7) i k S(k) / k^2.  The Hessian and the final displacement are
+    the C oracle's; numpy's rfftn is the forward transform of S (same sign and
+    normalisation convention as delta(k))."""
+    h, _ = hessian(delta_half, box, 0.0)
+    xx, yy, zz, xy, xz, yz = h
+    S = xx * yy + xx * zz + yy * zz - xy ** 2 - xz ** 2 - yz ** 2
+    Sk = np.fft.rfftn(S)
+    return displacement((3.0 / 7.0) * Sk, box, 0.0)

@@ -319,8 +319,10 @@ template <int N> __host__ __device__ constexpr int field_stride() {
 // smoothed displacement components, kept for the velocity at R_max).
 // FUSE: the collapse time and the running maximum of every particle follow
 // its eigenvalues in this kernel (no eigenvalue round trip through memory);
-// otherwise the eigenvalues go to lam_out for k_roots.
-template <int N, int LINES, bool DUMP, int NP, bool FUSE>
+// otherwise the eigenvalues go to lam_out for k_roots.  SRC: instead, the
+// second-order LPT source S = sum_{i<j} (phi_ii phi_jj - phi_ij^2) of every
+// particle goes to out[0] (a real field).
+template <int N, int LINES, bool DUMP, int NP, bool FUSE, bool SRC = false>
 __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_pass_z(ArgsZ a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P, NTW = Shape<N>::kTw;
   constexpr int NC = NP * LINES;  // pair-columns of the block
@@ -401,7 +403,18 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
     __syncthreads();
     constexpr int kPts = LINES * N;
     const size_t total = (size_t)nlines * N;
-    if constexpr (FUSE) {
+    if constexpr (SRC) {
+      for (int pt = tid; pt < kPts; pt += nthreads) {
+        const int l = pt / N, z = pt % N;
+        const int gl = blockIdx.x * LINES + l;
+        if (gl >= nlines) continue;
+        float h[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) h[f] = s_f[(l * NF + f) * kFS + z];
+        a.out[0][(size_t)gl * N + z] =
+            h[0] * h[1] + h[0] * h[2] + h[1] * h[2] - h[3] * h[3] - h[4] * h[4] - h[5] * h[5];
+      }
+    } else if constexpr (FUSE) {
       // eigenvalues, collapse time and running maximum, PIN_Z_ILP particles
       // per thread and iteration
       constexpr int U = PIN_Z_ILP;
@@ -529,6 +542,80 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
         }
       }
     }
+  }
+}
+
+// --------------------------------------------------- forward z (real in) --
+// T(x, y, kz) = sum_z s(x, y, z) exp(+2 pi i z kz / N) for kz in [0, N/2] of
+// every real line s (the inverse-sign transform of real data; its conjugate is
+// the forward transform).  Two lines A, B ride one complex transform of A + iB,
+// Z = T_A + i T_B, and are separated with T_A(k) = (Z(k) + conj Z(N-k)) / 2,
+// T_B(k) = (Z(k) - conj Z(N-k)) / 2i.  Output in the padded half-spectrum
+// layout (kz stride nhp, pad modes zero).
+template <int N, int NC>
+__global__ void __launch_bounds__(NC * Shape<N>::P) k_fwd_z(const float* __restrict__ src, float2* dst, int nlines,
+                                                          int nhp, const float2* tw) {
+  constexpr int E = Shape<N>::E, P = Shape<N>::P, NTW = Shape<N>::kTw;
+  using L = XLayoutLines<E, P, NC, Shape<N>::P1>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* s_x = reinterpret_cast<float2*>(smem_raw);
+  constexpr int kXBytes = L::kSize * 8, kZBytes = NC * N * 8;
+  constexpr int kBufBytes = kXBytes > kZBytes ? kXBytes : kZBytes;
+  float2* s_tw = reinterpret_cast<float2*>(smem_raw + kBufBytes);
+  float2* s_z = s_x;  // after the transform: Z of each pair, [NC][N]
+  const int tid = threadIdx.x, c = tid / P, p = tid % P;
+  for (int i = tid; i < NTW; i += NC * P) s_tw[i] = tw[i];
+  __syncthreads();
+  const int la = 2 * (blockIdx.x * NC + c);  // lines la, la + 1
+  const bool active = la < nlines;
+  float2 v[E];
+  const float* A = src + (size_t)(active ? la : 0) * N;
+#pragma unroll
+  for (int t = 0; t < E; ++t) {
+    const int n = p + P * t;
+    v[t] = active ? make_float2(__ldg(A + n), __ldg(A + N + n)) : make_float2(0.f, 0.f);
+  }
+  fft_line<N, L>(v, p, c, s_x, s_tw);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < E; ++j) s_z[c * N + fft_out_index<N>(p, j)] = v[j];
+  __syncthreads();
+  if (!active) return;
+  float2* oa = dst + (size_t)la * nhp;
+  float2* ob = oa + nhp;
+  for (int k = p; k < nhp; k += P) {
+    float2 ta = make_float2(0.f, 0.f), tb = make_float2(0.f, 0.f);
+    if (k <= N / 2) {
+      const float2 zk = s_z[c * N + k], zm = s_z[c * N + (k == 0 ? 0 : N - k)];
+      ta = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      tb = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+    }
+    oa[k] = ta;
+    ob[k] = tb;
+  }
+}
+
+// Phi2(k) = scale conj(T(k)) / k^2 on the padded half-spectrum (k = 0 and
+// pad modes zero): with T the inverse-sign transform of the 2LPT source, the
+// potential whose gradient i k Phi2 is the second-order displacement.
+__global__ void k_phi2(const float2* __restrict__ T, float2* out, int n, int nhp, double box, float scale) {
+  const size_t total = (size_t)n * n * nhp;
+  const float kf = (float)(2.0 * M_PI / box);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int iz = (int)(i % nhp);
+    const size_t row = i / nhp;
+    const int iy = (int)(row % n), ix = (int)(row / n);
+    float2 r = make_float2(0.f, 0.f);
+    if (iz <= n / 2) {
+      const int sx = ix < n / 2 ? ix : ix - n, sy = iy < n / 2 ? iy : iy - n;
+      const float k2 = kf * kf * (float)(sx * sx + sy * sy + iz * iz);
+      if (k2 > 0.f) {
+        const float2 t = T[i];
+        const float f = scale / k2;
+        r = make_float2(f * t.x, -f * t.y);
+      }
+    }
+    out[i] = r;
   }
 }
 
@@ -678,6 +765,11 @@ template <int N> struct Cfg {
   static constexpr size_t fzv = (size_t)LINES_V * 10 * field_stride<N>() * 4;
   static constexpr size_t smem_zv = (xzv > fzv ? xzv : fzv) + (size_t)NTW * 8;
   static constexpr int threads_zv = 5 * LINES_V * P;
+  // forward z: NCF complex transforms (two real lines each) per block
+  static constexpr int NCF = P >= 64 ? 3 : 3 * (64 / P);
+  static constexpr size_t xf = (size_t)XLayoutLines<E, P, NCF, P1>::kSize * 8;
+  static constexpr size_t zf = (size_t)NCF * N * 8;
+  static constexpr size_t smem_fz = (xf > zf ? xf : zf) + (size_t)NTW * 8;
 };
 
 template <int N>
@@ -695,6 +787,11 @@ static cudaError_t set_attrs() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_pass_z<N, C::LINES_V, false, 5, C::FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)C::smem_zv);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass_z<N, C::LINES, false, 3, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_z);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fwd_z<N, C::NCF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_fz);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_pass_z<N, C::LINES, true, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)C::smem_z);
@@ -759,6 +856,24 @@ static cudaError_t run_z(const ArgsZ& a, bool dump, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int N>
+static cudaError_t run_z_source(const ArgsZ& a, cudaStream_t st) {
+  using C = Cfg<N>;
+  const unsigned grid = (unsigned)((a.nlines + C::LINES - 1) / C::LINES);
+  k_pass_z<N, C::LINES, false, 3, false, true><<<grid, C::threads_z, C::smem_z, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t run_fwd_z(const float* src, float2* dst, int nlines, int nhp, const float2* tw,
+                             cudaStream_t st) {
+  using C = Cfg<N>;
+  const int pairs = nlines / 2;
+  const unsigned grid = (unsigned)((pairs + C::NCF - 1) / C::NCF);
+  k_fwd_z<N, C::NCF><<<grid, C::NCF * C::P, C::smem_fz, st>>>(src, dst, nlines, nhp, tw);
+  return cudaGetLastError();
+}
+
 #define PIN_SIZES(X) X(8) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
 
 bool z_fuses_roots(int n) {
@@ -813,6 +928,34 @@ cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st) {
 #undef CASE
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_z_source(int n, const ArgsZ& a, cudaStream_t st) {
+  switch (n) {
+#define CASE(N) case N: return run_z_source<N>(a, st);
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fwd_z(int n, const float* src, float2* dst, int nlines, int nhp, const float2* tw,
+                         cudaStream_t st) {
+  if (nlines % 2) return cudaErrorInvalidValue;
+  switch (n) {
+#define CASE(N) case N: return run_fwd_z<N>(src, dst, nlines, nhp, tw, st);
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_phi2(const float2* T, float2* out, int n, int nhp, double box, float scale, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_phi2<<<sms * 8, 256, 0, st>>>(T, out, n, nhp, box, scale);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st) {

@@ -125,6 +125,14 @@ cudaError_t prepare_kernels(int n);  // sets shared-memory attributes (once per 
 cudaError_t launch_x(int n, const ArgsX& a, cudaStream_t st);
 cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st);
 cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st);
+// Second-order LPT pieces: the z pass writing the source S of every particle
+// (from the six fields in src[0..5]) to out[0]; the inverse-sign transform
+// along z of real lines (nlines of them, an even number) into a padded
+// half-spectrum; and Phi2 = scale conj(T) / k^2.
+cudaError_t launch_z_source(int n, const ArgsZ& a, cudaStream_t st);
+cudaError_t launch_fwd_z(int n, const float* src, float2* dst, int nlines, int nhp, const float2* tw,
+                         cudaStream_t st);
+cudaError_t launch_phi2(const float2* T, float2* out, int n, int nhp, double box, float scale, cudaStream_t st);
 // True when the z pass of size n also computes the collapse times and the
 // running maximum (launch_roots is then not called for that size).
 bool z_fuses_roots(int n);

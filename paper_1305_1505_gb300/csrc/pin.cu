@@ -230,10 +230,12 @@ void release(pin_plan_t p) {
 float2* spec(pin_plan_t p, float2* base, int f) { return base + (size_t)f * p->field_elems; }
 
 // Filter-and-transform passes of one radius (mult set `ms`), ending in the
-// collapse update (dump == nullptr) or a dump of the six real components.
-pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
+// collapse update (dump and source null), a dump of the six real components,
+// or the 2LPT source field S of every particle (source, batch 1).
+pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, float* source = nullptr) {
   const float* mult = p->mult + (size_t)ms * 3 * p->n;
-  const bool rec = p->profile && dump == nullptr && !p->events.empty();
+  const bool collapse = dump == nullptr && source == nullptr;
+  const bool rec = p->profile && collapse && !p->events.empty();
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 0], p->stream, cudaEventRecordExternal));
   ArgsX ax{};
   ax.tm = p->tm_x;
@@ -265,7 +267,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
     ay.zm[o] = zm[o];
     ay.muli[o] = 0;
   }
-  if (p->velocities && !dump) {
+  if (p->velocities && collapse) {
     // smoothed displacement psi = i k W Phi0 shares the y transforms of
     // xz (psi_x: z factor W), zz (psi_z: z factor k W) and yz (psi_y: z factor W)
     ay.dst2[2] = spec(p, p->V, 6);
@@ -288,11 +290,11 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 2], p->stream, cudaEventRecordExternal));
 
   ArgsZ az{};
-  const int nf = (p->velocities && !dump) ? 9 : 6;
+  const int nf = (p->velocities && collapse) ? 9 : 6;
   for (int f = 0; f < nf; ++f) az.src[f] = spec(p, p->V, f);
   az.nfields = nf;
   az.psi_out = p->psi;
-  az.vstate = (p->velocities && !dump) ? p->vstate : nullptr;
+  az.vstate = (p->velocities && collapse) ? p->vstate : nullptr;
   az.nlines = p->n * p->n * p->batch;
   az.npart = az.nlines * p->n;
   az.lam_out = reinterpret_cast<float*>(p->U);  // the x-pass spectra are free by now
@@ -312,6 +314,11 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump) {
   az.redo_cap = p->redo_cap;
   if (dump)
     for (int f = 0; f < 6; ++f) az.out[f] = dump[f];
+  if (source) {
+    az.out[0] = source;
+    PIN_CK(p, launch_z_source(p->n, az, p->stream));
+    return PIN_OK;
+  }
   if (!dump) PIN_CK(p, cudaMemsetAsync(p->redo_count, 0, sizeof(unsigned), p->stream));
   PIN_CK(p, launch_z(p->n, az, dump != nullptr, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 3], p->stream, cudaEventRecordExternal));
@@ -635,6 +642,128 @@ pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
   if (e != cudaSuccess) st = cuda_fail(p, e, "displacement passes");
   if (st == PIN_OK && !on_device) {
     e = cudaMemcpyAsync(psi, dev, 3 * n3 * 4, cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) st = cuda_fail(p, e, "cudaMemcpyAsync");
+  }
+  if (!on_device) {
+    cudaFreeAsync(dev, p->stream);
+    if (st == PIN_OK) st = finish_host(p);
+  }
+  return st;
+}
+
+// The three displacement passes psi = IDFT(i k Phi) of a potential spectrum
+// Phi (padded half-spectrum, R = 0: no smoothing), through the spectra a0, a1
+// (x-pass outputs, stored back to back) and b0..b2 (y-pass outputs), into
+// out = [3][N^3].
+static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float2* b0, float* out) {
+  const size_t n3 = (size_t)p->n * p->n * p->n;
+  const float* mult = p->mult + (size_t)p->nscales * 3 * p->n;  // R = 0
+  ArgsX ax{};
+  cudaError_t e = make_tmap_x(&ax.tm, phi, p->n, p->nhp, 1);
+  if (e != cudaSuccess) return e;
+  ax.src = phi;
+  ax.dst[0] = a0;
+  ax.dst[1] = a0 + p->field_elems;
+  ax.xm[0] = 0;
+  ax.xm[1] = 1;
+  ax.nout = 2;
+  ax.mult = mult;
+  ax.tw = p->tw;
+  ax.nhp = p->nhp;
+  ax.batch = 1;
+  ax.err = p->err;
+  e = launch_x(p->n, ax, p->stream);
+  if (e != cudaSuccess) return e;
+  // psi_x <- a1 (k_x), psi_y <- a0 (k_y), psi_z <- a0 (z: k_z); all times i
+  ArgsY ay{};
+  e = make_tmap_y(&ay.tm, a0, p->n, p->nhp, p->field_elems, 1);
+  if (e != cudaSuccess) return e;
+  ay.src[0] = a0;
+  ay.src[1] = a0 + p->field_elems;
+  ay.src[2] = a0 + 2 * p->field_elems;
+  const int sel[3] = {1, 0, 0}, ym[3] = {0, 1, 0}, zm[3] = {0, 0, 1};
+  for (int f = 0; f < 3; ++f) {
+    ay.dst[f] = b0 + (size_t)f * p->field_elems;
+    ay.sel[f] = sel[f];
+    ay.ym[f] = ym[f];
+    ay.zm[f] = zm[f];
+    ay.muli[f] = 1;
+  }
+  ay.nout = 3;
+  ay.mult = mult;
+  ay.tw = p->tw;
+  ay.nhp = p->nhp;
+  ay.batch = 1;
+  ay.err = p->err;
+  e = launch_y(p->n, ay, p->stream);
+  if (e != cudaSuccess) return e;
+  ArgsZ az{};
+  for (int f = 0; f < 3; ++f) {
+    az.src[f] = b0 + (size_t)f * p->field_elems;
+    az.out[f] = out + (size_t)f * n3;
+  }
+  az.nfields = 3;
+  az.nlines = p->n * p->n;
+  az.tw = p->tw;
+  az.nhp = p->nhp;
+  return launch_z(p->n, az, true, p->stream);
+}
+
+pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!psi2) return fail(p, PIN_EINVAL, "null output");
+  if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_displacements_2lpt needs a plan with batch 1");
+  if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
+  const int n = p->n;
+  const size_t n3 = (size_t)n * n * n;
+  float* dev = psi2;
+  if (!on_device) PIN_CK(p, cudaMallocAsync((void**)&dev, 3 * n3 * 4, p->stream));
+  float2* U0 = spec(p, p->U, 0);
+  float2* V0 = spec(p, p->V, 0);
+  float* S = reinterpret_cast<float*>(U0);  // N^3 floats fit in one padded spectrum
+  // 1) the unsmoothed deformation tensor, reduced per particle to the source S
+  st = enqueue_radius(p, p->nscales, 0, nullptr, S);
+  // 2) T = inverse-sign transform of S: z into V0, y into V1, x into V2; the
+  //    R = 0 multipliers scale each y and x line by 1/N and the y outputs by a
+  //    further 1/N (z factor), so T / N^3 arrives in V2
+  cudaError_t e = cudaSuccess;
+  if (st == PIN_OK) e = launch_fwd_z(n, S, V0, n * n, p->nhp, p->tw, p->stream);
+  if (st == PIN_OK && e == cudaSuccess) {
+    const float* mult = p->mult + (size_t)p->nscales * 3 * n;
+    ArgsY ay{};
+    e = make_tmap_y(&ay.tm, V0, n, p->nhp, p->field_elems, 1);
+    ay.src[0] = V0;
+    ay.src[1] = V0;
+    ay.src[2] = V0;
+    ay.dst[0] = spec(p, p->V, 1);
+    ay.nout = 1;
+    ay.mult = mult;
+    ay.tw = p->tw;
+    ay.nhp = p->nhp;
+    ay.batch = 1;
+    ay.err = p->err;
+    if (e == cudaSuccess) e = launch_y(n, ay, p->stream);
+    ArgsX ax{};
+    if (e == cudaSuccess) e = make_tmap_x(&ax.tm, spec(p, p->V, 1), n, p->nhp, 1);
+    ax.src = spec(p, p->V, 1);
+    ax.dst[0] = spec(p, p->V, 2);
+    ax.nout = 1;
+    ax.mult = mult;
+    ax.tw = p->tw;
+    ax.nhp = p->nhp;
+    ax.batch = 1;
+    ax.err = p->err;
+    if (e == cudaSuccess) e = launch_x(n, ax, p->stream);
+    // 3) Phi2 = (3/7) S(k) / k^2 with S(k) = conj(T) (forward transform of real S), into U0
+    if (e == cudaSuccess)
+      e = launch_phi2(spec(p, p->V, 2), U0, n, p->nhp, p->box, (float)(3.0 / 7.0 * (double)n3), p->stream);
+    // 4) psi2 = IDFT(i k Phi2)
+    if (e == cudaSuccess) e = enqueue_gradient(p, U0, spec(p, p->V, 0), spec(p, p->V, 3), dev);
+    if (e != cudaSuccess) st = cuda_fail(p, e, "2LPT passes");
+  }
+  if (st == PIN_OK && !on_device) {
+    e = cudaMemcpyAsync(psi2, dev, 3 * n3 * 4, cudaMemcpyDeviceToHost, p->stream);
     if (e != cudaSuccess) st = cuda_fail(p, e, "cudaMemcpyAsync");
   }
   if (!on_device) {

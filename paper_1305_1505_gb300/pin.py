@@ -47,7 +47,8 @@ class pin_stats(ctypes.Structure):
 EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_hessian",
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
-           "pin_fragment_order", "pin_strerror", "pin_last_error", "pin_destroy")
+           "pin_fragment_order", "pin_displacements_2lpt", "pin_strerror", "pin_last_error",
+           "pin_destroy")
 
 _lib = None
 
@@ -75,6 +76,8 @@ def load(path=None):
     L.pin_velocities.restype = ctypes.c_int
     L.pin_fragment_order.argtypes = [P, P, P, ctypes.c_int]
     L.pin_fragment_order.restype = ctypes.c_int
+    L.pin_displacements_2lpt.argtypes = [P, P, ctypes.c_int]
+    L.pin_displacements_2lpt.restype = ctypes.c_int
     L.pin_hessian.argtypes = [P, ctypes.c_int, P, ctypes.c_int]
     L.pin_hessian.restype = ctypes.c_int
     L.pin_displacements.argtypes = [P, P, ctypes.c_int]
@@ -158,6 +161,10 @@ def pin_fragment_order(plan, order_ptr, n_before_ptr, on_device):
     _check(load().pin_fragment_order(plan, ctypes.c_void_p(order_ptr) if order_ptr else None,
                                      ctypes.c_void_p(n_before_ptr) if n_before_ptr else None,
                                      int(on_device)), plan)
+
+
+def pin_displacements_2lpt(plan, out_ptr, on_device):
+    _check(load().pin_displacements_2lpt(plan, ctypes.c_void_p(out_ptr), int(on_device)), plan)
 
 
 def pin_hessian(plan, scale, out_ptr, on_device):
@@ -313,6 +320,16 @@ class Plan:
                            c.data_ptr() if c is not None else 0, 1)
         self.sync()
         return o, c
+
+    def displacements_2lpt(self):
+        """(3, n, n, n) second-order LPT displacement of the unsmoothed field."""
+        import torch
+        n = self.n
+        out = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        pin_displacements_2lpt(self.handle, out.data_ptr(), 1)
+        self.sync()
+        return out
 
     def hessian(self, scale):
         import torch

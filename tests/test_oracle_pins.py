@@ -504,3 +504,47 @@ def test_fragment_order_invariants():
     o2, nb2 = oracle.fragment_order(np.zeros((4, 4, 4), dtype=np.float32))
     assert np.array_equal(o2, np.arange(64))
     assert nb2[0, 0, 0] == 0 and nb2[3, 3, 3] == 6 and nb2[1, 1, 1] == 3
+
+
+# ---- second-order LPT displacement ----
+
+def _half_spectrum(field):
+    """Forward-convention half-spectrum D(k) = sum_q d(q) e^{-ik.q} of a real
+    field, in the [kx][ky][kz <= N/2] layout (numpy's rfftn)."""
+    return np.fft.rfftn(field)
+
+
+def test_2lpt_vanishes_for_a_plane_wave():
+    # one Fourier mode: the deformation tensor has rank one, its second
+    # invariant is zero, and the motion is exactly Zel'dovich
+    n, box = 16, 64.0
+    x = np.arange(n) * box / n
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    k = 2 * np.pi / box
+    d = 0.7 * np.cos(2 * k * X + 3 * k * Y - k * Z)
+    psi2 = oracle.displacement_2lpt(_half_spectrum(d), box)
+    assert np.abs(psi2).max() < 1e-12
+
+
+def test_2lpt_two_crossed_waves_closed_form():
+    # delta = A cos(k1 x) + B cos(k2 y): phi_xx = A cos(k1 x), phi_yy = B cos(k2 y),
+    # S = A B cos(k1 x) cos(k2 y) = (AB/2) [cos(K+.q) + cos(K-.q)], K+- = (k1, +-k2, 0),
+    # and each c cos(K.q) gives psi2 = -(3/7) c K sin(K.q) / K^2
+    n, box = 16, 64.0
+    x = np.arange(n) * box / n
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    k1, k2 = 2 * np.pi * 2 / box, 2 * np.pi * 3 / box
+    A, B = 0.8, -0.5
+    d = A * np.cos(k1 * X) + B * np.cos(k2 * Y)
+    psi2 = oracle.displacement_2lpt(_half_spectrum(d), box)
+    K2 = k1 ** 2 + k2 ** 2
+    sp, sm = np.sin(k1 * X + k2 * Y), np.sin(k1 * X - k2 * Y)
+    c = -(3.0 / 7.0) * A * B / 2 / K2
+    assert np.allclose(psi2[0], c * k1 * (sp + sm), atol=1e-12)
+    assert np.allclose(psi2[1], c * k2 * (sp - sm), atol=1e-12)
+    assert np.abs(psi2[2]).max() < 1e-12
+    # div psi2 = -(3/7) S, read back spectrally from the result
+    kk = 2 * np.pi * np.fft.fftfreq(n, d=box / n)
+    div = sum(np.real(np.fft.ifftn(1j * np.meshgrid(kk, kk, kk, indexing="ij")[i] * np.fft.fftn(psi2[i])))
+              for i in range(3))
+    assert np.allclose(div, -(3.0 / 7.0) * A * B * np.cos(k1 * X) * np.cos(k2 * Y), atol=1e-12)
