@@ -16,12 +16,14 @@
  *    of the last error of a plan is available from pin_last_error().
  *  - The caller owns every input and output buffer; the plan owns all device
  *    workspace (pin_footprint_bytes() tells how much).
- *  - Half-spectra are [N][N][N/2+1] complex, row major, index
- *    (ix*N + iy)*(N/2+1) + iz; the signed wavenumber index of i is i for
- *    i < N/2 and i - N otherwise (the Nyquist index is -N/2), k = 2 pi s / L
- *    with L in Mpc/h.  DFT convention: d(q) = N^-3 sum_k D(k) e^{+i k.q}; the
- *    kz = 0 and kz = N/2 planes must be Hermitian (D(-kx,-ky) = conj D(kx,ky)).
- *  - Real fields are [N][N][N] row major, q = (x*N + y)*N + z.
+ *  - Half-spectra are [nx][ny][nz/2+1] complex, row major, index
+ *    (ix*ny + iy)*(nz/2+1) + iz; the signed wavenumber index of i along an
+ *    axis of n points is i for i < n/2 and i - n otherwise (the Nyquist index
+ *    is -n/2), k = 2 pi s / L with L the side of that axis in Mpc/h.  DFT
+ *    convention: d(q) = (nx ny nz)^-1 sum_k D(k) e^{+i k.q}; the kz = 0 and
+ *    kz = nz/2 planes must be Hermitian (D(-kx,-ky) = conj D(kx,ky)).
+ *    "N^3" below stands for nx*ny*nz.
+ *  - Real fields are [nx][ny][nz] row major, q = (x*ny + y)*nz + z.
  *  - Calls on one plan are not re-entrant; different plans may be used from
  *    different threads.  Work is enqueued on the plan's CUDA stream.
  *  - No call makes a device wait without bound: pin_sync() takes a timeout.
@@ -53,8 +55,11 @@ enum { PIN_FP32_FALLBACK64 = 0 };
 enum { PIN_C64 = 0, PIN_C128 = 1 };
 
 typedef struct {
-  int nx, ny, nz;        /* grid; must be equal, N in {8,16,32,48,64,96,128,192,256,384,512,768} */
-  double box;            /* side L in Mpc/h, > 0 */
+  int nx, ny, nz;        /* grid, each in {8,16,32,48,64,96,128,192,256,384,512,768}; they
+                            may differ (the paper's code runs on non-cubic grids as well,
+                            Sec. 2.1.1); the cells are cubic */
+  double box;            /* side along x in Mpc/h, > 0; the sides along y and z are
+                            box ny / nx and box nz / nx */
   int nscales;           /* number of radii S, 1..64 */
   const double* radii;   /* S radii in Mpc/h (Gaussian sigma, >= 0); copied at pin_plan;
                             processed in the given order, index 0 first (callers

@@ -42,6 +42,13 @@ def lib():
         L.or_displacement_r.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
         L.or_hessian_points.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp]
+        L.or_hessian3.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, _dp, _dp]
+        L.or_displacement3.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, _dp]
+        L.or_collapse_times3.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int, _dp, ctypes.c_int, _dp, _ip, _dp, _dp, _ip, _dp,
+                                         _dp]
         L.or_eig3.argtypes = [_dp, _dp]
         L.or_axis_coeffs.argtypes = [_dp, ctypes.c_int, _dp]
         L.or_first_root.argtypes = [_dp]
@@ -70,6 +77,12 @@ def _c128(a):
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
+def _grid(half):
+    """(nx, ny, nz) of a half-spectrum of shape (nx, ny, nz/2 + 1), nz even."""
+    nx, ny, nh = half.shape
+    return nx, ny, 2 * (nh - 1)
+
+
 def dft1d(x, sign=+1):
     """Unnormalised 1D DFT with exp(sign 2 pi i jk/n)."""
     x = _c128(x)
@@ -86,24 +99,25 @@ def idft3d(a):
 
 
 def hessian(delta_half, box, radius):
-    """(6, n, n, n) FP64 deformation tensor xx, yy, zz, xy, xz, yz, and the
-    largest imaginary residue of the inverse transforms."""
+    """(6, nx, ny, nz) FP64 deformation tensor xx, yy, zz, xy, xz, yz, and the
+    largest imaginary residue of the inverse transforms (cubic cells: box is
+    the side along x)."""
     d = _c128(delta_half)
-    n = d.shape[0]
-    out = np.empty((6, n, n, n), dtype=np.float64)
+    nx, ny, nz = _grid(d)
+    out = np.empty((6, nx, ny, nz), dtype=np.float64)
     mi = ctypes.c_double()
-    rc = lib().or_hessian(_p(d.view(np.float64)), n, box, radius, _p(out), ctypes.byref(mi))
+    rc = lib().or_hessian3(_p(d.view(np.float64)), nx, ny, nz, box, radius, _p(out), ctypes.byref(mi))
     if rc:
         raise ValueError("or_hessian failed: %d" % rc)
     return out, mi.value
 
 
 def displacement(delta_half, box, radius=0.0):
-    """(3, n, n, n) FP64 Zel'dovich displacement psi = i k W(kR) delta / k^2."""
+    """(3, nx, ny, nz) FP64 Zel'dovich displacement psi = i k W(kR) delta / k^2."""
     d = _c128(delta_half)
-    n = d.shape[0]
-    out = np.empty((3, n, n, n), dtype=np.float64)
-    rc = lib().or_displacement_r(_p(d.view(np.float64)), n, box, radius, _p(out))
+    nx, ny, nz = _grid(d)
+    out = np.empty((3, nx, ny, nz), dtype=np.float64)
+    rc = lib().or_displacement3(_p(d.view(np.float64)), nx, ny, nz, box, radius, _p(out))
     if rc:
         raise ValueError("or_displacement failed: %d" % rc)
     return out
@@ -176,10 +190,10 @@ def collapse_times(delta_half, box, radii, correction=1, keep_all=False, velocit
     (S, n^3) when keep_all, and vmax (3, n^3: the smoothed displacement at the
     radius of F_max) when velocities."""
     d = _c128(delta_half)
-    n = d.shape[0]
+    nx, ny, nz = _grid(d)
     r = np.ascontiguousarray(radii, dtype=np.float64)
     S = r.size
-    n3 = n ** 3
+    n3 = nx * ny * nz
     fmax = np.empty(n3)
     idx = np.empty(n3, dtype=np.int32)
     f2 = np.empty(n3)
@@ -187,7 +201,7 @@ def collapse_times(delta_half, box, radii, correction=1, keep_all=False, velocit
     slope = np.empty(n3)
     f_all = np.empty((S, n3)) if keep_all else None
     vmax = np.empty((3, n3)) if velocities else None
-    rc = lib().or_collapse_times(_p(d.view(np.float64)), n, box, S, _p(r), correction,
+    rc = lib().or_collapse_times3(_p(d.view(np.float64)), nx, ny, nz, box, S, _p(r), correction,
                                  _p(fmax), _p(idx, ctypes.c_int), _p(f_all), _p(f2),
                                  _p(idx2, ctypes.c_int), _p(slope), _p(vmax))
     if rc:
@@ -262,3 +276,21 @@ def displacement_2lpt(delta_half, box):
     S = xx * yy + xx * zz + yy * zz - xy ** 2 - xz ** 2 - yz ** 2
     Sk = np.fft.rfftn(S)
     return displacement((3.0 / 7.0) * Sk, box, 0.0)
+
+
+def sigma2(shape, box, radius, power=None):
+    """Variance of the Gaussian-smoothed field on an nx x ny x nz grid with
+    cubic cells (box is the side along x), as the radius schedule reads
+    Sec. 2.1.1: V^-1 sum over every mode k != 0 of the grid of
+    P(k) exp(-k^2 R^2).  power: P(k) for an array of k (default: the power
+    spectrum of the initial conditions).  A direct sum over all modes."""
+    from paper_1305_1505_gb300 import ic
+    nx, ny, nz = shape
+    L = [box, box * ny / nx, box * nz / nx]
+    k = [2 * np.pi * (np.arange(n) - n // 2) / Li for n, Li in zip(shape, L)]
+    k2 = k[0][:, None, None] ** 2 + k[1][None, :, None] ** 2 + k[2][None, None, :] ** 2
+    kk = np.sqrt(k2.ravel())
+    nz_mask = kk > 0
+    P = np.zeros(kk.size)
+    P[nz_mask] = (ic.power(kk[nz_mask]) if power is None else power(kk[nz_mask]))
+    return float(np.sum(P * np.exp(-k2.ravel() * radius * radius)) / (L[0] * L[1] * L[2]))

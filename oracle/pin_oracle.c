@@ -100,42 +100,52 @@ void or_dft1d(const double* in_ri, int n, int sign, double* out_ri) {
   else dft_direct(in, n, sign, out);
 }
 
-/* In-place 3D inverse DFT of a full complex cube a[n][n][n] (row major,
- * last index fastest), normalised by n^-3: one 1D transform per line along
- * each axis in turn. */
-static void idft3d(double complex* a, int n) {
-  const size_t n2 = (size_t)n * n;
+/* In-place 3D inverse DFT of a full complex box a[nx][ny][nz] (row major,
+ * last index fastest), normalised by (nx ny nz)^-1: one 1D transform per
+ * line along each axis in turn (x, then y, then z). */
+static void idft3d3(double complex* a, int nx, int ny, int nz) {
+  const int len[3] = {nx, ny, nz};
+  const size_t stride[3] = {(size_t)ny * nz, (size_t)nz, 1};
+  const size_t total = (size_t)nx * ny * nz;
   for (int axis = 0; axis < 3; ++axis) {
-    size_t stride = axis == 0 ? n2 : (axis == 1 ? (size_t)n : 1);
+    const int n = len[axis];
+    const size_t st = stride[axis];
+    const long long nlines = (long long)(total / n);
 #pragma omp parallel
     {
       double complex* line = malloc(sizeof(double complex) * n);
       double complex* res = malloc(sizeof(double complex) * n);
 #pragma omp for schedule(static)
-      for (long long l = 0; l < (long long)n2; ++l) {
-        /* enumerate the n^2 lines orthogonal to this axis */
-        size_t u = (size_t)l / n, v = (size_t)l % n, base;
-        if (axis == 0) base = u * n + v;
-        else if (axis == 1) base = u * n2 + v;
-        else base = u * n2 + v * n;
-        for (int j = 0; j < n; ++j) line[j] = a[base + j * stride];
+      for (long long l = 0; l < nlines; ++l) {
+        /* the lines orthogonal to this axis: (y, z), (x, z) or (x, y) */
+        size_t base;
+        if (axis == 0) base = (size_t)l;
+        else if (axis == 1) base = (size_t)(l / nz) * ny * nz + (size_t)(l % nz);
+        else base = (size_t)l * nz;
+        for (int j = 0; j < n; ++j) line[j] = a[base + j * st];
         or_dft1d((const double*)line, n, +1, (double*)res);
-        for (int j = 0; j < n; ++j) a[base + j * stride] = res[j];
+        for (int j = 0; j < n; ++j) a[base + j * st] = res[j];
       }
       free(line);
       free(res);
     }
   }
-  const double norm = 1.0 / ((double)n * n * n);
+  const double norm = 1.0 / ((double)nx * ny * nz);
 #pragma omp parallel for schedule(static)
-  for (long long i = 0; i < (long long)(n2 * n); ++i) a[i] *= norm;
+  for (long long i = 0; i < (long long)total; ++i) a[i] *= norm;
 }
+
+static void idft3d(double complex* a, int n) { idft3d3(a, n, n, n); }
 
 void or_idft3d(double* a_ri, int n) { idft3d((double complex*)a_ri, n); }
 
 /* ------------------------------------------------------------- filter -- */
 
 static int signed_index(int i, int n) { return i < n / 2 ? i : i - n; }
+
+/* Cubic cells: the box side along x is `box`; an axis of m points has side
+ * box m / nx (exactly box when m = nx). */
+static double axis_len(double box, int m, int nx) { return m == nx ? box : box * m / nx; }
 
 /* Component c of the symmetric tensor, in the order xx, yy, zz, xy, xz, yz. */
 static const int COMP_I[6] = {0, 1, 2, 0, 0, 1};
@@ -145,55 +155,53 @@ static const int COMP_J[6] = {0, 1, 2, 1, 2, 2};
  * ([n][n][n/2+1]).  Modes with kz > n/2 come from Hermitian symmetry,
  * T(-k) = conj T(k), which the filter preserves (it is an even real function
  * of k once the off-diagonal Nyquist modes are zeroed). */
-static void filtered_full(const double complex* half, int n, double box, double radius,
+static void filtered_full(const double complex* half, int nx, int ny, int nz, double box, double radius,
                           int comp, double complex* full) {
-  const int nh = n / 2 + 1;
+  const int nh = nz / 2 + 1;
   const int ci = COMP_I[comp], cj = COMP_J[comp];
-  const double kf = 2.0 * M_PI / box;
+  const int ns[3] = {nx, ny, nz};
+  const double kf[3] = {2.0 * M_PI / box, 2.0 * M_PI / axis_len(box, ny, nx), 2.0 * M_PI / axis_len(box, nz, nx)};
 #pragma omp parallel for schedule(static)
-  for (int ix = 0; ix < n; ++ix) {
-    for (int iy = 0; iy < n; ++iy) {
-      for (int iz = 0; iz < n; ++iz) {
+  for (int ix = 0; ix < nx; ++ix) {
+    for (int iy = 0; iy < ny; ++iy) {
+      for (int iz = 0; iz < nz; ++iz) {
         /* the stored mode that holds this one, conjugated if mirrored */
-        int sx, sy, sz, mirrored = iz > n / 2;
+        int mirrored = iz > nz / 2;
         size_t src;
         if (!mirrored) {
-          src = ((size_t)ix * n + iy) * nh + iz;
+          src = ((size_t)ix * ny + iy) * nh + iz;
         } else {
-          src = ((size_t)((n - ix) % n) * n + (n - iy) % n) * nh + (n - iz);
+          src = ((size_t)((nx - ix) % nx) * ny + (ny - iy) % ny) * nh + (nz - iz);
         }
-        /* signed index of THIS mode (iz = n/2 maps to -n/2) */
-        sx = signed_index(ix, n);
-        sy = signed_index(iy, n);
-        sz = signed_index(iz, n);
-        int s[3] = {sx, sy, sz};
-        double k[3] = {kf * sx, kf * sy, kf * sz};
+        /* signed index of THIS mode (iz = nz/2 maps to -nz/2) */
+        int s[3] = {signed_index(ix, nx), signed_index(iy, ny), signed_index(iz, nz)};
+        double k[3] = {kf[0] * s[0], kf[1] * s[1], kf[2] * s[2]};
         double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
         double complex d = mirrored ? conj(half[src]) : half[src];
         double complex t = 0.0;
         if (k2 > 0.0) {
-          int nyq = (ci != cj) && (s[ci] == -n / 2 || s[cj] == -n / 2);
+          int nyq = (ci != cj) && (s[ci] == -ns[ci] / 2 || s[cj] == -ns[cj] / 2);
           if (!nyq) {
             double w = exp(-0.5 * k2 * radius * radius);
             t = k[ci] * k[cj] / k2 * w * d;
           }
         }
-        full[((size_t)ix * n + iy) * n + iz] = t;
+        full[((size_t)ix * ny + iy) * nz + iz] = t;
       }
     }
   }
 }
 
-int or_hessian(const double* delta_half_ri, int n, double box, double radius,
-               double* out6, double* max_imag) {
-  if (n < 2 || (n & 1)) return -1;
-  const size_t n3 = (size_t)n * n * n;
+int or_hessian3(const double* delta_half_ri, int nx, int ny, int nz, double box, double radius,
+                double* out6, double* max_imag) {
+  if (nx < 2 || ny < 2 || nz < 2 || (nz & 1)) return -1;
+  const size_t n3 = (size_t)nx * ny * nz;
   double complex* full = malloc(sizeof(double complex) * n3);
   if (!full) return -2;
   double worst = 0.0;
   for (int c = 0; c < 6; ++c) {
-    filtered_full((const double complex*)delta_half_ri, n, box, radius, c, full);
-    idft3d(full, n);
+    filtered_full((const double complex*)delta_half_ri, nx, ny, nz, box, radius, c, full);
+    idft3d3(full, nx, ny, nz);
     for (size_t q = 0; q < n3; ++q) {
       out6[c * n3 + q] = creal(full[q]);
       double a = fabs(cimag(full[q]));
@@ -203,6 +211,12 @@ int or_hessian(const double* delta_half_ri, int n, double box, double radius,
   if (max_imag) *max_imag = worst;
   free(full);
   return 0;
+}
+
+int or_hessian(const double* delta_half_ri, int n, double box, double radius,
+               double* out6, double* max_imag) {
+  if (n < 2 || (n & 1)) return -1;
+  return or_hessian3(delta_half_ri, n, n, n, box, radius, out6, max_imag);
 }
 
 /* Direct evaluation of phi_c(q) at one grid point from the half-spectrum:
@@ -305,37 +319,44 @@ int or_hessian_points(const double* delta_half_ri, int n, double box, double rad
  * psi_i(k) = i k_i W(kR) delta(k) / k^2, so that delta = -div psi for R = 0.
  * A mode whose k_i sits on the Nyquist index is zeroed for component i (the
  * odd multiplier breaks Hermitian symmetry). */
-int or_displacement_r(const double* delta_half_ri, int n, double box, double radius, double* out3) {
-  if (n < 2 || (n & 1)) return -1;
+int or_displacement3(const double* delta_half_ri, int nx, int ny, int nz, double box, double radius,
+                     double* out3) {
+  if (nx < 2 || ny < 2 || nz < 2 || (nz & 1)) return -1;
   const double complex* half = (const double complex*)delta_half_ri;
-  const int nh = n / 2 + 1;
-  const size_t n3 = (size_t)n * n * n;
-  const double kf = 2.0 * M_PI / box;
+  const int nh = nz / 2 + 1;
+  const int ns[3] = {nx, ny, nz};
+  const size_t n3 = (size_t)nx * ny * nz;
+  const double kf[3] = {2.0 * M_PI / box, 2.0 * M_PI / axis_len(box, ny, nx), 2.0 * M_PI / axis_len(box, nz, nx)};
   double complex* full = malloc(sizeof(double complex) * n3);
   if (!full) return -2;
   for (int c = 0; c < 3; ++c) {
 #pragma omp parallel for schedule(static)
-    for (int ix = 0; ix < n; ++ix) {
-      for (int iy = 0; iy < n; ++iy) {
-        for (int iz = 0; iz < n; ++iz) {
-          int mirrored = iz > n / 2;
-          size_t src = mirrored ? ((size_t)((n - ix) % n) * n + (n - iy) % n) * nh + (n - iz)
-                                : ((size_t)ix * n + iy) * nh + iz;
-          int s[3] = {signed_index(ix, n), signed_index(iy, n), signed_index(iz, n)};
-          double k[3] = {kf * s[0], kf * s[1], kf * s[2]};
+    for (int ix = 0; ix < nx; ++ix) {
+      for (int iy = 0; iy < ny; ++iy) {
+        for (int iz = 0; iz < nz; ++iz) {
+          int mirrored = iz > nz / 2;
+          size_t src = mirrored ? ((size_t)((nx - ix) % nx) * ny + (ny - iy) % ny) * nh + (nz - iz)
+                                : ((size_t)ix * ny + iy) * nh + iz;
+          int s[3] = {signed_index(ix, nx), signed_index(iy, ny), signed_index(iz, nz)};
+          double k[3] = {kf[0] * s[0], kf[1] * s[1], kf[2] * s[2]};
           double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
           double complex d = mirrored ? conj(half[src]) : half[src];
           double complex t = 0.0;
-          if (k2 > 0.0 && s[c] != -n / 2) t = I * k[c] / k2 * exp(-0.5 * k2 * radius * radius) * d;
-          full[((size_t)ix * n + iy) * n + iz] = t;
+          if (k2 > 0.0 && s[c] != -ns[c] / 2) t = I * k[c] / k2 * exp(-0.5 * k2 * radius * radius) * d;
+          full[((size_t)ix * ny + iy) * nz + iz] = t;
         }
       }
     }
-    idft3d(full, n);
+    idft3d3(full, nx, ny, nz);
     for (size_t q = 0; q < n3; ++q) out3[c * n3 + q] = creal(full[q]);
   }
   free(full);
   return 0;
+}
+
+int or_displacement_r(const double* delta_half_ri, int n, double box, double radius, double* out3) {
+  if (n < 2 || (n & 1)) return -1;
+  return or_displacement3(delta_half_ri, n, n, n, box, radius, out3);
 }
 
 int or_displacement(const double* delta_half_ri, int n, double box, double* out3) {
@@ -515,11 +536,11 @@ double or_collapse_slope(const double* lam) {
 
 /* --------------------------------------------------------- trajectory -- */
 
-int or_collapse_times(const double* delta_half_ri, int n, double box, int nscales,
-                      const double* radii, int correction, double* fmax, int* idx,
-                      double* f_all, double* f2, int* idx2, double* slope, double* vmax) {
-  if (n < 2 || (n & 1) || nscales < 1) return -1;
-  const size_t n3 = (size_t)n * n * n;
+int or_collapse_times3(const double* delta_half_ri, int nx, int ny, int nz, double box, int nscales,
+                       const double* radii, int correction, double* fmax, int* idx,
+                       double* f_all, double* f2, int* idx2, double* slope, double* vmax) {
+  if (nx < 2 || ny < 2 || nz < 2 || (nz & 1) || nscales < 1) return -1;
+  const size_t n3 = (size_t)nx * ny * nz;
   double* h = malloc(sizeof(double) * 6 * n3);
   double* psi = vmax ? malloc(sizeof(double) * 3 * n3) : NULL;
   if (!h || (vmax && !psi)) { free(h); free(psi); return -2; }
@@ -532,8 +553,8 @@ int or_collapse_times(const double* delta_half_ri, int n, double box, int nscale
     if (slope) slope[q] = 0.0;
   }
   for (int s = 0; s < nscales; ++s) {
-    int rc = or_hessian(delta_half_ri, n, box, radii[s], h, NULL);
-    if (!rc && vmax) rc = or_displacement_r(delta_half_ri, n, box, radii[s], psi);
+    int rc = or_hessian3(delta_half_ri, nx, ny, nz, box, radii[s], h, NULL);
+    if (!rc && vmax) rc = or_displacement3(delta_half_ri, nx, ny, nz, box, radii[s], psi);
     if (rc) { free(h); free(psi); return rc; }
 #pragma omp parallel for schedule(static)
     for (long long q = 0; q < (long long)n3; ++q) {
@@ -558,6 +579,14 @@ int or_collapse_times(const double* delta_half_ri, int n, double box, int nscale
   free(h);
   free(psi);
   return 0;
+}
+
+int or_collapse_times(const double* delta_half_ri, int n, double box, int nscales,
+                      const double* radii, int correction, double* fmax, int* idx,
+                      double* f_all, double* f2, int* idx2, double* slope, double* vmax) {
+  if (n < 2 || (n & 1) || nscales < 1) return -1;
+  return or_collapse_times3(delta_half_ri, n, n, n, box, nscales, radii, correction, fmax, idx, f_all, f2,
+                            idx2, slope, vmax);
 }
 
 int or_collapse_times_sampled(const double* delta_half_ri, int n, double box, int nscales,

@@ -5,6 +5,8 @@
  *
  * Complex arrays are interleaved (re, im) doubles.  Half-spectra are
  * [n][n][n/2+1]; real fields and outputs are [n][n][n], q = (x n + y) n + z.
+ * The *3 variants take a grid of nx x ny x nz points with cubic cells (box
+ * is the side along x): half-spectra [nx][ny][nz/2+1], fields [nx][ny][nz].
  * Hessian components are ordered xx, yy, zz, xy, xz, yz.
  */
 #ifndef PIN_ORACLE_H
@@ -20,6 +22,13 @@ int or_hessian_points(const double* delta_half_ri, int n, double box, double rad
                       const long long* q_list, double* out);
 int or_displacement(const double* delta_half_ri, int n, double box, double* out3);
 int or_displacement_r(const double* delta_half_ri, int n, double box, double radius, double* out3);
+int or_hessian3(const double* delta_half_ri, int nx, int ny, int nz, double box, double radius,
+                double* out6, double* max_imag);
+int or_displacement3(const double* delta_half_ri, int nx, int ny, int nz, double box, double radius,
+                     double* out3);
+int or_collapse_times3(const double* delta_half_ri, int nx, int ny, int nz, double box, int nscales,
+                       const double* radii, int correction, double* fmax, int* idx,
+                       double* f_all, double* f2, int* idx2, double* slope, double* vmax);
 void or_eig3(const double* h6, double* lam);
 void or_axis_coeffs(const double* lam, int i, double* c);
 double or_first_root(const double* c);

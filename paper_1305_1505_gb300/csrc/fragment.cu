@@ -224,27 +224,28 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restr
 // Number of the six periodic neighbours (+-1 along x, y, z) that come before
 // particle q in the order: larger F_max, or equal F_max and smaller index.
 // One block per (x, y) line; the six neighbour lines are read in step along z.
-__global__ void __launch_bounds__(256) k_neighbours_before(const float* __restrict__ F, int n, uint8_t* out) {
-  const int line = blockIdx.x;  // x n + y
-  const int x = line / n, y = line - x * n;
-  const int xp = x + 1 == n ? 0 : x + 1, xm = x == 0 ? n - 1 : x - 1;
-  const int yp = y + 1 == n ? 0 : y + 1, ym = y == 0 ? n - 1 : y - 1;
-  const int lines[4] = {xp * n + y, xm * n + y, x * n + yp, x * n + ym};
-  const int q0 = line * n;  // N^3 < 2^31
-  for (int z = threadIdx.x; z < n; z += blockDim.x) {
+__global__ void __launch_bounds__(256) k_neighbours_before(const float* __restrict__ F, int nx, int ny, int nz,
+                                                           uint8_t* out) {
+  const int line = blockIdx.x;  // x ny + y
+  const int x = line / ny, y = line - x * ny;
+  const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+  const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+  const int lines[4] = {xp * ny + y, xm * ny + y, x * ny + yp, x * ny + ym};
+  const int q0 = line * nz;  // nx ny nz < 2^31
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
     const int q = q0 + z;
     const float f = __ldg(F + q);
-    const int zp = z + 1 == n ? 0 : z + 1, zm = z == 0 ? n - 1 : z - 1;
+    const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
     int c = 0;
-    const int nz[2] = {q0 + zp, q0 + zm};
+    const int zs[2] = {q0 + zp, q0 + zm};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const float g = __ldg(F + nz[k]);
-      c += (g > f) | ((g == f) & (nz[k] < q));
+      const float g = __ldg(F + zs[k]);
+      c += (g > f) | ((g == f) & (zs[k] < q));
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int r = lines[k] * n + z;
+      const int r = lines[k] * nz + z;
       const float g = __ldg(F + r);
       c += (g > f) | ((g == f) & (r < q));
     }
@@ -261,11 +262,12 @@ size_t fragment_scratch_bytes(long n3) {
   return (size_t)n3 * 16 + (size_t)m * 4 + (size_t)nchunks * 4 + 256;
 }
 
-cudaError_t fragment_order(const float* fmax, int n, void* scratch, int32_t* order, uint8_t* n_before,
-                           cudaStream_t st) {
-  const long n3 = (long)n * n * n;
+cudaError_t fragment_order(const float* fmax, int nx, int ny, int nz, void* scratch, int32_t* order,
+                           uint8_t* n_before, cudaStream_t st) {
+  const long n3 = (long)nx * ny * nz;
   if (n_before) {
-    k_neighbours_before<<<(unsigned)(n * n), n < 256 ? ((n + 31) / 32) * 32 : 256, 0, st>>>(fmax, n, n_before);
+    k_neighbours_before<<<(unsigned)(nx * ny), nz < 256 ? ((nz + 31) / 32) * 32 : 256, 0, st>>>(fmax, nx, ny, nz,
+                                                                                              n_before);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(co
     mbar_init_fence();
   }
   __syncthreads();
-  const int ncols = N * a.nhp;
+  const int ncols = a.ny * a.nhp;
   const int tpr = (ncols + TC - 1) / TC;  // tiles per realisation; the last may run past ncols
   const int ntiles = tpr * a.batch;        // realisation r owns rows [r N, r N + N)
   auto issue = [&](int tile) {
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
   __syncthreads();
   const int nhp = a.nhp, nout = a.nout;
   const int ktiles = (nhp + TC - 1) / TC;
-  const int ntiles = N * a.batch * ktiles;  // x planes of all realisations, back to back
+  const int ntiles = a.nx * a.batch * ktiles;  // x planes of all realisations, back to back
   auto issue = [&](int tile, int src) {
     const int x = tile / ktiles, kz0 = (tile % ktiles) * TC;
     mbar_expect_tx(bar, N * TC * 8);
@@ -263,9 +263,14 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
           }
         }
       }
+      // z factors of this column (kz <= nz/2; pad columns carry zeros anyway),
+      // requested before the transform so that their latency is hidden
+      const int nz = a.nz;
+      const float zf = (ok && kz <= nz / 2) ? __ldg(a.mult_z + s_zm[o] * nz + kz) : 0.f;
+      float zf2 = 0.f;
+      if constexpr (DUAL)
+        zf2 = (ok && s_dst2[o] != nullptr && kz <= nz / 2) ? __ldg(a.mult_z + s_zm2[o] * nz + kz) : 0.f;
       fft_line<N, L>(v, p, c, s_x, s_tw);
-      // z factor of this column (kz <= N/2; pad columns carry zeros anyway)
-      const float zf = (ok && kz <= N / 2) ? s_m[s_zm[o] * N + kz] : 0.f;
       const bool mi = s_mi[o] != 0;
       float2* d = s_dst[o] + base;
       if constexpr (DUAL) {
@@ -274,7 +279,6 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(co
         // that each slot dies after its two stores
         float2* d2 = s_dst2[o];
         const bool two = ok && d2 != nullptr;
-        const float zf2 = (two && kz <= N / 2) ? s_m[s_zm2[o] * N + kz] : 0.f;
         const bool mi2 = s_mi2[o] != 0;
         d2 = two ? d2 + base : nullptr;
 #pragma unroll
@@ -598,17 +602,21 @@ __global__ void __launch_bounds__(NC * Shape<N>::P) k_fwd_z(const float* __restr
 // Phi2(k) = scale conj(T(k)) / k^2 on the padded half-spectrum (k = 0 and
 // pad modes zero): with T the inverse-sign transform of the 2LPT source, the
 // potential whose gradient i k Phi2 is the second-order displacement.
-__global__ void k_phi2(const float2* __restrict__ T, float2* out, int n, int nhp, double box, float scale) {
-  const size_t total = (size_t)n * n * nhp;
-  const float kf = (float)(2.0 * M_PI / box);
+// Cubic cells: the box side along x is `box`, L_y = box ny / nx, L_z = box nz / nx.
+__global__ void k_phi2(const float2* __restrict__ T, float2* out, int nx, int ny, int nz, int nhp, double box,
+                       float scale) {
+  const size_t total = (size_t)nx * ny * nhp;
+  const float kfx = (float)(2.0 * M_PI / box), kfy = (float)(2.0 * M_PI / (ny == nx ? box : box * ny / nx)),
+              kfz = (float)(2.0 * M_PI / (nz == nx ? box : box * nz / nx));
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const int iz = (int)(i % nhp);
     const size_t row = i / nhp;
-    const int iy = (int)(row % n), ix = (int)(row / n);
+    const int iy = (int)(row % ny), ix = (int)(row / ny);
     float2 r = make_float2(0.f, 0.f);
-    if (iz <= n / 2) {
-      const int sx = ix < n / 2 ? ix : ix - n, sy = iy < n / 2 ? iy : iy - n;
-      const float k2 = kf * kf * (float)(sx * sx + sy * sy + iz * iz);
+    if (iz <= nz / 2) {
+      const int sx = ix < nx / 2 ? ix : ix - nx, sy = iy < ny / 2 ? iy : iy - ny;
+      const float kx = kfx * sx, ky = kfy * sy, kz = kfz * iz;
+      const float k2 = kx * kx + ky * ky + kz * kz;
       if (k2 > 0.f) {
         const float2 t = T[i];
         const float f = scale / k2;
@@ -819,7 +827,7 @@ static unsigned persistent_grid(K kernel, int threads, size_t smem, long ntiles)
 template <int N>
 static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
   using C = Cfg<N>;
-  const long ntiles = (((long)N * a.nhp + C::TC - 1) / C::TC) * a.batch;
+  const long ntiles = (((long)a.ny * a.nhp + C::TC - 1) / C::TC) * a.batch;
   const unsigned grid = persistent_grid(k_pass_x<N, C::TC>, C::threads_xy, C::smem_xy, ntiles);
   k_pass_x<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
   return cudaGetLastError();
@@ -828,7 +836,7 @@ static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
 template <int N>
 static cudaError_t run_y(const ArgsY& a, cudaStream_t st) {
   using C = Cfg<N>;
-  const long ntiles = (long)N * a.batch * ((a.nhp + C::TC - 1) / C::TC);
+  const long ntiles = (long)a.nx * a.batch * ((a.nhp + C::TC - 1) / C::TC);
   bool dual = false;
   for (int o = 0; o < a.nout; ++o) dual = dual || a.dst2[o] != nullptr;
   if (dual) {
@@ -950,11 +958,12 @@ cudaError_t launch_fwd_z(int n, const float* src, float2* dst, int nlines, int n
   }
 }
 
-cudaError_t launch_phi2(const float2* T, float2* out, int n, int nhp, double box, float scale, cudaStream_t st) {
+cudaError_t launch_phi2(const float2* T, float2* out, int nx, int ny, int nz, int nhp, double box, float scale,
+                        cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_phi2<<<sms * 8, 256, 0, st>>>(T, out, n, nhp, box, scale);
+  k_phi2<<<sms * 8, 256, 0, st>>>(T, out, nx, ny, nz, nhp, box, scale);
   return cudaGetLastError();
 }
 
@@ -1001,21 +1010,22 @@ static cudaError_t encode(CUtensorMap* tm, int rank, const void* base, const cuu
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int n, int nhp, int batch) {
-  const PassShape sh = pass_shape(n);
-  const int boxes = (n + 255) / 256;
-  const cuuint64_t dims[2] = {(cuuint64_t)n * nhp, (cuuint64_t)n * batch};
-  const cuuint64_t strides[1] = {(cuuint64_t)n * nhp * 8};
-  const cuuint32_t box[2] = {(cuuint32_t)sh.tc, (cuuint32_t)(n / boxes)};
+cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int nhp, int batch) {
+  const PassShape sh = pass_shape(nx);
+  const int boxes = (nx + 255) / 256;
+  const cuuint64_t dims[2] = {(cuuint64_t)ny * nhp, (cuuint64_t)nx * batch};
+  const cuuint64_t strides[1] = {(cuuint64_t)ny * nhp * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)sh.tc, (cuuint32_t)(nx / boxes)};
   return encode(tm, 2, src, dims, strides, box);
 }
 
-cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int n, int nhp, size_t spec_elems, int batch) {
-  const PassShape sh = pass_shape(n);
-  const int boxes = (n + 255) / 256;
-  const cuuint64_t dims[4] = {(cuuint64_t)nhp, (cuuint64_t)n, (cuuint64_t)n * batch, 3};
-  const cuuint64_t strides[3] = {(cuuint64_t)nhp * 8, (cuuint64_t)n * nhp * 8, (cuuint64_t)spec_elems * 8};
-  const cuuint32_t box[4] = {(cuuint32_t)sh.tc, (cuuint32_t)(n / boxes), 1, 1};
+cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int nx, int ny, int nhp, size_t spec_elems,
+                        int batch) {
+  const PassShape sh = pass_shape(ny);
+  const int boxes = (ny + 255) / 256;
+  const cuuint64_t dims[4] = {(cuuint64_t)nhp, (cuuint64_t)ny, (cuuint64_t)nx * batch, 3};
+  const cuuint64_t strides[3] = {(cuuint64_t)nhp * 8, (cuuint64_t)ny * nhp * 8, (cuuint64_t)spec_elems * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)sh.tc, (cuuint32_t)(ny / boxes), 1, 1};
   return encode(tm, 4, src3, dims, strides, box);
 }
 

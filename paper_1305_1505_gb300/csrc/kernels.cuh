@@ -19,27 +19,30 @@ namespace pin {
 
 constexpr int kMaxFields = 9;
 
-// x pass: for each output f, dst[f] = IDFT_x(mult[xm[f]] * src).  The source
-// tiles arrive by TMA: tm is a 2D map over src, {N*nhp columns, batch*N rows}
-// (realisations stacked along rows), box {tc, rows/boxes}.
+// x pass (lines of length nx): for each output f, dst[f] = IDFT_x(mult[xm[f]]
+// * src).  The source tiles arrive by TMA: tm is a 2D map over src,
+// {ny*nhp columns, batch*nx rows} (realisations stacked along rows), box
+// {tc, nx/boxes}.
 struct ArgsX {
   CUtensorMap tm;
   const float2* src;
   float2* dst[3];
   int xm[3];
   int nout;
-  const float* mult;  // [3][N] multipliers of this radius (W, kW, k^2W, each / N)
+  int ny;             // rows of a plane: the columns are (ky, kz), ny * nhp of them
+  const float* mult;  // [3][nx] multipliers of this radius (W, kW, k^2W, each / nx)
   const float2* tw;   // twiddles: w_N^{p k1} [E][P], then w_P^{p1 k2a} [P2][P1] for three levels
   int nhp;
   int batch;          // realisations stacked back to back (same N, radii)
   int* err;           // set to 1 if a TMA wait gave up (bounded wait)
 };
 
-// y pass: dst[f] = zfac[f](kz) * IDFT_y(mult[ym[f]] * src[sel[f]]), where the
-// z factor mult[zm[f]](kz), times i when muli[f], is constant along a y line.
-// Outputs are processed in the given order; consecutive outputs with the same
-// source share one staged tile.  tm is a 4D map over the three source spectra
-// (stored back to back), {nhp, N, batch*N, 3}, box {tc, rows/boxes, 1, 1}.
+// y pass (lines of length ny): dst[f] = zfac[f](kz) * IDFT_y(mult[ym[f]] *
+// src[sel[f]]), where the z factor mult_z[zm[f]](kz), times i when muli[f], is
+// constant along a y line.  Outputs are processed in the given order;
+// consecutive outputs with the same source share one staged tile.  tm is a 4D
+// map over the three source spectra (stored back to back),
+// {nhp, ny, batch*nx, 3}, box {tc, ny/boxes, 1, 1}.
 struct ArgsY {
   CUtensorMap tm;
   const float2* src[3];
@@ -53,7 +56,9 @@ struct ArgsY {
   int zm2[kMaxFields];
   int muli2[kMaxFields];
   int nout;
-  const float* mult;
+  int nx, nz;           // x planes per realisation; z line length (z factors for kz <= nz/2)
+  const float* mult;    // [3][ny] y multipliers
+  const float* mult_z;  // [3][nz] z multipliers
   const float2* tw;
   int nhp;
   int batch;
@@ -116,8 +121,9 @@ struct PassShape {
 // Tensor maps of the x and y passes (host; the encoder comes from the driver
 // entry point, so no driver library is linked).  spec_elems is the stride
 // between the spectra the y map spans.
-cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int n, int nhp, int batch);
-cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int n, int nhp, size_t spec_elems, int batch);
+cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int nhp, int batch);
+cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int nx, int ny, int nhp, size_t spec_elems,
+                        int batch);
 
 bool size_supported(int n);
 PassShape pass_shape(int n);
@@ -132,7 +138,8 @@ cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st);
 cudaError_t launch_z_source(int n, const ArgsZ& a, cudaStream_t st);
 cudaError_t launch_fwd_z(int n, const float* src, float2* dst, int nlines, int nhp, const float2* tw,
                          cudaStream_t st);
-cudaError_t launch_phi2(const float2* T, float2* out, int n, int nhp, double box, float scale, cudaStream_t st);
+cudaError_t launch_phi2(const float2* T, float2* out, int nx, int ny, int nz, int nhp, double box, float scale,
+                        cudaStream_t st);
 // True when the z pass of size n also computes the collapse times and the
 // running maximum (launch_roots is then not called for that size).
 bool z_fuses_roots(int n);
@@ -142,13 +149,13 @@ cudaError_t launch_roots(const ArgsZ& a, cudaStream_t st);
 cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st);
 cudaError_t upload_constant_twiddles();  // per device
 
-// Fragmentation front end (fragment.cu): the particles of one N^3 grid in
+// Fragmentation front end (fragment.cu): the particles of one nx*ny*nz grid in
 // descending F_max (ties: ascending index) into `order`, and the number of
 // their six periodic neighbours that precede them into `n_before`; either
 // output may be null.  `scratch` holds fragment_scratch_bytes(N^3) bytes.
 size_t fragment_scratch_bytes(long n3);
-cudaError_t fragment_order(const float* fmax, int n, void* scratch, int32_t* order, uint8_t* n_before,
-                           cudaStream_t st);
+cudaError_t fragment_order(const float* fmax, int nx, int ny, int nz, void* scratch, int32_t* order,
+                           uint8_t* n_before, cudaStream_t st);
 int fragment_kernels(bool order, bool counts);  // launches of one fragment_order call
 
 }  // namespace pin

@@ -178,8 +178,8 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
   unsigned* redo_count = reinterpret_cast<unsigned*>(base + kOffRedoCount);
   int* err = reinterpret_cast<int*>(base + kOffErr);
   CUtensorMap tm_x, tm_y;
-  if (pin::make_tmap_x(&tm_x, phi0, n, nhp, 1) != cudaSuccess ||
-      pin::make_tmap_y(&tm_y, U, n, nhp, spec, 1) != cudaSuccess)
+  if (pin::make_tmap_x(&tm_x, phi0, n, n, nhp, 1) != cudaSuccess ||
+      pin::make_tmap_y(&tm_y, U, n, n, nhp, spec, 1) != cudaSuccess)
     return PIN_ECUDA;
   pin::RedoEntry* redo_list = reinterpret_cast<pin::RedoEntry*>(base + kOffRedo);
   const double dcorr = noalloc_dcorr();
@@ -206,6 +206,7 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
     ax.src = phi0;
     for (int f = 0; f < 3; ++f) { ax.dst[f] = U + f * spec; ax.xm[f] = f; }
     ax.nout = 3;
+    ax.ny = n;
     ax.mult = m;
     ax.tw = tw;
     ax.nhp = nhp;
@@ -222,7 +223,10 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
       ay.muli[o] = 0;
     }
     ay.nout = 6;
+    ay.nx = n;
+    ay.nz = n;
     ay.mult = m;
+    ay.mult_z = m;  // cubic grid: one table serves every axis
     ay.tw = tw;
     ay.nhp = nhp;
     ay.batch = 1;

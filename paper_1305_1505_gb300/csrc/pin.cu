@@ -24,7 +24,7 @@
 using namespace pin;
 
 struct pin_plan_s {
-  int n = 0, nhp = 0, nscales = 0, correction = 1, precision = 0;
+  int nx = 0, ny = 0, nz = 0, nhp = 0, nscales = 0, correction = 1, precision = 0;
   int batch = 1;          // realisations sharing the grid and radii
   bool velocities = false; // keep the smoothed displacement at R_max (v_max)
   double box = 0.0;
@@ -32,7 +32,7 @@ struct pin_plan_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  PassShape shape{};
+  PassShape shape_x{}, shape_y{}, shape_z{};  // line transforms along x, y, z
   size_t spec_elems = 0;  // complex elements of one padded half-spectrum
   size_t field_elems = 0; // batch * spec_elems: one field of every realisation
   float2* phi0 = nullptr;
@@ -58,6 +58,18 @@ struct pin_plan_s {
   bool profile = false;             // graph carries per-pass event records
   std::vector<cudaEvent_t> events;  // 5 per radius: before x, after x, y, z, roots+redo
   std::string last_error;
+  size_t tw_off[3] = {0, 0, 0};  // per-axis twiddle tables within tw (x, y, z)
+  size_t n3() const { return (size_t)nx * ny * nz; }
+  // multiplier set ms: [3][nx] for x, then [3][ny] for y, then [3][nz] for z
+  size_t mult_set() const { return 3 * (size_t)(nx + ny + nz); }
+  const float* mx(int ms) const { return mult + ms * mult_set(); }
+  const float* my(int ms) const { return mx(ms) + 3 * (size_t)nx; }
+  const float* mz(int ms) const { return my(ms) + 3 * (size_t)ny; }
+  const float2* twx() const { return tw + tw_off[0]; }
+  const float2* twy() const { return tw + tw_off[1]; }
+  const float2* twz() const { return tw + tw_off[2]; }
+  // cubic cells: side of an axis with nax points (exactly box along x)
+  double len(int nax) const { return nax == nx ? box : box * nax / nx; }
 };
 
 namespace {
@@ -107,8 +119,8 @@ double x3_value() {
 
 bool validate(const pin_plan_desc* d, std::string* why) {
   if (!d) { *why = "null descriptor"; return false; }
-  if (d->nx != d->ny || d->ny != d->nz) { *why = "non-cubic grids are not supported"; return false; }
-  if (!size_supported(d->nx)) { *why = "unsupported grid size " + std::to_string(d->nx); return false; }
+  for (int m : {d->nx, d->ny, d->nz})
+    if (!size_supported(m)) { *why = "unsupported grid size " + std::to_string(m); return false; }
   if (!(d->box > 0.0) || !std::isfinite(d->box)) { *why = "box must be positive"; return false; }
   if (d->nscales < 1 || d->nscales > 64) { *why = "nscales must be in 1..64"; return false; }
   if (!d->radii) { *why = "null radii"; return false; }
@@ -119,24 +131,26 @@ bool validate(const pin_plan_desc* d, std::string* why) {
   if (d->velocities != 0 && d->velocities != 1) { *why = "velocities must be 0 or 1"; return false; }
   const long long b = d->batch <= 0 ? 1 : d->batch;
   if (b > 4096) { *why = "batch must be in 1..4096"; return false; }
-  if (b * (long long)d->nx * d->nx * d->nx >= (1ll << 31)) { *why = "batch * N^3 must stay below 2^31"; return false; }
+  if (b * (long long)d->nx * d->ny * d->nz >= (1ll << 31)) {
+    *why = "batch * nx * ny * nz must stay below 2^31";
+    return false;
+  }
   return true;
 }
 
 // FP64 redo queue capacity: 1/64 of the grid (observed rate ~2e-4), at least 64 Ki.
-unsigned redo_capacity(int n, int batch) {
-  const size_t n3 = (size_t)n * n * n * batch;
-  return (unsigned)std::max<size_t>(65536, n3 / 64);
+unsigned redo_capacity(size_t n3, int batch) {
+  return (unsigned)std::max<size_t>(65536, n3 * batch / 64);
 }
 
 int batch_of(const pin_plan_desc* d) { return d->batch <= 0 ? 1 : d->batch; }
 
-size_t footprint(int n, int nscales, int batch, bool velocities) {
-  const size_t spec = (size_t)n * n * padded_half(n) * batch;
-  const size_t n3 = (size_t)n * n * n * batch;
+size_t footprint(int nx, int ny, int nz, int nscales, int batch, bool velocities) {
+  const size_t spec = (size_t)nx * ny * padded_half(nz) * batch;
+  const size_t n3 = (size_t)nx * ny * nz * batch;
   return spec * 8 * (velocities ? 13 : 10) + n3 * 8 + (velocities ? n3 * 24 : 0) +
-         (size_t)(nscales + 1) * 3 * n * 4 + (size_t)n * 8 + 64 +
-         (size_t)redo_capacity(n, batch) * sizeof(RedoEntry) + 16 + sizeof(int);
+         (size_t)(nscales + 1) * 3 * (nx + ny + nz) * 4 + (size_t)(nx + ny + nz + 3 * 64) * 8 + 64 +
+         (size_t)redo_capacity((size_t)nx * ny * nz, batch) * sizeof(RedoEntry) + 16 + sizeof(int);
 }
 
 // Per-axis multipliers for one radius: {W, k W, k^2 W} / n with
@@ -152,16 +166,18 @@ void fill_mult(float* out, int n, double box, double radius) {
   }
 }
 
-__global__ void k_load_phi0(const void* src, int dtype, int n, int nhp, double box, int batch,
+// Cubic cells: the side along x is `box`, L_y = box ny / nx, L_z = box nz / nx.
+__global__ void k_load_phi0(const void* src, int dtype, int nx, int ny, int nz, int nhp, double box, int batch,
                             float2* phi0) {
-  const int nh = n / 2 + 1;
-  const size_t total = (size_t)n * n * nhp * batch;
-  const double kf = 2.0 * M_PI / box;
+  const int nh = nz / 2 + 1;
+  const size_t total = (size_t)nx * ny * nhp * batch;
+  const double kfx = 2.0 * M_PI / box, kfy = 2.0 * M_PI / (ny == nx ? box : box * ny / nx),
+               kfz = 2.0 * M_PI / (nz == nx ? box : box * nz / nx);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     const int iz = (int)(i % nhp);
     const size_t r = i / nhp;
-    const int iy = (int)(r % n), ix = (int)((r / n) % n);  // r runs over realisations too
+    const int iy = (int)(r % ny), ix = (int)((r / ny) % nx);  // r runs over realisations too
     float2 out = make_float2(0.f, 0.f);
     if (iz < nh) {
       const size_t j = r * nh + iz;
@@ -172,9 +188,10 @@ __global__ void k_load_phi0(const void* src, int dtype, int n, int nhp, double b
         const double2 dd = reinterpret_cast<const double2*>(src)[j];
         d = make_float2((float)dd.x, (float)dd.y);
       }
-      const double sx = ix < n / 2 ? ix : ix - n, sy = iy < n / 2 ? iy : iy - n;
-      const double sz = iz < n / 2 ? iz : -(n / 2);
-      const double k2 = kf * kf * (sx * sx + sy * sy + sz * sz);
+      const double sx = ix < nx / 2 ? ix : ix - nx, sy = iy < ny / 2 ? iy : iy - ny;
+      const double sz = iz < nz / 2 ? iz : -(nz / 2);
+      const double kx = kfx * sx, ky = kfy * sy, kz = kfz * sz;
+      const double k2 = kx * kx + ky * ky + kz * kz;
       if (k2 > 0.0) {
         const float inv = (float)(1.0 / k2);
         out = make_float2(d.x * inv, d.y * inv);
@@ -196,10 +213,12 @@ pin_status ensure_device_init(pin_plan_t p) {
     g_tw_done[dev] = 1;
   }
   auto& v = g_attr_done[dev];
-  if ((int)v.size() <= p->n) v.resize(p->n + 1, 0);
-  if (!v[p->n]) {
-    PIN_CK(p, prepare_kernels(p->n));
-    v[p->n] = 1;
+  for (int m : {p->nx, p->ny, p->nz}) {
+    if ((int)v.size() <= m) v.resize(m + 1, 0);
+    if (!v[m]) {
+      PIN_CK(p, prepare_kernels(m));
+      v[m] = 1;
+    }
   }
   return PIN_OK;
 }
@@ -233,7 +252,6 @@ float2* spec(pin_plan_t p, float2* base, int f) { return base + (size_t)f * p->f
 // collapse update (dump and source null), a dump of the six real components,
 // or the 2LPT source field S of every particle (source, batch 1).
 pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, float* source = nullptr) {
-  const float* mult = p->mult + (size_t)ms * 3 * p->n;
   const bool collapse = dump == nullptr && source == nullptr;
   const bool rec = p->profile && collapse && !p->events.empty();
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 0], p->stream, cudaEventRecordExternal));
@@ -242,12 +260,13 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
   ax.src = p->phi0;
   for (int f = 0; f < 3; ++f) { ax.dst[f] = spec(p, p->U, f); ax.xm[f] = f; }
   ax.nout = 3;
-  ax.mult = mult;
-  ax.tw = p->tw;
+  ax.ny = p->ny;
+  ax.mult = p->mx(ms);
+  ax.tw = p->twx();
   ax.nhp = p->nhp;
   ax.batch = p->batch;
   ax.err = p->err;
-  PIN_CK(p, launch_x(p->n, ax, p->stream));
+  PIN_CK(p, launch_x(p->nx, ax, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 1], p->stream, cudaEventRecordExternal));
 
   // y pass, outputs grouped by source so that each staged tile serves them in
@@ -281,12 +300,15 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
     ay.muli2[5] = 1;
   }
   ay.nout = 6;
-  ay.mult = mult;
-  ay.tw = p->tw;
+  ay.nx = p->nx;
+  ay.nz = p->nz;
+  ay.mult = p->my(ms);
+  ay.mult_z = p->mz(ms);
+  ay.tw = p->twy();
   ay.nhp = p->nhp;
   ay.batch = p->batch;
   ay.err = p->err;
-  PIN_CK(p, launch_y(p->n, ay, p->stream));
+  PIN_CK(p, launch_y(p->ny, ay, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 2], p->stream, cudaEventRecordExternal));
 
   ArgsZ az{};
@@ -295,10 +317,10 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
   az.nfields = nf;
   az.psi_out = p->psi;
   az.vstate = (p->velocities && collapse) ? p->vstate : nullptr;
-  az.nlines = p->n * p->n * p->batch;
-  az.npart = az.nlines * p->n;
+  az.nlines = p->nx * p->ny * p->batch;
+  az.npart = az.nlines * p->nz;
   az.lam_out = reinterpret_cast<float*>(p->U);  // the x-pass spectra are free by now
-  az.tw = p->tw;
+  az.tw = p->twz();
   az.nhp = p->nhp;
   az.fmax = p->fmax;
   az.idx = p->idx;
@@ -316,14 +338,14 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
     for (int f = 0; f < 6; ++f) az.out[f] = dump[f];
   if (source) {
     az.out[0] = source;
-    PIN_CK(p, launch_z_source(p->n, az, p->stream));
+    PIN_CK(p, launch_z_source(p->nz, az, p->stream));
     return PIN_OK;
   }
   if (!dump) PIN_CK(p, cudaMemsetAsync(p->redo_count, 0, sizeof(unsigned), p->stream));
-  PIN_CK(p, launch_z(p->n, az, dump != nullptr, p->stream));
+  PIN_CK(p, launch_z(p->nz, az, dump != nullptr, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 3], p->stream, cudaEventRecordExternal));
   if (!dump) {
-    if (!z_fuses_roots(p->n)) PIN_CK(p, launch_roots(az, p->stream));
+    if (!z_fuses_roots(p->nz)) PIN_CK(p, launch_roots(az, p->stream));
     PIN_CK(p, launch_redo(az, p->stream));
   }
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 4], p->stream, cudaEventRecordExternal));
@@ -331,7 +353,7 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
 }
 
 pin_status enqueue_collapse(pin_plan_t p) {
-  const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
+  const size_t n3 = p->n3() * p->batch;
   PIN_CK(p, cudaMemsetAsync(p->fmax, 0, n3 * sizeof(float), p->stream));
   PIN_CK(p, cudaMemsetAsync(p->idx, 0xFF, n3 * sizeof(int), p->stream));
   if (p->velocities) PIN_CK(p, cudaMemsetAsync(p->vstate, 0, 3 * n3 * sizeof(float), p->stream));
@@ -392,7 +414,7 @@ extern "C" {
 size_t pin_footprint_bytes(const pin_plan_desc* d) {
   std::string why;
   if (!validate(d, &why)) return 0;
-  return footprint(d->nx, d->nscales, batch_of(d), d->velocities != 0);
+  return footprint(d->nx, d->ny, d->nz, d->nscales, batch_of(d), d->velocities != 0);
 }
 
 pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
@@ -402,8 +424,10 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   if (!validate(d, &why)) return PIN_EINVAL;
   pin_plan_s* p = new (std::nothrow) pin_plan_s();
   if (!p) return PIN_ENOMEM;
-  p->n = d->nx;
-  p->nhp = padded_half(p->n);
+  p->nx = d->nx;
+  p->ny = d->ny;
+  p->nz = d->nz;
+  p->nhp = padded_half(p->nz);
   p->box = d->box;
   p->nscales = d->nscales;
   p->radii.assign(d->radii, d->radii + d->nscales);
@@ -411,11 +435,13 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   p->precision = d->precision;
   p->batch = batch_of(d);
   p->velocities = d->velocities != 0;
-  p->shape = pass_shape(p->n);
-  p->spec_elems = (size_t)p->n * p->n * p->nhp;
+  p->shape_x = pass_shape(p->nx);
+  p->shape_y = pass_shape(p->ny);
+  p->shape_z = pass_shape(p->nz);
+  p->spec_elems = (size_t)p->nx * p->ny * p->nhp;
   p->field_elems = p->spec_elems * p->batch;
   p->dcorr = 1.0 / delta_c_value() - 1.0 / x3_value();
-  p->redo_cap = redo_capacity(p->n, p->batch);
+  p->redo_cap = redo_capacity(p->n3(), p->batch);
   auto bail = [&](pin_status s) {
     release(p);
     delete p;
@@ -429,8 +455,16 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
     if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PIN_ECUDA);
     p->own_stream = true;
   }
-  const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
-  const size_t mult_elems = (size_t)(p->nscales + 1) * 3 * p->n;
+  const size_t n3 = p->n3() * p->batch;
+  const size_t mult_elems = (size_t)(p->nscales + 1) * p->mult_set();
+  // twiddle tables of the three axes, back to back
+  const PassShape* shapes[3] = {&p->shape_x, &p->shape_y, &p->shape_z};
+  const int ns[3] = {p->nx, p->ny, p->nz};
+  size_t tw_elems = 0;
+  for (int a = 0; a < 3; ++a) {
+    p->tw_off[a] = tw_elems;
+    tw_elems += (size_t)ns[a] + (shapes[a]->P2 > 1 ? shapes[a]->P : 0);
+  }
   if (cudaMalloc(&p->phi0, p->field_elems * 8) != cudaSuccess ||
       cudaMalloc(&p->U, 3 * p->field_elems * 8) != cudaSuccess ||
       cudaMalloc(&p->V, (p->velocities ? 9 : 6) * p->field_elems * 8) != cudaSuccess ||
@@ -438,7 +472,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
                          cudaMalloc(&p->vstate, 3 * n3 * 4) != cudaSuccess)) ||
       cudaMalloc(&p->fmax, n3 * 4) != cudaSuccess || cudaMalloc(&p->idx, n3 * 4) != cudaSuccess ||
       cudaMalloc(&p->mult, mult_elems * 4) != cudaSuccess ||
-      cudaMalloc(&p->tw, ((size_t)p->n + p->shape.P) * 8) != cudaSuccess ||
+      cudaMalloc(&p->tw, tw_elems * 8) != cudaSuccess ||
       cudaMalloc(&p->counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&p->redo_list, (size_t)p->redo_cap * sizeof(RedoEntry)) != cudaSuccess ||
       cudaMalloc(&p->redo_count, sizeof(unsigned)) != cudaSuccess ||
@@ -447,30 +481,38 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
     return bail(PIN_ENOMEM);
   }
   std::vector<float> mult(mult_elems);
-  for (int s = 0; s < p->nscales; ++s) fill_mult(mult.data() + (size_t)s * 3 * p->n, p->n, p->box, p->radii[s]);
-  fill_mult(mult.data() + (size_t)p->nscales * 3 * p->n, p->n, p->box, 0.0);
-  // twiddles w_N^{p k1} in [k1][p] order; for a three-level line (P = P1 P2)
-  // then w_P^{p1 k2a} in [k2a][p1] order
-  const int E = p->shape.E, P = p->shape.P, P1 = p->shape.P1, P2 = p->shape.P2;
-  std::vector<float2> tw((size_t)p->n + (P2 > 1 ? P : 0));
-  for (int k1 = 0; k1 < E; ++k1)
-    for (int q = 0; q < P; ++q) {
-      const double ang = 2.0 * M_PI * (double)((long)q * k1 % p->n) / p->n;
-      tw[(size_t)k1 * P + q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    }
-  if (P2 > 1)
-    for (int k2a = 0; k2a < P2; ++k2a)
-      for (int q1 = 0; q1 < P1; ++q1) {
-        const double ang = 2.0 * M_PI * (double)(q1 * k2a % P) / P;
-        tw[(size_t)p->n + k2a * P1 + q1] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  for (int s = 0; s <= p->nscales; ++s) {
+    const double R = s < p->nscales ? p->radii[s] : 0.0;  // the last set has R = 0
+    float* m = mult.data() + (size_t)s * p->mult_set();
+    fill_mult(m, p->nx, p->len(p->nx), R);
+    fill_mult(m + 3 * (size_t)p->nx, p->ny, p->len(p->ny), R);
+    fill_mult(m + 3 * (size_t)(p->nx + p->ny), p->nz, p->len(p->nz), R);
+  }
+  // per axis: twiddles w_N^{p k1} in [k1][p] order; for a three-level line
+  // (P = P1 P2) then w_P^{p1 k2a} in [k2a][p1] order
+  std::vector<float2> tw(tw_elems);
+  for (int a = 0; a < 3; ++a) {
+    const int n = ns[a], E = shapes[a]->E, P = shapes[a]->P, P1 = shapes[a]->P1, P2 = shapes[a]->P2;
+    float2* t = tw.data() + p->tw_off[a];
+    for (int k1 = 0; k1 < E; ++k1)
+      for (int q = 0; q < P; ++q) {
+        const double ang = 2.0 * M_PI * (double)((long)q * k1 % n) / n;
+        t[(size_t)k1 * P + q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
       }
+    if (P2 > 1)
+      for (int k2a = 0; k2a < P2; ++k2a)
+        for (int q1 = 0; q1 < P1; ++q1) {
+          const double ang = 2.0 * M_PI * (double)(q1 * k2a % P) / P;
+          t[(size_t)n + k2a * P1 + q1] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+  }
   if (cudaMemcpy(p->mult, mult.data(), mult_elems * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(p->counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess)
     return bail(PIN_ECUDA);
-  if (make_tmap_x(&p->tm_x, p->phi0, p->n, p->nhp, p->batch) != cudaSuccess ||
-      make_tmap_y(&p->tm_y, p->U, p->n, p->nhp, p->field_elems, p->batch) != cudaSuccess)
+  if (make_tmap_x(&p->tm_x, p->phi0, p->nx, p->ny, p->nhp, p->batch) != cudaSuccess ||
+      make_tmap_y(&p->tm_y, p->U, p->nx, p->ny, p->nhp, p->field_elems, p->batch) != cudaSuccess)
     return bail(PIN_ECUDA);
   *out = p;
   return PIN_OK;
@@ -481,8 +523,8 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
   if (st != PIN_OK) return st;
   if (!delta_k) return fail(p, PIN_EINVAL, "null delta_k");
   if (dtype != PIN_C64 && dtype != PIN_C128) return fail(p, PIN_EINVAL, "dtype must be PIN_C64 or PIN_C128");
-  const size_t nh = (size_t)p->n / 2 + 1;
-  const size_t bytes = (size_t)p->n * p->n * nh * (dtype == PIN_C64 ? 8 : 16) * p->batch;
+  const size_t nh = (size_t)p->nz / 2 + 1;
+  const size_t bytes = (size_t)p->nx * p->ny * nh * (dtype == PIN_C64 ? 8 : 16) * p->batch;
   const void* src = delta_k;
   if (!on_device) {
     // stage through the V workspace (6 spectra >= one C128 half-spectrum)
@@ -492,7 +534,8 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
   const size_t total = p->field_elems;
   const int threads = 256;
   const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, 152 * 64);
-  k_load_phi0<<<blocks, threads, 0, p->stream>>>(src, dtype, p->n, p->nhp, p->box, p->batch, p->phi0);
+  k_load_phi0<<<blocks, threads, 0, p->stream>>>(src, dtype, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch,
+                                                  p->phi0);
   PIN_CK(p, cudaGetLastError());
   if (!on_device) PIN_CK(p, cudaStreamSynchronize(p->stream));
   p->ic_set = true;
@@ -507,7 +550,7 @@ pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, in
   st = ensure_graph(p);
   if (st != PIN_OK) return st;
   PIN_CK(p, cudaGraphLaunch(p->graph_exec, p->stream));
-  const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
+  const size_t n3 = p->n3() * p->batch;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   PIN_CK(p, cudaMemcpyAsync(F_max, p->fmax, n3 * 4, kind, p->stream));
   PIN_CK(p, cudaMemcpyAsync(scale_idx, p->idx, n3 * 4, kind, p->stream));
@@ -522,7 +565,7 @@ pin_status pin_velocities(pin_plan_t p, float* psi_max, int on_device) {
   if (!psi_max) return fail(p, PIN_EINVAL, "null output");
   if (!p->velocities) return fail(p, PIN_EINVAL, "the plan was created without velocities");
   if (p->calls == 0) return fail(p, PIN_ESTATE, "pin_collapse_times has not been called");
-  const size_t n3 = (size_t)p->n * p->n * p->n * p->batch;
+  const size_t n3 = p->n3() * p->batch;
   PIN_CK(p, cudaMemcpyAsync(psi_max, p->vstate, 3 * n3 * 4,
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
   if (!on_device) return finish_host(p);
@@ -535,7 +578,7 @@ pin_status pin_fragment_order(pin_plan_t p, int32_t* order, uint8_t* n_before, i
   if (!order && !n_before) return fail(p, PIN_EINVAL, "both outputs are null");
   if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_fragment_order needs a plan with batch 1");
   if (p->calls == 0) return fail(p, PIN_ESTATE, "pin_collapse_times has not been called");
-  const long n3 = (long)p->n * p->n * p->n;
+  const long n3 = (long)p->n3();
   // the y-pass spectra are free once the radius loop is done: sort scratch,
   // and (for host outputs) the device copies of the results after it
   const size_t need = fragment_scratch_bytes(n3);
@@ -551,7 +594,7 @@ pin_status pin_fragment_order(pin_plan_t p, int32_t* order, uint8_t* n_before, i
     if (order) order_dev = reinterpret_cast<int32_t*>(scratch + (size_t)3 * n3 * 4);
     if (n_before) nb_dev = reinterpret_cast<uint8_t*>(scratch + tail);
   }
-  PIN_CK(p, fragment_order(p->fmax, p->n, scratch, order_dev, nb_dev, p->stream));
+  PIN_CK(p, fragment_order(p->fmax, p->nx, p->ny, p->nz, scratch, order_dev, nb_dev, p->stream));
   if (!on_device) {
     if (order) PIN_CK(p, cudaMemcpyAsync(order, order_dev, (size_t)n3 * 4, cudaMemcpyDeviceToHost, p->stream));
     if (n_before) PIN_CK(p, cudaMemcpyAsync(n_before, nb_dev, (size_t)n3, cudaMemcpyDeviceToHost, p->stream));
@@ -567,7 +610,7 @@ pin_status pin_hessian(pin_plan_t p, int scale, float* out6, int on_device) {
   if (scale < 0 || scale >= p->nscales) return fail(p, PIN_EINVAL, "scale index out of range");
   if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_hessian needs a plan with batch 1");
   if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
-  const size_t n3 = (size_t)p->n * p->n * p->n;
+  const size_t n3 = p->n3();
   float* dev = out6;
   if (!on_device) PIN_CK(p, cudaMallocAsync((void**)&dev, 6 * n3 * 4, p->stream));
   float* outs[6];
@@ -584,82 +627,15 @@ pin_status pin_hessian(pin_plan_t p, int scale, float* out6, int on_device) {
   return st;
 }
 
-pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
-  pin_status st = check_plan(p);
-  if (st != PIN_OK) return st;
-  if (!psi) return fail(p, PIN_EINVAL, "null output");
-  if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_displacements needs a plan with batch 1");
-  if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
-  const size_t n3 = (size_t)p->n * p->n * p->n;
-  float* dev = psi;
-  if (!on_device) PIN_CK(p, cudaMallocAsync((void**)&dev, 3 * n3 * 4, p->stream));
-  const float* mult = p->mult + (size_t)p->nscales * 3 * p->n;  // R = 0: no smoothing
-  ArgsX ax{};
-  ax.tm = p->tm_x;
-  ax.src = p->phi0;
-  ax.dst[0] = spec(p, p->U, 0);
-  ax.dst[1] = spec(p, p->U, 1);
-  ax.xm[0] = 0;
-  ax.xm[1] = 1;
-  ax.nout = 2;
-  ax.mult = mult;
-  ax.tw = p->tw;
-  ax.nhp = p->nhp;
-  ax.batch = 1;
-  ax.err = p->err;
-  cudaError_t e = launch_x(p->n, ax, p->stream);
-  // psi_x <- U1, psi_y <- U0 (k_y), psi_z <- U0 (z: k_z); all times i
-  ArgsY ay{};
-  ay.tm = p->tm_y;
-  ay.src[0] = spec(p, p->U, 0);
-  ay.src[1] = spec(p, p->U, 1);
-  ay.src[2] = spec(p, p->U, 2);
-  const int sel[3] = {1, 0, 0}, ym[3] = {0, 1, 0}, zm[3] = {0, 0, 1};
-  for (int f = 0; f < 3; ++f) {
-    ay.dst[f] = spec(p, p->V, f);
-    ay.sel[f] = sel[f];
-    ay.ym[f] = ym[f];
-    ay.zm[f] = zm[f];
-    ay.muli[f] = 1;
-  }
-  ay.nout = 3;
-  ay.mult = mult;
-  ay.tw = p->tw;
-  ay.nhp = p->nhp;
-  ay.batch = 1;
-  ay.err = p->err;
-  if (e == cudaSuccess) e = launch_y(p->n, ay, p->stream);
-  ArgsZ az{};
-  for (int f = 0; f < 3; ++f) {
-    az.src[f] = spec(p, p->V, f);
-    az.out[f] = dev + (size_t)f * n3;
-  }
-  az.nfields = 3;
-  az.nlines = p->n * p->n;
-  az.tw = p->tw;
-  az.nhp = p->nhp;
-  if (e == cudaSuccess) e = launch_z(p->n, az, true, p->stream);
-  if (e != cudaSuccess) st = cuda_fail(p, e, "displacement passes");
-  if (st == PIN_OK && !on_device) {
-    e = cudaMemcpyAsync(psi, dev, 3 * n3 * 4, cudaMemcpyDeviceToHost, p->stream);
-    if (e != cudaSuccess) st = cuda_fail(p, e, "cudaMemcpyAsync");
-  }
-  if (!on_device) {
-    cudaFreeAsync(dev, p->stream);
-    if (st == PIN_OK) st = finish_host(p);
-  }
-  return st;
-}
-
 // The three displacement passes psi = IDFT(i k Phi) of a potential spectrum
 // Phi (padded half-spectrum, R = 0: no smoothing), through the spectra a0, a1
 // (x-pass outputs, stored back to back) and b0..b2 (y-pass outputs), into
 // out = [3][N^3].
 static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float2* b0, float* out) {
-  const size_t n3 = (size_t)p->n * p->n * p->n;
-  const float* mult = p->mult + (size_t)p->nscales * 3 * p->n;  // R = 0
+  const size_t n3 = p->n3();
+  const int r0 = p->nscales;  // the R = 0 multiplier set
   ArgsX ax{};
-  cudaError_t e = make_tmap_x(&ax.tm, phi, p->n, p->nhp, 1);
+  cudaError_t e = make_tmap_x(&ax.tm, phi, p->nx, p->ny, p->nhp, 1);
   if (e != cudaSuccess) return e;
   ax.src = phi;
   ax.dst[0] = a0;
@@ -667,16 +643,17 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
   ax.xm[0] = 0;
   ax.xm[1] = 1;
   ax.nout = 2;
-  ax.mult = mult;
-  ax.tw = p->tw;
+  ax.ny = p->ny;
+  ax.mult = p->mx(r0);
+  ax.tw = p->twx();
   ax.nhp = p->nhp;
   ax.batch = 1;
   ax.err = p->err;
-  e = launch_x(p->n, ax, p->stream);
+  e = launch_x(p->nx, ax, p->stream);
   if (e != cudaSuccess) return e;
   // psi_x <- a1 (k_x), psi_y <- a0 (k_y), psi_z <- a0 (z: k_z); all times i
   ArgsY ay{};
-  e = make_tmap_y(&ay.tm, a0, p->n, p->nhp, p->field_elems, 1);
+  e = make_tmap_y(&ay.tm, a0, p->nx, p->ny, p->nhp, p->field_elems, 1);
   if (e != cudaSuccess) return e;
   ay.src[0] = a0;
   ay.src[1] = a0 + p->field_elems;
@@ -690,12 +667,15 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
     ay.muli[f] = 1;
   }
   ay.nout = 3;
-  ay.mult = mult;
-  ay.tw = p->tw;
+  ay.nx = p->nx;
+  ay.nz = p->nz;
+  ay.mult = p->my(r0);
+  ay.mult_z = p->mz(r0);
+  ay.tw = p->twy();
   ay.nhp = p->nhp;
   ay.batch = 1;
   ay.err = p->err;
-  e = launch_y(p->n, ay, p->stream);
+  e = launch_y(p->ny, ay, p->stream);
   if (e != cudaSuccess) return e;
   ArgsZ az{};
   for (int f = 0; f < 3; ++f) {
@@ -703,10 +683,32 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
     az.out[f] = out + (size_t)f * n3;
   }
   az.nfields = 3;
-  az.nlines = p->n * p->n;
-  az.tw = p->tw;
+  az.nlines = p->nx * p->ny;
+  az.tw = p->twz();
   az.nhp = p->nhp;
-  return launch_z(p->n, az, true, p->stream);
+  return launch_z(p->nz, az, true, p->stream);
+}
+
+pin_status pin_displacements(pin_plan_t p, float* psi, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!psi) return fail(p, PIN_EINVAL, "null output");
+  if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_displacements needs a plan with batch 1");
+  if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
+  const size_t n3 = p->n3();
+  float* dev = psi;
+  if (!on_device) PIN_CK(p, cudaMallocAsync((void**)&dev, 3 * n3 * 4, p->stream));
+  cudaError_t e = enqueue_gradient(p, p->phi0, spec(p, p->U, 0), spec(p, p->V, 0), dev);
+  if (e != cudaSuccess) st = cuda_fail(p, e, "displacement passes");
+  if (st == PIN_OK && !on_device) {
+    e = cudaMemcpyAsync(psi, dev, 3 * n3 * 4, cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) st = cuda_fail(p, e, "cudaMemcpyAsync");
+  }
+  if (!on_device) {
+    cudaFreeAsync(dev, p->stream);
+    if (st == PIN_OK) st = finish_host(p);
+  }
+  return st;
 }
 
 pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
@@ -715,49 +717,54 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
   if (!psi2) return fail(p, PIN_EINVAL, "null output");
   if (p->batch != 1) return fail(p, PIN_EINVAL, "pin_displacements_2lpt needs a plan with batch 1");
   if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
-  const int n = p->n;
-  const size_t n3 = (size_t)n * n * n;
+  const int nx = p->nx, ny = p->ny, nz = p->nz;
+  const size_t n3 = p->n3();
   float* dev = psi2;
   if (!on_device) PIN_CK(p, cudaMallocAsync((void**)&dev, 3 * n3 * 4, p->stream));
   float2* U0 = spec(p, p->U, 0);
   float2* V0 = spec(p, p->V, 0);
-  float* S = reinterpret_cast<float*>(U0);  // N^3 floats fit in one padded spectrum
+  float* S = reinterpret_cast<float*>(U0);  // nx ny nz floats fit in one padded spectrum
   // 1) the unsmoothed deformation tensor, reduced per particle to the source S
   st = enqueue_radius(p, p->nscales, 0, nullptr, S);
   // 2) T = inverse-sign transform of S: z into V0, y into V1, x into V2; the
-  //    R = 0 multipliers scale each y and x line by 1/N and the y outputs by a
-  //    further 1/N (z factor), so T / N^3 arrives in V2
+  //    R = 0 multipliers scale each y line by 1/ny, each x line by 1/nx and
+  //    the y outputs by 1/nz (z factor), so T / (nx ny nz) arrives in V2
   cudaError_t e = cudaSuccess;
-  if (st == PIN_OK) e = launch_fwd_z(n, S, V0, n * n, p->nhp, p->tw, p->stream);
+  if (st == PIN_OK) e = launch_fwd_z(nz, S, V0, nx * ny, p->nhp, p->twz(), p->stream);
   if (st == PIN_OK && e == cudaSuccess) {
-    const float* mult = p->mult + (size_t)p->nscales * 3 * n;
+    const int r0 = p->nscales;
     ArgsY ay{};
-    e = make_tmap_y(&ay.tm, V0, n, p->nhp, p->field_elems, 1);
+    e = make_tmap_y(&ay.tm, V0, nx, ny, p->nhp, p->field_elems, 1);
     ay.src[0] = V0;
     ay.src[1] = V0;
     ay.src[2] = V0;
     ay.dst[0] = spec(p, p->V, 1);
     ay.nout = 1;
-    ay.mult = mult;
-    ay.tw = p->tw;
+    ay.nx = nx;
+    ay.nz = nz;
+    ay.mult = p->my(r0);
+    ay.mult_z = p->mz(r0);
+    ay.tw = p->twy();
     ay.nhp = p->nhp;
     ay.batch = 1;
     ay.err = p->err;
-    if (e == cudaSuccess) e = launch_y(n, ay, p->stream);
+    if (e == cudaSuccess) e = launch_y(ny, ay, p->stream);
     ArgsX ax{};
-    if (e == cudaSuccess) e = make_tmap_x(&ax.tm, spec(p, p->V, 1), n, p->nhp, 1);
+    if (e == cudaSuccess) e = make_tmap_x(&ax.tm, spec(p, p->V, 1), nx, ny, p->nhp, 1);
     ax.src = spec(p, p->V, 1);
     ax.dst[0] = spec(p, p->V, 2);
     ax.nout = 1;
-    ax.mult = mult;
-    ax.tw = p->tw;
+    ax.ny = ny;
+    ax.mult = p->mx(r0);
+    ax.tw = p->twx();
     ax.nhp = p->nhp;
     ax.batch = 1;
     ax.err = p->err;
-    if (e == cudaSuccess) e = launch_x(n, ax, p->stream);
+    if (e == cudaSuccess) e = launch_x(nx, ax, p->stream);
     // 3) Phi2 = (3/7) S(k) / k^2 with S(k) = conj(T) (forward transform of real S), into U0
     if (e == cudaSuccess)
-      e = launch_phi2(spec(p, p->V, 2), U0, n, p->nhp, p->box, (float)(3.0 / 7.0 * (double)n3), p->stream);
+      e = launch_phi2(spec(p, p->V, 2), U0, nx, ny, nz, p->nhp, p->box, (float)(3.0 / 7.0 * (double)n3),
+                      p->stream);
     // 4) psi2 = IDFT(i k Phi2)
     if (e == cudaSuccess) e = enqueue_gradient(p, U0, spec(p, p->V, 0), spec(p, p->V, 3), dev);
     if (e != cudaSuccess) st = cuda_fail(p, e, "2LPT passes");
@@ -806,7 +813,7 @@ pin_status pin_get_stats(pin_plan_t p, pin_stats* out) {
 
 int pin_kernels_per_call(pin_plan_t p) {
   if (!p) return 0;
-  return (z_fuses_roots(p->n) ? 4 : 5) * p->nscales;  // x, y, z, [roots,] redo per radius
+  return (z_fuses_roots(p->nz) ? 4 : 5) * p->nscales;  // x, y, z, [roots,] redo per radius
 }
 
 pin_status pin_profile(pin_plan_t p, int enable) {

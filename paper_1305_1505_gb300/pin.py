@@ -121,9 +121,20 @@ def _check(status, plan=None):
         raise PinError(status, msg)
 
 
+def grid_shape(n):
+    """(nx, ny, nz) from a side length or a 3-tuple."""
+    if np.ndim(n) == 0:
+        return (int(n),) * 3
+    nx, ny, nz = (int(v) for v in n)
+    return nx, ny, nz
+
+
 def make_desc(n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1, velocities=False):
+    """n: the grid side, or (nx, ny, nz) for a non-cubic grid (cubic cells:
+    box is the side along x)."""
     r = np.ascontiguousarray(radii, dtype=np.float64)
-    d = pin_plan_desc(n, n, n, float(box), int(r.size),
+    nx, ny, nz = grid_shape(n)
+    d = pin_plan_desc(nx, ny, nz, float(box), int(r.size),
                       r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(correction),
                       PIN_FP32_FALLBACK64, ctypes.c_void_p(stream) if stream else None, int(batch),
                       1 if velocities else 0)
@@ -233,15 +244,18 @@ class Plan:
 
     def __init__(self, n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1,
                  velocities=False):
+        """n: grid side, or (nx, ny, nz) for a non-cubic grid with cubic cells
+        (box is the side along x)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("pin needs a CUDA device; none is available")
-        self.n = int(n)
+        self.shape = grid_shape(n)
+        self.n = self.shape[0]
         self.box = float(box)
         self.batch = int(batch)
         self.radii = np.ascontiguousarray(radii, dtype=np.float64)
         s = stream.cuda_stream if stream is not None else None
-        self._desc = make_desc(self.n, self.box, self.radii, correction, s, self.batch, velocities)
+        self._desc = make_desc(self.shape, self.box, self.radii, correction, s, self.batch, velocities)
         self.handle = pin_plan(self._desc)
 
     def __del__(self):
@@ -280,8 +294,7 @@ class Plan:
         on the device unless host tensors are passed in.  With sync=False the
         work is only enqueued on the plan's stream (call .sync() before use)."""
         import torch
-        n = self.n
-        shape = (n, n, n) if self.batch == 1 else (self.batch, n, n, n)
+        shape = self.shape if self.batch == 1 else (self.batch,) + self.shape
         if fmax is None:
             fmax = torch.empty(shape, dtype=torch.float32, device="cuda")
         if idx is None:
@@ -298,8 +311,7 @@ class Plan:
     def velocities(self):
         """(3, [batch,] n, n, n) displacement at R_max of the last collapse_times."""
         import torch
-        n = self.n
-        shape = (3, n, n, n) if self.batch == 1 else (3, self.batch, n, n, n)
+        shape = (3,) + self.shape if self.batch == 1 else (3, self.batch) + self.shape
         out = torch.empty(shape, dtype=torch.float32, device="cuda")
         torch.cuda.current_stream().synchronize()
         pin_velocities(self.handle, out.data_ptr(), 1)
@@ -312,9 +324,8 @@ class Plan:
         int32 tensor, and per particle the number of its six neighbours that
         precede it, (n, n, n) uint8; either may be skipped (None)."""
         import torch
-        n = self.n
-        o = torch.empty((n ** 3,), dtype=torch.int32, device="cuda") if order else None
-        c = torch.empty((n, n, n), dtype=torch.uint8, device="cuda") if n_before else None
+        o = torch.empty((int(np.prod(self.shape)),), dtype=torch.int32, device="cuda") if order else None
+        c = torch.empty(self.shape, dtype=torch.uint8, device="cuda") if n_before else None
         torch.cuda.current_stream().synchronize()
         pin_fragment_order(self.handle, o.data_ptr() if o is not None else 0,
                            c.data_ptr() if c is not None else 0, 1)
@@ -324,8 +335,7 @@ class Plan:
     def displacements_2lpt(self):
         """(3, n, n, n) second-order LPT displacement of the unsmoothed field."""
         import torch
-        n = self.n
-        out = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+        out = torch.empty((3,) + self.shape, dtype=torch.float32, device="cuda")
         torch.cuda.current_stream().synchronize()
         pin_displacements_2lpt(self.handle, out.data_ptr(), 1)
         self.sync()
@@ -333,8 +343,7 @@ class Plan:
 
     def hessian(self, scale):
         import torch
-        n = self.n
-        out = torch.empty((6, n, n, n), dtype=torch.float32, device="cuda")
+        out = torch.empty((6,) + self.shape, dtype=torch.float32, device="cuda")
         torch.cuda.current_stream().synchronize()
         pin_hessian(self.handle, scale, out.data_ptr(), 1)
         self.sync()
@@ -342,8 +351,7 @@ class Plan:
 
     def displacements(self):
         import torch
-        n = self.n
-        out = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+        out = torch.empty((3,) + self.shape, dtype=torch.float32, device="cuda")
         torch.cuda.current_stream().synchronize()
         pin_displacements(self.handle, out.data_ptr(), 1)
         self.sync()

@@ -47,8 +47,10 @@ def test_validation_without_gpu():
         h = ctypes.c_void_p()
         assert L.pin_plan(ctypes.byref(h), ctypes.byref(bad)) == pin.PIN_EINVAL
         assert not h.value
+    nc = pin.make_desc((64, 32, 48), 100.0, [1.0])  # non-cubic grids of supported sizes are valid
+    assert pin.pin_footprint_bytes(nc) > 64 * 32 * 48 * 8
     nc = pin.make_desc(64, 100.0, [1.0])
-    nc.ny = 32
+    nc.ny = 60  # one unsupported axis is enough to reject
     assert pin.pin_footprint_bytes(nc) == 0
     nc = pin.make_desc(64, 100.0, [1.0])
     nc.correction = 7

@@ -548,3 +548,81 @@ def test_2lpt_two_crossed_waves_closed_form():
     div = sum(np.real(np.fft.ifftn(1j * np.meshgrid(kk, kk, kk, indexing="ij")[i] * np.fft.fftn(psi2[i])))
               for i in range(3))
     assert np.allclose(div, -(3.0 / 7.0) * A * B * np.cos(k1 * X) * np.cos(k2 * Y), atol=1e-12)
+
+
+# ---- non-cubic grids (cubic cells: the side along an axis of m points is box m / nx) ----
+
+@pytest.mark.parametrize("shape,mode", [((8, 12, 16), (1, 2, 3)), ((16, 8, 12), (5, 1, 2)), ((12, 16, 8), (0, 7, 1)),
+                                        ((8, 16, 12), (3, 0, 0))])
+def test_single_mode_closed_form_non_cubic(shape, mode):
+    """A single mode on an nx x ny x nz grid: phi_ij(q) = (k_i k_j / k^2) W(k)
+    2 Re(A e^{i k.q}) / (nx ny nz) with k_i = 2 pi s_i / L_i and
+    k.q = 2 pi sum_i s_i q_i / n_i: pins the per-axis wavenumbers, the axis
+    order and the normalisation off the cube."""
+    nx, ny, nz = shape
+    box, radius = 40.0, 2.0
+    L = np.array([box, box * ny / nx, box * nz / nx])
+    d = np.zeros((nx, ny, nz // 2 + 1), dtype=np.complex128)
+    amp = 0.4 + 0.9j
+    mx, my, mz = mode
+    d[mx, my, mz] = amp
+    if mz == 0:
+        d[(-mx) % nx, (-my) % ny, 0] = np.conj(amp)
+    h, _ = oracle.hessian(d, box, radius)
+    s = np.array([mx if mx < nx // 2 else mx - nx, my if my < ny // 2 else my - ny, mz])
+    k = 2 * np.pi * s / L
+    k2 = k @ k
+    q = np.indices(shape)
+    phase = 2 * np.pi * (s[0] * q[0] / nx + s[1] * q[1] / ny + s[2] * q[2] / nz)
+    wave = 2 * np.real(amp * np.exp(1j * phase)) / (nx * ny * nz)
+    w = np.exp(-0.5 * k2 * radius ** 2)
+    for c, (i, j) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        ref = k[i] * k[j] / k2 * w * wave
+        assert np.abs(h[c] - ref).max() < 1e-14 + 1e-12 * np.abs(wave).max(), (c, shape, mode)
+
+
+@pytest.mark.parametrize("shape,radius", [((8, 16, 12), 3.0), ((16, 12, 8), 0.0)])
+def test_trace_and_displacement_divergence_non_cubic(shape, radius):
+    """Off the cube: the trace of the Hessian is the smoothed delta and the
+    divergence of the displacement is minus delta, both against numpy's irfftn
+    of a random Hermitian spectrum (numpy's rfftn of a real field)."""
+    nx, ny, nz = shape
+    box = 48.0
+    L = [box, box * ny / nx, box * nz / nx]
+    d = np.fft.rfftn(np.random.default_rng(5).normal(size=shape))
+    d[0, 0, 0] = 0.0
+    kx = 2 * np.pi * np.fft.fftfreq(nx, 1.0 / nx) / L[0]
+    ky = 2 * np.pi * np.fft.fftfreq(ny, 1.0 / ny) / L[1]
+    kz = 2 * np.pi * np.arange(nz // 2 + 1) / L[2]
+    k2 = kx[:, None, None] ** 2 + ky[None, :, None] ** 2 + kz[None, None, :] ** 2
+    h, _ = oracle.hessian(d, box, radius)
+    ref = np.fft.irfftn(d * np.exp(-0.5 * k2 * radius ** 2), s=shape, axes=(0, 1, 2))
+    assert np.abs(h[0] + h[1] + h[2] - ref).max() < 1e-12 * np.abs(ref).max()
+    psi = oracle.displacement(d, box, 0.0)
+    # divergence spectrally, Nyquist components of each derivative dropped as in psi
+    kxs, kys = kx.copy(), ky.copy()
+    kxs[nx // 2] = 0.0
+    kys[ny // 2] = 0.0
+    kzs = kz.copy()
+    kzs[-1] = 0.0
+    kk = [kxs[:, None, None], kys[None, :, None], kzs[None, None, :]]
+    div = sum(np.fft.irfftn(1j * kk[i] * np.fft.rfftn(psi[i]), s=shape, axes=(0, 1, 2)) for i in range(3))
+    lapl = np.fft.irfftn(-d * (kk[0] ** 2 + kk[1] ** 2 + kk[2] ** 2) / np.where(k2 > 0, k2, 1.0), s=shape,
+                         axes=(0, 1, 2))
+    assert np.abs(div - lapl).max() < 1e-11 * np.abs(lapl).max()
+
+
+# ---- mass variance of the smoothed field (radius schedule) ----
+
+@pytest.mark.parametrize("shape,radius", [((8, 8, 8), 0.0), ((8, 12, 16), 3.0), ((16, 8, 12), 7.5)])
+def test_sigma2_flat_spectrum_closed_form(shape, radius):
+    """With a flat spectrum P = A the sum separates:
+    sigma^2 = (A / V) (prod_i theta_i - 1), theta_i = sum_m exp(-(2 pi m / L_i)^2 R^2)."""
+    A, box = 2.5, 30.0
+    nx, ny, nz = shape
+    L = [box, box * ny / nx, box * nz / nx]
+    theta = [np.sum(np.exp(-(2 * np.pi * (np.arange(n) - n // 2) / Li) ** 2 * radius ** 2))
+             for n, Li in zip(shape, L)]
+    ref = A / (L[0] * L[1] * L[2]) * (theta[0] * theta[1] * theta[2] - 1.0)
+    got = oracle.sigma2(shape, box, radius, power=lambda k: np.full(k.shape, A))
+    assert abs(got - ref) <= 1e-13 * ref
