@@ -74,3 +74,22 @@ def explain_with_gpu_hessians(plan, bad_q, F_gpu, nscales, rms, correction=1):
     F_gpu = np.asarray(F_gpu, dtype=np.float64).ravel()[bad_q]
     ok = np.abs(F_gpu - out["fmax"]) <= tolerance(out["fmax"], rms)
     return ok, out
+
+
+def assert_parity(plan, F, I, orc, nscales, correction=1, label=""):
+    """The whole rule: every particle within the F tolerance with an equal
+    or near-tie index, or explained by the oracle on the GPU's own FP32
+    Hessians (FP32 rounding of the transforms feeding an ill-conditioned
+    collapse), such particles below 1e-4 of the grid, and the index equal on
+    >= 99.99 % of particles."""
+    F = np.asarray(F).ravel()
+    I = np.asarray(I).ravel()
+    bad, rep = classify(F, I, orc["fmax"], orc["idx"], orc.get("f2"), orc.get("idx2"), orc.get("f_all"))
+    print("parity %s:" % label, rep, plan.stats())
+    bq = np.nonzero(bad)[0]
+    if bq.size:
+        ok, _ = explain_with_gpu_hessians(plan, bq, F, nscales, rep["rms"], correction)
+        assert ok.all(), "unexplained mismatches at %s" % bq[~ok][:10]
+        assert bq.size <= max(1, 1e-4 * F.size), "too many ill-conditioned particles: %d" % bq.size
+    assert rep["idx_mismatch"] <= max(1, 1e-4 * F.size), rep
+    return rep

@@ -50,19 +50,7 @@ def test_non_cubic_collapse_hessian_displacement(shape):
     assert tuple(F.shape) == shape
     orc = oracle.collapse_times(d64, box, radii, keep_all=True, velocities=True)
     Fh, Ih = F.cpu().numpy().ravel(), I.cpu().numpy().ravel()
-    bad, rep = parity.classify(Fh, Ih, orc["fmax"], orc["idx"], f_all=orc["f_all"])
-    print(shape, rep, plan.stats())
-    bq = np.nonzero(bad)[0]
-    if bq.size:
-        # the same rule as the cubic parity tests: a miss must be reproduced by
-        # the oracle on the GPU's own FP32 Hessians (FP32 rounding at a
-        # near-tangent crossing), and such particles must stay rare
-        ok, ex = parity.explain_with_gpu_hessians(plan, bq, Fh, len(radii), rep["rms"])
-        print("misses:", [(int(q), float(Fh[q]), float(orc["fmax"][q]), int(Ih[q]), int(orc["idx"][q]),
-                           float(ex["fmax"][i])) for i, q in enumerate(bq[:8])])
-        assert ok.all(), "unexplained mismatches at %s" % bq[~ok][:10]
-        assert bq.size <= max(1, 1e-4 * Fh.size), bq.size
-    assert rep["idx_mismatch"] <= max(1, 1e-4 * Fh.size), rep
+    parity.assert_parity(plan, Fh, Ih, orc, len(radii), label=str(shape))
     # v_max: the displacement smoothed on R_max, where the indices agree
     v = plan.velocities().double().cpu().numpy().reshape(3, -1)
     same = I.cpu().numpy().ravel() == orc["idx"]
@@ -96,3 +84,4 @@ def test_non_cubic_fragment_order():
     assert np.array_equal(order.cpu().numpy(), oref)
     assert np.array_equal(nb.cpu().numpy().astype(np.int64), nbref)
     plan.close()
+

@@ -43,17 +43,7 @@ def _run(n, box, seed, radii, correction=1, keep_all=None):
 
 
 def _assert_parity(plan, F, I, orc, nscales, correction=1):
-    bad, rep = parity.classify(F, I, orc["fmax"], orc["idx"], orc["f2"], orc["idx2"],
-                               orc.get("f_all"))
-    print("parity:", rep, plan.stats())
-    bq = np.nonzero(bad)[0]
-    if bq.size:
-        ok, _ = parity.explain_with_gpu_hessians(plan, bq, F, nscales, rep["rms"], correction)
-        assert ok.all(), "unexplained mismatches at %s" % bq[~ok][:10]
-        assert bq.size <= max(1, 1e-4 * F.size), "too many ill-conditioned particles: %d" % bq.size
-    # scale index: equal on >= 99.99 % of particles (at least one near-tie
-    # allowed on the smallest grids), every other one a near-tie or explained
-    assert rep["idx_mismatch"] <= max(1, 1e-4 * F.size), rep
+    parity.assert_parity(plan, F, I, orc, nscales, correction)
 
 
 @pytest.mark.parametrize("case", CASES, ids=[str(c[0]) for c in CASES])
