@@ -99,7 +99,11 @@ pin_status cuda_fail(pin_plan_t p, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail((p), e_, #call); \
   } while (0)
 
-int padded_half(int n) { return (n / 2 + 1 + 1) & ~1; }
+// kz stride of the half-spectra: n/2 + 1 modes rounded up to a multiple of 4
+// complex values, so that every row starts on a 32-byte sector (column tiles
+// of the y pass then write whole sectors; rows also meet the 16-byte TMA
+// stride rule)
+int padded_half(int n) { return (n / 2 + 1 + 3) & ~3; }
 
 double delta_c_value() { return 3.0 / 20.0 * std::pow(12.0 * M_PI, 2.0 / 3.0); }
 
