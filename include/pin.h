@@ -34,6 +34,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "pin_ic.h" /* pin_spectrum */
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -104,6 +106,17 @@ size_t pin_footprint_bytes(const pin_plan_desc* d);
  * copied; the caller may reuse its buffer when the call returns (host input)
  * or once the plan's stream has passed this point (device input). */
 pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_device);
+
+/* Generates delta(k) on the device from a seed instead of loading it: the
+ * seeded Gaussian field of include/pin_ic.h (P(k) = A k^ns T_BBKS(k/Gamma)^2
+ * normalised to sigma8, splitmix64 keyed on (seed, linear mode index),
+ * Box-Muller), computed per mode in FP64 and rounded to FP32; realisation b of
+ * a batch uses seed + b.  The paper generates its linear field with N-GenIC
+ * (Sec. 2.2); this generator stands in for it.  Equal to pin_set_ic of the
+ * host module's FP32 field up to the last bits of the device's FP64 math
+ * functions (they may differ from the host's by an ulp, which survives the
+ * rounding to FP32 for about one mode in 1e8).  Cubic grids only. */
+pin_status pin_set_ic_seed(pin_plan_t p, uint64_t seed, const pin_spectrum* ps);
 
 /* Runs the whole collapse-time loop over all radii (Sec. 2.1.1): filter,
  * inverse 3D FFTs of the six Hessian components, eigenvalues, collapse time F,

@@ -7,6 +7,7 @@ Both are compiled in parallel; nothing is installed outside the tree.
 """
 import glob
 import os
+import shlex
 import subprocess
 
 PKG = os.path.dirname(os.path.abspath(__file__))
@@ -27,7 +28,12 @@ def _sources_pin():
 
 def _deps_pin():
     return (_sources_pin() + glob.glob(os.path.join(PKG, "csrc", "*.cuh"))
-            + glob.glob(os.path.join(PKG, "csrc", "*.h")) + [os.path.join(INC, "pin.h")])
+            + glob.glob(os.path.join(PKG, "csrc", "*.h")) + [os.path.join(INC, "pin.h")]
+            + [IC_SRC, os.path.join(INC, "pin_ic.h")])
+
+
+IC_SRC = os.path.join(PKG, "ic", "pin_ic.c")
+IC_OBJ = os.path.join(OUT_DIR, "pin_ic_in_libpin.o")
 
 
 def _stale(target, deps):
@@ -38,10 +44,16 @@ def _stale(target, deps):
 
 
 def cmd_pin(extra=()):
-    return ([NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared",
-                             "-Werror", "cross-execution-space-call",
-                             "-Xcompiler", "-fPIC", "-I", INC, "-I", os.path.join(PKG, "csrc"),
-                             "-o", LIBPIN] + list(extra) + _sources_pin())
+    """libpin links the seeded generator's host part (amplitude, key) for
+    pin_set_ic_seed: pin_ic.c compiled by gcc with the flags of libpin_ic, then
+    the CUDA sources and that object by nvcc."""
+    ic = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-ffp-contract=off", "-I", INC,
+          "-c", "-o", IC_OBJ, IC_SRC]
+    nv = ([NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared",
+                           "-Werror", "cross-execution-space-call",
+                           "-Xcompiler", "-fPIC", "-I", INC, "-I", os.path.join(PKG, "csrc"),
+                           "-o", LIBPIN] + list(extra) + _sources_pin() + [IC_OBJ, "-lm"])
+    return ["sh", "-c", shlex.join(ic) + " && " + shlex.join(nv)]
 
 
 def cmd_ic():

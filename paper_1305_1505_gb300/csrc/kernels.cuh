@@ -149,6 +149,12 @@ cudaError_t launch_roots(const ArgsZ& a, cudaStream_t st);
 cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st);
 cudaError_t upload_constant_twiddles();  // per device
 
+// Seeded initial conditions on the device (ic_gpu.cu): batch cubic
+// half-spectra [n][n][n/2+1] complex64 into out, realisation b keyed by
+// keys_dev[b] (the splitmix64 of its seed), amplitude amp of P(k).
+cudaError_t generate_ic(int n, double box, const uint64_t* keys_dev, int batch, double amp, double ns,
+                        double gamma, float2* out, cudaStream_t st);
+
 // Fragmentation front end (fragment.cu): the particles of one nx*ny*nz grid in
 // descending F_max (ties: ascending index) into `order`, and the number of
 // their six periodic neighbours that precede them into `n_before`; either

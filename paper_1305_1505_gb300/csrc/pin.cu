@@ -20,6 +20,7 @@
 
 #include "kernels.cuh"
 #include "pin.h"
+#include "pin_ic.h"
 
 using namespace pin;
 
@@ -542,6 +543,34 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
                                                   p->phi0);
   PIN_CK(p, cudaGetLastError());
   if (!on_device) PIN_CK(p, cudaStreamSynchronize(p->stream));
+  p->ic_set = true;
+  return PIN_OK;
+}
+
+pin_status pin_set_ic_seed(pin_plan_t p, uint64_t seed, const pin_spectrum* ps) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!ps) return fail(p, PIN_EINVAL, "null spectrum");
+  if (p->nx != p->ny || p->ny != p->nz) return fail(p, PIN_EINVAL, "pin_set_ic_seed needs a cubic grid");
+  if (!(ps->gamma > 0.0) || !std::isfinite(ps->ns) || !(ps->sigma8 > 0.0))
+    return fail(p, PIN_EINVAL, "bad spectrum parameters");
+  const double amp = pin_ic_amplitude(ps);
+  std::vector<uint64_t> keys(p->batch);
+  for (int b = 0; b < p->batch; ++b) keys[b] = pin_ic_splitmix64(seed + (uint64_t)b);
+  // stage: the keys after the generated half-spectra in the V workspace (>= 6 spectra)
+  const size_t half = (size_t)p->nx * p->nx * (p->nx / 2 + 1) * p->batch;
+  float2* field = p->V;
+  uint64_t* keys_dev = reinterpret_cast<uint64_t*>(p->V + half + 1);
+  PIN_CK(p, cudaMemcpyAsync(keys_dev, keys.data(), keys.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                            p->stream));
+  PIN_CK(p, generate_ic(p->nx, p->box, keys_dev, p->batch, amp, ps->ns, ps->gamma, field, p->stream));
+  const size_t total = p->field_elems;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, 152 * 64);
+  k_load_phi0<<<blocks, threads, 0, p->stream>>>(field, PIN_C64, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch,
+                                                  p->phi0);
+  PIN_CK(p, cudaGetLastError());
+  PIN_CK(p, cudaStreamSynchronize(p->stream));  // the host key vector goes out of scope
   p->ic_set = true;
   return PIN_OK;
 }

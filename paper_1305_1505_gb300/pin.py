@@ -38,6 +38,14 @@ class pin_plan_desc(ctypes.Structure):
                 ("batch", ctypes.c_int), ("velocities", ctypes.c_int)]
 
 
+class pin_spectrum(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_double), ("gamma", ctypes.c_double), ("sigma8", ctypes.c_double)]
+
+
+def spectrum(ns=0.96, gamma=0.21, sigma8=0.8):
+    return pin_spectrum(ns, gamma, sigma8)
+
+
 class pin_stats(ctypes.Structure):
     _fields_ = [("eig_fp64_redo", ctypes.c_uint64), ("root_fp64_redo", ctypes.c_uint64),
                 ("fp64_queue_overflow", ctypes.c_uint64), ("collapse_calls", ctypes.c_uint64)]
@@ -47,8 +55,8 @@ class pin_stats(ctypes.Structure):
 EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_hessian",
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
-           "pin_fragment_order", "pin_displacements_2lpt", "pin_strerror", "pin_last_error",
-           "pin_destroy")
+           "pin_fragment_order", "pin_displacements_2lpt", "pin_set_ic_seed", "pin_strerror",
+           "pin_last_error", "pin_destroy")
 
 _lib = None
 
@@ -78,6 +86,8 @@ def load(path=None):
     L.pin_fragment_order.restype = ctypes.c_int
     L.pin_displacements_2lpt.argtypes = [P, P, ctypes.c_int]
     L.pin_displacements_2lpt.restype = ctypes.c_int
+    L.pin_set_ic_seed.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(pin_spectrum)]
+    L.pin_set_ic_seed.restype = ctypes.c_int
     L.pin_hessian.argtypes = [P, ctypes.c_int, P, ctypes.c_int]
     L.pin_hessian.restype = ctypes.c_int
     L.pin_displacements.argtypes = [P, P, ctypes.c_int]
@@ -172,6 +182,11 @@ def pin_fragment_order(plan, order_ptr, n_before_ptr, on_device):
     _check(load().pin_fragment_order(plan, ctypes.c_void_p(order_ptr) if order_ptr else None,
                                      ctypes.c_void_p(n_before_ptr) if n_before_ptr else None,
                                      int(on_device)), plan)
+
+
+def pin_set_ic_seed(plan, seed, spec=None):
+    sp = spec if spec is not None else spectrum()
+    _check(load().pin_set_ic_seed(plan, ctypes.c_uint64(int(seed)), ctypes.byref(sp)), plan)
 
 
 def pin_displacements_2lpt(plan, out_ptr, on_device):
@@ -288,6 +303,11 @@ class Plan:
         pin_set_ic(self.handle, t.data_ptr(), dt, 1 if t.is_cuda else 0)
         if t.is_cuda:
             self.sync()
+
+    def set_ic_seed(self, seed, ns=0.96, gamma=0.21, sigma8=0.8):
+        """delta(k) generated on the device from `seed` (realisation b of a
+        batch: seed + b), the seeded field of the input module."""
+        pin_set_ic_seed(self.handle, seed, spectrum(ns, gamma, sigma8))
 
     def collapse_times(self, fmax=None, idx=None, sync=True):
         """Returns (F_max float32, scale_idx int32) tensors of shape (n,n,n),

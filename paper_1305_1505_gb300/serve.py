@@ -63,8 +63,9 @@ class Request:
 
 
 class PinEngine:
-    """Runs one request on the GPU: input generation on the host, a plan on a
-    stream of its own, the whole radius loop, results copied to the host."""
+    """Runs one request on the GPU: a plan on a stream of its own, delta(k)
+    generated on the device from the request's seed (pin_set_ic_seed), the
+    whole radius loop, results copied to the host."""
 
     def __init__(self, device=0):
         import torch
@@ -75,10 +76,8 @@ class PinEngine:
         return pin.pin_footprint_bytes(pin.make_desc(req.n, req.box, req.radii))
 
     def run(self, req, timeout_s=None):
-        from . import ic
         torch = self.torch
         torch.cuda.set_device(self.device)
-        d32 = ic.delta_k(req.n, req.box, req.seed, dtype=np.complex64)
         stream = torch.cuda.Stream()
         plan = pin.Plan(req.n, req.box, req.radii, stream=stream)
         try:
@@ -86,7 +85,7 @@ class PinEngine:
             F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
             I = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
             torch.cuda.current_stream().synchronize()
-            pin.pin_set_ic(plan.handle, d32.ctypes.data, pin.PIN_C64, 0)
+            pin.pin_set_ic_seed(plan.handle, req.seed)
             pin.pin_collapse_times(plan.handle, F.data_ptr(), I.data_ptr(), 1)
             st = pin.pin_sync(plan.handle, -1 if timeout_s is None else int(timeout_s * 1e9))
             if st == pin.PIN_ETIMEOUT:
