@@ -218,10 +218,17 @@ __device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { retur
 // fft_out_index gives the frequency of each slot.  All threads of the block
 // must call it; it synchronises once (twice more for three levels) and leaves
 // the exchange buffer in use (callers synchronise before writing s_x again).
-template <int N, class Layout>
+// WARP: every transform is held by one whole warp (P = 32) with an exchange
+// region of its own, so the exchanges need only warp-level synchronisation.
+template <int N, class Layout, bool WARP = false>
 __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c, float2* s_x,
                                          const float2* s_tw) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P, P1 = Shape<N>::P1, P2 = Shape<N>::P2;
+  static_assert(!WARP || P == 32, "warp-level exchanges need one transform per warp");
+  auto sync = [] {
+    if constexpr (WARP) __syncwarp();
+    else __syncthreads();
+  };
   DFT<E>::run(v);
   if constexpr (P2 > 1) {
     // level 1 done; twiddle w_N^{p k1} and first exchange
@@ -230,7 +237,7 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c,
       float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P>(s_tw, k1, p));
       s_x[Layout::at(k1, p, c)] = z;
     }
-    __syncthreads();
+    sync();
     // level 2: for k1 = q + P2 i, the length-P2 DFT over p2 of Z[k1][p1 + P1 p2],
     // then the twiddle w_P^{p1 k2a}
     const int p1 = p % P1, q = p / P1;
@@ -246,12 +253,12 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c,
 #pragma unroll
       for (int k2a = 0; k2a < P2; ++k2a) v[i * P2 + k2a] = (k2a == 0) ? t[k2a] : cmul(t[k2a], twb[k2a]);
     }
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int i = 0; i < E / P2; ++i)
 #pragma unroll
       for (int k2a = 0; k2a < P2; ++k2a) s_x[Layout::at2(q + P2 * i, k2a, p1, c)] = v[i * P2 + k2a];
-    __syncthreads();
+    sync();
     // level 3: pairs (k1, k2a) = divmod(p + P m, P2), the length-P1 DFT over p1
 #pragma unroll
     for (int m = 0; m < E / P1; ++m) {
@@ -270,7 +277,7 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c,
       float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P>(s_tw, k1, p));
       s_x[Layout::at(k1, p, c)] = z;
     }
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int i = 0; i < E / P; ++i) {
       float2 t[P];
