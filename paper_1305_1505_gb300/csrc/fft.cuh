@@ -218,13 +218,14 @@ __device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { retur
 // fft_out_index gives the frequency of each slot.  All threads of the block
 // must call it; it synchronises once (twice more for three levels) and leaves
 // the exchange buffer in use (callers synchronise before writing s_x again).
-// WARP: every transform is held by one whole warp (P = 32) with an exchange
-// region of its own, so the exchanges need only warp-level synchronisation.
+// WARP: every transform is held within one warp (P divides 32, transform c on
+// threads [c P, c P + P)) with an exchange region of its own, so the
+// exchanges need only warp-level synchronisation.
 template <int N, class Layout, bool WARP = false>
 __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c, float2* s_x,
                                          const float2* s_tw) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P, P1 = Shape<N>::P1, P2 = Shape<N>::P2;
-  static_assert(!WARP || P == 32, "warp-level exchanges need one transform per warp");
+  static_assert(!WARP || 32 % P == 0, "warp-level exchanges need whole transforms per warp");
   auto sync = [] {
     if constexpr (WARP) __syncwarp();
     else __syncthreads();

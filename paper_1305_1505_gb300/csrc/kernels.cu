@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
       v[t] = make_float2(xa.x - xb.y, xa.y + xb.x);  // A + iB
     }
   }
-  fft_line<N, L, Shape<N>::P == 32>(v, p, c, s_x, s_tw);
+  fft_line<N, L, 32 % Shape<N>::P == 0>(v, p, c, s_x, s_tw);
 
   if constexpr (DUMP) {
     if (active) {
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(NC * Shape<N>::P) k_fwd_z(const float* __restr
     const int n = p + P * t;
     v[t] = active ? make_float2(__ldg(A + n), __ldg(A + N + n)) : make_float2(0.f, 0.f);
   }
-  fft_line<N, L, Shape<N>::P == 32>(v, p, c, s_x, s_tw);
+  fft_line<N, L, 32 % Shape<N>::P == 0>(v, p, c, s_x, s_tw);
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j) s_z[c * N + fft_out_index<N>(p, j)] = v[j];
