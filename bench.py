@@ -279,6 +279,8 @@ def run_ours(args):
     plan = pin.Plan(n, w["box"], radii, stream=stream, velocities=args.velocities)
     dk = torch.from_numpy(d32).cuda()
     plan.set_ic(dk)
+    # x/y tile widths timed on this plan, outside the timed region
+    tiles = plan.tiles() if args.no_tune else plan.autotune(reps=5)
     F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
     I = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
     pin.pin_profile(plan.handle, 1)
@@ -359,7 +361,8 @@ def run_ours(args):
             "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(_config(w), velocities=bool(args.velocities)),
+            "config": dict(_config(w), velocities=bool(args.velocities),
+                           tiles={"x": tiles[0], "y": tiles[1], "tuned": not args.no_tune}),
             "roofline": roofline(names[dom], per_launch_ms[dom], n, bool(args.velocities), fused,
                                  achieved, peak, peak_kind, clocks, passes),
             "cpu_baseline": cb,
@@ -396,6 +399,8 @@ def run_ensemble(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     bplan = pin.Plan(n, e["box"], radii, stream=stream, batch=B)
+    if not args.no_tune:
+        bplan.autotune(reps=5)
     Fb = torch.empty((B, n, n, n), dtype=torch.float32, device="cuda")
     Ib = torch.empty((B, n, n, n), dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
@@ -416,6 +421,8 @@ def run_ensemble(args):
     t_batch = ev0.elapsed_time(ev1) / 1e3 / args.steps
 
     splan = pin.Plan(n, e["box"], radii, stream=stream)
+    if not args.no_tune:
+        splan.autotune(reps=5)
     Fs = torch.empty((B, n, n, n), dtype=torch.float32, device="cuda")
     Is = torch.empty((B, n, n, n), dtype=torch.int32, device="cuda")
 
@@ -561,6 +568,8 @@ def run_2lpt(args):
     plan = pin.Plan(n, w["box"], [w["r_max"]], stream=stream)
     d32 = ic.delta_k(n, w["box"], w["seed"], dtype=np.complex64)
     plan.set_ic(torch.from_numpy(d32).cuda())
+    if not args.no_tune:
+        plan.autotune(reps=5)
     out = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
 
@@ -626,6 +635,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="run the default x/y tile widths instead of the tuned ones")
     ap.add_argument("--grid", type=int, default=0,
                     help="grid side for profiling captures (box = 4 Mpc/h per cell); default 768")
     ap.add_argument("--nscales", type=int, default=0, help="number of radii; default 40")

@@ -189,7 +189,8 @@ pin_status pin_get_stats(pin_plan_t p, pin_stats* out);
 
 /* Number of kernels one pin_collapse_times call launches (for accounting):
  * per radius the x, y and z passes, the root pass unless the z pass of this
- * grid size computes the collapse times itself (N = 768), and the FP64 redo. */
+ * grid size computes the collapse times itself (N = 384 and 768, the sizes
+ * with three-level line transforms), and the FP64 redo. */
 int pin_kernels_per_call(pin_plan_t p);
 
 /* Measurement hooks.  pin_profile(p, 1) makes later pin_collapse_times calls
@@ -197,12 +198,39 @@ int pin_kernels_per_call(pin_plan_t p);
  * inside its graph); pin_pass_times() then waits for the plan's work and
  * returns, for the last completed call, the device time in milliseconds summed
  * over radii of: ms4[0] the x pass (filter + transform), ms4[1] the y pass,
- * ms4[2] the z pass (c2r + eigenvalues; at N = 768 also the collapse time and
- * running max), ms4[3] the root pass (collapse time + running max, where it
+ * ms4[2] the z pass (c2r + eigenvalues; at N = 384 and 768 also the collapse
+ * time and running max), ms4[3] the root pass (collapse time + running max, where it
  * is a kernel of its own) with the FP64 redo of the queued ill-conditioned
  * particles. */
 pin_status pin_profile(pin_plan_t p, int enable);
 pin_status pin_pass_times(pin_plan_t p, double* ms4);
+
+/* Tile schedule of the x and y passes (the paper has no counterpart: its FFTs
+ * are FFTW's).  Each of those passes transforms blocks of tc columns of the
+ * spectrum at a time; every width computes each column's line transform with
+ * the same arithmetic, so the choice changes timings, never results.
+ *
+ * pin_tile_options: the widths a pass over lines of n points can run, the
+ * default first, into opts[0 .. *count - 1] (*count <= 2); PIN_EINVAL for an
+ * unsupported n.
+ * pin_get_tiles / pin_set_tiles: the widths the plan runs for its x pass
+ * (lines of nx points) and y pass (ny points); 0 selects the default, any
+ * other value must be one of pin_tile_options (else PIN_EINVAL, plan
+ * unchanged).  Setting waits for the plan's stream.
+ * pin_autotune: times every candidate width of the x pass and of the y pass
+ * on the plan's own buffers (reps launches each, 1..1000, after one untimed
+ * launch; the first radius, the plan's mode) and keeps the fastest of each.
+ * Only the plan's workspaces are written (Phi0 is zeroed first if no field
+ * is set); F_max, the scale index and v_max are untouched.  Choices are kept
+ * per (nx, ny, nz, batch, velocities) for the process: a later call for the
+ * same shape applies the kept choice without timing unless flags has
+ * PIN_TUNE_FORCE.  The chosen widths go to *tc_x and *tc_y (either may be
+ * NULL).  Not to be called while the plan's stream is being captured. */
+#define PIN_TUNE_FORCE 1
+pin_status pin_tile_options(int n, int* opts, int* count);
+pin_status pin_get_tiles(pin_plan_t p, int* tc_x, int* tc_y);
+pin_status pin_set_tiles(pin_plan_t p, int tc_x, int tc_y);
+pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y);
 
 /* Largest grid side the no-allocation entry point below accepts. */
 #define PIN_NOALLOC_MAX_N 64

@@ -43,17 +43,27 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+OBJ_DIR = os.path.join(OUT_DIR, "obj")
+
+
 def cmd_pin(extra=()):
     """libpin links the seeded generator's host part (amplitude, key) for
-    pin_set_ic_seed: pin_ic.c compiled by gcc with the flags of libpin_ic, then
-    the CUDA sources and that object by nvcc."""
+    pin_set_ic_seed: pin_ic.c compiled by gcc with the flags of libpin_ic, and
+    each CUDA source compiled by nvcc, all at once (one process each), then
+    linked into the shared library."""
     ic = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-ffp-contract=off", "-I", INC,
           "-c", "-o", IC_OBJ, IC_SRC]
-    nv = ([NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared",
-                           "-Werror", "cross-execution-space-call",
-                           "-Xcompiler", "-fPIC", "-I", INC, "-I", os.path.join(PKG, "csrc"),
-                           "-o", LIBPIN] + list(extra) + _sources_pin() + [IC_OBJ, "-lm"])
-    return ["sh", "-c", shlex.join(ic) + " && " + shlex.join(nv)]
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Werror", "cross-execution-space-call",
+                    "-Xcompiler", "-fPIC", "-I", INC, "-I", os.path.join(PKG, "csrc")] + list(extra)
+    objs, steps = [], [shlex.join(ic) + " & pids=$!"]
+    for src in _sources_pin():
+        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        objs.append(obj)
+        steps.append(shlex.join([NVCC] + flags + ["-c", "-o", obj, src]) + ' & pids="$pids $!"')
+    link = [NVCC] + ARCH + ["-shared", "-o", LIBPIN] + objs + [IC_OBJ, "-lm"]
+    script = ["set -e", "mkdir -p " + shlex.quote(OBJ_DIR)] + steps + \
+        ["for p in $pids; do wait $p; done", shlex.join(link)]
+    return ["sh", "-c", "\n".join(script)]
 
 
 def cmd_ic():

@@ -170,12 +170,17 @@ template <int N> struct Shape : ShapeBase<N> {
 //    level-2 reads (stride P+1) do not collide on a bank.
 // at(k1, p, c): exchange after level 1; at2(k1, k2a, p1, c): second exchange
 // of the three-level form (P = P1 P2).
+// In at2 the p1 index is flipped in its lowest bit for odd k2a: a level-3
+// read (lanes over consecutive k2a and the columns) then alternates between
+// bank halves when the columns fill only half of the banks (TC = 8); for
+// wider tiles it is a harmless permutation within each row.
 template <int E, int P, int TC, int P1 = P>
 struct XLayoutCols {
   static constexpr int P2 = P / P1;
   static constexpr int kSize = E * P * TC;
   __device__ __forceinline__ static int at(int k1, int p, int c) { return (k1 * P + p) * TC + c; }
   __device__ __forceinline__ static int at2(int k1, int k2a, int p1, int c) {
+    if constexpr (P1 > 1) p1 ^= (k2a & 1);
     return ((k1 * P2 + k2a) * P1 + p1) * TC + c;
   }
 };

@@ -105,10 +105,10 @@ template <int N> struct Stage {
 #endif
 // Three-level lines hold half the registers per thread: the z pass is sized
 // for more resident blocks.
-template <int N> struct MinBlocks {
-  // three-level x/y blocks (16 columns x P threads) are sized for 512
+template <int N, int TC = 16> struct MinBlocks {
+  // three-level x/y blocks (TC columns x P threads) are sized for 512
   // resident threads per SM
-  static constexpr int xy = Shape<N>::P2 > 1 ? 32 / Shape<N>::P : (N >= 384 ? PIN_XY_MINB : 1);
+  static constexpr int xy = Shape<N>::P2 > 1 ? 512 / (TC * Shape<N>::P) : (N >= 384 ? PIN_XY_MINB : 1);
   static constexpr int z = Shape<N>::P2 > 1 ? PIN_Z_MINB3 : (N >= 384 ? PIN_Z_MINB : 1);
 };
 
@@ -119,7 +119,7 @@ template <int N> struct MinBlocks {
 // outputs, and the next tile is requested as soon as the last output has read
 // the current one into registers.
 template <int N, int TC>
-__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(const __grid_constant__ ArgsX a) {
+__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N, TC>::xy) k_pass_x(const __grid_constant__ ArgsX a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P, NTW = Shape<N>::kTw;
   using L = XLayoutCols<E, P, TC, Shape<N>::P1>;
   using G = Stage<N>;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_x(co
 // (ky, kz) of plane x sits at (x*N + ky)*nhp + kz.  Columns past nhp are
 // zero-filled by the tensor map and not stored.
 template <int N, int TC, bool DUAL>
-__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N>::xy) k_pass_y(const __grid_constant__ ArgsY a) {
+__global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N, TC>::xy) k_pass_y(const __grid_constant__ ArgsY a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P, NTW = Shape<N>::kTw;
   using L = XLayoutCols<E, P, TC, Shape<N>::P1>;
   using G = Stage<N>;
@@ -759,13 +759,9 @@ template <int N> struct Cfg {
 #else
   static constexpr bool FUSE = PIN_Z_FUSE != 0;
 #endif
-  // staged tile + exchange + twiddles + multipliers + alignment slack
-  static constexpr size_t smem_xy = (size_t)N * TC * 8 + (size_t)XLayoutCols<E, P, TC, P1>::kSize * 8 +
-                                    (size_t)NTW * 8 + (size_t)3 * N * 4 + 128;
   static constexpr size_t xz = (size_t)XLayoutLines<E, P, 3 * LINES, P1>::kSize * 8;
   static constexpr size_t fz = (size_t)LINES * 6 * field_stride<N>() * 4;
   static constexpr size_t smem_z = (xz > fz ? xz : fz) + (size_t)NTW * 8;
-  static constexpr int threads_xy = TC * P;
   static constexpr int threads_z = 3 * LINES * P;
   // with the displacement fields: five pairs per line, half as many lines
   static constexpr int LINES_V = LINES >= 2 ? LINES / 2 : 1;
@@ -780,16 +776,43 @@ template <int N> struct Cfg {
   static constexpr size_t smem_fz = (xf > zf ? xf : zf) + (size_t)NTW * 8;
 };
 
+// One x/y tile width: staged tile + exchange + twiddles + multipliers +
+// alignment slack, and the block size.
+template <int N, int TC> struct CfgXY {
+  static constexpr int E = Shape<N>::E, P = Shape<N>::P, P1 = Shape<N>::P1, NTW = Shape<N>::kTw;
+  static constexpr size_t smem = (size_t)N * TC * 8 + (size_t)XLayoutCols<E, P, TC, P1>::kSize * 8 +
+                                 (size_t)NTW * 8 + (size_t)3 * N * 4 + 128;
+  static constexpr int threads = TC * P;
+};
+
+// The x/y tile widths a plan may run (the autotuner's candidates): the
+// default and half of it while a TMA box row stays at least 64 bytes.  Every
+// width computes each column's transform with the same arithmetic, so the
+// choice changes timings only.
+template <int N> struct Tiles {
+  static constexpr int T0 = Cfg<N>::TC;
+  static constexpr int T1 = Cfg<N>::TC / 2 >= 8 ? Cfg<N>::TC / 2 : Cfg<N>::TC;
+};
+
+template <int N, int TC>
+static cudaError_t set_attrs_xy() {
+  constexpr int smem = (int)CfgXY<N, TC>::smem;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_x<N, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass_y<N, TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_pass_y<N, TC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 template <int N>
 static cudaError_t set_attrs() {
   using C = Cfg<N>;
-  cudaError_t e;
-  e = cudaFuncSetAttribute(k_pass_x<N, C::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
+  cudaError_t e = set_attrs_xy<N, Tiles<N>::T0>();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pass_y<N, C::TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pass_y<N, C::TC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_xy);
-  if (e != cudaSuccess) return e;
+  if constexpr (Tiles<N>::T1 != Tiles<N>::T0) {
+    e = set_attrs_xy<N, Tiles<N>::T1>();
+    if (e != cudaSuccess) return e;
+  }
   e = cudaFuncSetAttribute(k_pass_z<N, C::LINES, false, 3, C::FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)C::smem_z);
   if (e != cudaSuccess) return e;
@@ -808,8 +831,8 @@ static cudaError_t set_attrs() {
 template <int N>
 static PassShape shape_of() {
   using C = Cfg<N>;
-  return PassShape{C::E, C::P, Shape<N>::P1, Shape<N>::P2, C::TC, C::LINES, C::smem_xy, C::smem_z,
-                   C::threads_xy, C::threads_z};
+  return PassShape{C::E, C::P, Shape<N>::P1, Shape<N>::P2, C::TC, C::LINES, CfgXY<N, C::TC>::smem, C::smem_z,
+                   CfgXY<N, C::TC>::threads, C::threads_z};
 }
 
 // Persistent grid: as many blocks as fit on the device at once, at most one
@@ -824,27 +847,27 @@ static unsigned persistent_grid(K kernel, int threads, size_t smem, long ntiles)
   return (unsigned)std::min<long>(g, std::max<long>(1, ntiles));
 }
 
-template <int N>
+template <int N, int TC>
 static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
-  using C = Cfg<N>;
-  const long ntiles = (((long)a.ny * a.nhp + C::TC - 1) / C::TC) * a.batch;
-  const unsigned grid = persistent_grid(k_pass_x<N, C::TC>, C::threads_xy, C::smem_xy, ntiles);
-  k_pass_x<N, C::TC><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
+  using C = CfgXY<N, TC>;
+  const long ntiles = (((long)a.ny * a.nhp + TC - 1) / TC) * a.batch;
+  const unsigned grid = persistent_grid(k_pass_x<N, TC>, C::threads, C::smem, ntiles);
+  k_pass_x<N, TC><<<grid, C::threads, C::smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int TC>
 static cudaError_t run_y(const ArgsY& a, cudaStream_t st) {
-  using C = Cfg<N>;
-  const long ntiles = (long)a.nx * a.batch * ((a.nhp + C::TC - 1) / C::TC);
+  using C = CfgXY<N, TC>;
+  const long ntiles = (long)a.nx * a.batch * ((a.nhp + TC - 1) / TC);
   bool dual = false;
   for (int o = 0; o < a.nout; ++o) dual = dual || a.dst2[o] != nullptr;
   if (dual) {
-    const unsigned grid = persistent_grid(k_pass_y<N, C::TC, true>, C::threads_xy, C::smem_xy, ntiles);
-    k_pass_y<N, C::TC, true><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
+    const unsigned grid = persistent_grid(k_pass_y<N, TC, true>, C::threads, C::smem, ntiles);
+    k_pass_y<N, TC, true><<<grid, C::threads, C::smem, st>>>(a);
   } else {
-    const unsigned grid = persistent_grid(k_pass_y<N, C::TC, false>, C::threads_xy, C::smem_xy, ntiles);
-    k_pass_y<N, C::TC, false><<<grid, C::threads_xy, C::smem_xy, st>>>(a);
+    const unsigned grid = persistent_grid(k_pass_y<N, TC, false>, C::threads, C::smem, ntiles);
+    k_pass_y<N, TC, false><<<grid, C::threads, C::smem, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -920,18 +943,33 @@ cudaError_t prepare_kernels(int n) {
   }
 }
 
-cudaError_t launch_x(int n, const ArgsX& a, cudaStream_t st) {
+int xy_tile_options(int n, int* opts) {
   switch (n) {
-#define CASE(N) case N: return run_x<N>(a, st);
+#define CASE(N)                                             \
+  case N:                                                   \
+    opts[0] = Tiles<N>::T0;                                 \
+    opts[1] = Tiles<N>::T1;                                 \
+    return Tiles<N>::T1 != Tiles<N>::T0 ? 2 : 1;
+    PIN_SIZES(CASE)
+#undef CASE
+    default: return 0;
+  }
+}
+
+cudaError_t launch_x(int n, int tc, const ArgsX& a, cudaStream_t st) {
+  switch (n) {
+#define CASE(N) \
+  case N: return tc == Tiles<N>::T1 ? run_x<N, Tiles<N>::T1>(a, st) : run_x<N, Tiles<N>::T0>(a, st);
     PIN_SIZES(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st) {
+cudaError_t launch_y(int n, int tc, const ArgsY& a, cudaStream_t st) {
   switch (n) {
-#define CASE(N) case N: return run_y<N>(a, st);
+#define CASE(N) \
+  case N: return tc == Tiles<N>::T1 ? run_y<N, Tiles<N>::T1>(a, st) : run_y<N, Tiles<N>::T0>(a, st);
     PIN_SIZES(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -1010,22 +1048,20 @@ static cudaError_t encode(CUtensorMap* tm, int rank, const void* base, const cuu
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int nhp, int batch) {
-  const PassShape sh = pass_shape(nx);
+cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int nhp, int batch, int tc) {
   const int boxes = (nx + 255) / 256;
   const cuuint64_t dims[2] = {(cuuint64_t)ny * nhp, (cuuint64_t)nx * batch};
   const cuuint64_t strides[1] = {(cuuint64_t)ny * nhp * 8};
-  const cuuint32_t box[2] = {(cuuint32_t)sh.tc, (cuuint32_t)(nx / boxes)};
+  const cuuint32_t box[2] = {(cuuint32_t)tc, (cuuint32_t)(nx / boxes)};
   return encode(tm, 2, src, dims, strides, box);
 }
 
 cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int nx, int ny, int nhp, size_t spec_elems,
-                        int batch) {
-  const PassShape sh = pass_shape(ny);
+                        int batch, int tc) {
   const int boxes = (ny + 255) / 256;
   const cuuint64_t dims[4] = {(cuuint64_t)nhp, (cuuint64_t)ny, (cuuint64_t)nx * batch, 3};
   const cuuint64_t strides[3] = {(cuuint64_t)nhp * 8, (cuuint64_t)ny * nhp * 8, (cuuint64_t)spec_elems * 8};
-  const cuuint32_t box[4] = {(cuuint32_t)sh.tc, (cuuint32_t)(ny / boxes), 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)tc, (cuuint32_t)(ny / boxes), 1, 1};
   return encode(tm, 4, src3, dims, strides, box);
 }
 

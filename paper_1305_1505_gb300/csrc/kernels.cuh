@@ -120,16 +120,21 @@ struct PassShape {
 
 // Tensor maps of the x and y passes (host; the encoder comes from the driver
 // entry point, so no driver library is linked).  spec_elems is the stride
-// between the spectra the y map spans.
-cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int nhp, int batch);
+// between the spectra the y map spans; tc is the tile width (columns) of the
+// pass that reads the map, one of xy_tile_options.
+cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int nhp, int batch, int tc);
 cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int nx, int ny, int nhp, size_t spec_elems,
-                        int batch);
+                        int batch, int tc);
+// Tile widths the x/y pass over lines of n points can run (opts[0] is the
+// default); returns their number (0 for an unsupported size).
+int xy_tile_options(int n, int* opts);
 
 bool size_supported(int n);
 PassShape pass_shape(int n);
 cudaError_t prepare_kernels(int n);  // sets shared-memory attributes (once per device)
-cudaError_t launch_x(int n, const ArgsX& a, cudaStream_t st);
-cudaError_t launch_y(int n, const ArgsY& a, cudaStream_t st);
+// tc: tile width, one of xy_tile_options(n) (anything else runs the default)
+cudaError_t launch_x(int n, int tc, const ArgsX& a, cudaStream_t st);
+cudaError_t launch_y(int n, int tc, const ArgsY& a, cudaStream_t st);
 cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st);
 // Second-order LPT pieces: the z pass writing the source S of every particle
 // (from the six fields in src[0..5]) to out[0]; the inverse-sign transform

@@ -178,8 +178,9 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
   unsigned* redo_count = reinterpret_cast<unsigned*>(base + kOffRedoCount);
   int* err = reinterpret_cast<int*>(base + kOffErr);
   CUtensorMap tm_x, tm_y;
-  if (pin::make_tmap_x(&tm_x, phi0, n, n, nhp, 1) != cudaSuccess ||
-      pin::make_tmap_y(&tm_y, U, n, n, nhp, spec, 1) != cudaSuccess)
+  const int tc = pin::pass_shape(n).tc;  // the default tile width
+  if (pin::make_tmap_x(&tm_x, phi0, n, n, nhp, 1, tc) != cudaSuccess ||
+      pin::make_tmap_y(&tm_y, U, n, n, nhp, spec, 1, tc) != cudaSuccess)
     return PIN_ECUDA;
   pin::RedoEntry* redo_list = reinterpret_cast<pin::RedoEntry*>(base + kOffRedo);
   const double dcorr = noalloc_dcorr();
@@ -251,7 +252,7 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
     az.redo_list = redo_list;
     az.redo_count = redo_count;
     az.redo_cap = (unsigned)kRedoCap;
-    if (pin::launch_x(n, ax, cs) != cudaSuccess || pin::launch_y(n, ay, cs) != cudaSuccess ||
+    if (pin::launch_x(n, tc, ax, cs) != cudaSuccess || pin::launch_y(n, tc, ay, cs) != cudaSuccess ||
         cudaMemsetAsync(redo_count, 0, sizeof(unsigned), cs) != cudaSuccess ||
         pin::launch_z(n, az, false, cs) != cudaSuccess ||
         (!pin::z_fuses_roots(n) && pin::launch_roots(az, cs) != cudaSuccess) ||

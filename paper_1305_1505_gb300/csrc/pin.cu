@@ -12,7 +12,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <thread>
@@ -51,6 +53,7 @@ struct pin_plan_s {
   unsigned redo_cap = 0;
   int* err = nullptr;                      // set by a pass whose bounded TMA wait gave up
   CUtensorMap tm_x{}, tm_y{};              // Phi0 -> x pass, U[3] -> y pass
+  int tc_x = 0, tc_y = 0;                  // tile widths (columns per block) of the x and y passes
   bool ic_set = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -253,13 +256,16 @@ void release(pin_plan_t p) {
 
 float2* spec(pin_plan_t p, float2* base, int f) { return base + (size_t)f * p->field_elems; }
 
-// Filter-and-transform passes of one radius (mult set `ms`), ending in the
-// collapse update (dump and source null), a dump of the six real components,
-// or the 2LPT source field S of every particle (source, batch 1).
-pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, float* source = nullptr) {
-  const bool collapse = dump == nullptr && source == nullptr;
-  const bool rec = p->profile && collapse && !p->events.empty();
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 0], p->stream, cudaEventRecordExternal));
+void drop_graph(pin_plan_t p) {
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->graph_exec = nullptr;
+  p->graph = nullptr;
+}
+
+// x pass of one radius (mult set `ms`): Phi0 -> U[0..2] with the x factors
+// W, k W, k^2 W.
+ArgsX radius_args_x(pin_plan_t p, int ms) {
   ArgsX ax{};
   ax.tm = p->tm_x;
   ax.src = p->phi0;
@@ -271,12 +277,16 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
   ax.nhp = p->nhp;
   ax.batch = p->batch;
   ax.err = p->err;
-  PIN_CK(p, launch_x(p->nx, ax, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 1], p->stream, cudaEventRecordExternal));
+  return ax;
+}
 
-  // y pass, outputs grouped by source so that each staged tile serves them in
-  // a row: V[xx] <- U2; V[xy] <- U1 (k_y), V[xz] <- U1 (z: k_z);
-  // V[yy] <- U0 (k_y^2), V[zz] <- U0 (z: k_z^2), V[yz] <- U0 (k_y; z: k_z)
+// y pass of one radius, outputs grouped by source so that each staged tile
+// serves them in a row: V[xx] <- U2; V[xy] <- U1 (k_y), V[xz] <- U1 (z: k_z);
+// V[yy] <- U0 (k_y^2), V[zz] <- U0 (z: k_z^2), V[yz] <- U0 (k_y; z: k_z).
+// With the velocities of a collapse call, the smoothed displacement
+// psi = i k W Phi0 shares the y transforms of xz (psi_x: z factor W), zz
+// (psi_z: z factor k W) and yz (psi_y: z factor W).
+ArgsY radius_args_y(pin_plan_t p, int ms, bool collapse) {
   static const int vout[6] = {0, 3, 4, 1, 2, 5};
   static const int sel[6] = {2, 1, 1, 0, 0, 0};
   static const int ym[6] = {0, 1, 0, 2, 0, 1};
@@ -292,8 +302,6 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
     ay.muli[o] = 0;
   }
   if (p->velocities && collapse) {
-    // smoothed displacement psi = i k W Phi0 shares the y transforms of
-    // xz (psi_x: z factor W), zz (psi_z: z factor k W) and yz (psi_y: z factor W)
     ay.dst2[2] = spec(p, p->V, 6);
     ay.zm2[2] = 0;
     ay.muli2[2] = 1;
@@ -313,7 +321,22 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
   ay.nhp = p->nhp;
   ay.batch = p->batch;
   ay.err = p->err;
-  PIN_CK(p, launch_y(p->ny, ay, p->stream));
+  return ay;
+}
+
+// Filter-and-transform passes of one radius (mult set `ms`), ending in the
+// collapse update (dump and source null), a dump of the six real components,
+// or the 2LPT source field S of every particle (source, batch 1).
+pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, float* source = nullptr) {
+  const bool collapse = dump == nullptr && source == nullptr;
+  const bool rec = p->profile && collapse && !p->events.empty();
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 0], p->stream, cudaEventRecordExternal));
+  const ArgsX ax = radius_args_x(p, ms);
+  PIN_CK(p, launch_x(p->nx, p->tc_x, ax, p->stream));
+  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 1], p->stream, cudaEventRecordExternal));
+
+  const ArgsY ay = radius_args_y(p, ms, collapse);
+  PIN_CK(p, launch_y(p->ny, p->tc_y, ay, p->stream));
   if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 2], p->stream, cudaEventRecordExternal));
 
   ArgsZ az{};
@@ -409,6 +432,67 @@ pin_status check_error_word(pin_plan_t p) {
 
 pin_status finish_host(pin_plan_t p) {
   PIN_CK(p, cudaStreamSynchronize(p->stream));
+  return check_error_word(p);
+}
+
+// ------------------------------------------------------------ tile tuner --
+// Tile widths chosen by pin_autotune, per grid shape, batch and mode, shared
+// by every plan of the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+std::tuple<int, int, int, int, int> tune_key(pin_plan_t p) {
+  return std::make_tuple(p->nx, p->ny, p->nz, p->batch, p->velocities ? 1 : 0);
+}
+
+bool tile_allowed(int n, int tc) {
+  int opts[2];
+  const int k = xy_tile_options(n, opts);
+  for (int i = 0; i < k; ++i)
+    if (opts[i] == tc) return true;
+  return false;
+}
+
+// Re-encode the plan's tensor maps for new tile widths; the captured graph
+// holds the old maps and launch shapes, so it is dropped (after the stream
+// drains) and captured again by the next call.
+pin_status apply_tiles(pin_plan_t p, int tc_x, int tc_y) {
+  CUtensorMap mx, my;
+  if (make_tmap_x(&mx, p->phi0, p->nx, p->ny, p->nhp, p->batch, tc_x) != cudaSuccess ||
+      make_tmap_y(&my, p->U, p->nx, p->ny, p->nhp, p->field_elems, p->batch, tc_y) != cudaSuccess)
+    return fail(p, PIN_ECUDA, "tensor map encoding failed");
+  PIN_CK(p, cudaStreamSynchronize(p->stream));
+  drop_graph(p);
+  p->tm_x = mx;
+  p->tm_y = my;
+  p->tc_x = tc_x;
+  p->tc_y = tc_y;
+  return PIN_OK;
+}
+
+// Mean device time (ms) of `reps` launches of the first radius's x or y pass
+// at tile width tc, after one untimed launch, on the plan's stream.
+pin_status time_pass(pin_plan_t p, bool y_pass, int tc, int reps, float* ms) {
+  ArgsX ax = radius_args_x(p, 0);
+  ArgsY ay = radius_args_y(p, 0, true);
+  cudaError_t e = y_pass ? make_tmap_y(&ay.tm, p->U, p->nx, p->ny, p->nhp, p->field_elems, p->batch, tc)
+                         : make_tmap_x(&ax.tm, p->phi0, p->nx, p->ny, p->nhp, p->batch, tc);
+  if (e != cudaSuccess) return fail(p, PIN_ECUDA, "tensor map encoding failed");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PIN_CK(p, cudaEventCreate(&e0));
+  e = cudaEventCreate(&e1);
+  for (int r = 0; e == cudaSuccess && r <= reps; ++r) {
+    if (r == 1) e = cudaEventRecord(e0, p->stream);
+    if (e == cudaSuccess) e = y_pass ? launch_y(p->ny, tc, ay, p->stream) : launch_x(p->nx, tc, ax, p->stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(p, e, "timing a pass");
+  *ms = t / reps;
   return check_error_word(p);
 }
 
@@ -516,8 +600,10 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
       cudaMemset(p->counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess)
     return bail(PIN_ECUDA);
-  if (make_tmap_x(&p->tm_x, p->phi0, p->nx, p->ny, p->nhp, p->batch) != cudaSuccess ||
-      make_tmap_y(&p->tm_y, p->U, p->nx, p->ny, p->nhp, p->field_elems, p->batch) != cudaSuccess)
+  p->tc_x = p->shape_x.tc;
+  p->tc_y = p->shape_y.tc;
+  if (make_tmap_x(&p->tm_x, p->phi0, p->nx, p->ny, p->nhp, p->batch, p->tc_x) != cudaSuccess ||
+      make_tmap_y(&p->tm_y, p->U, p->nx, p->ny, p->nhp, p->field_elems, p->batch, p->tc_y) != cudaSuccess)
     return bail(PIN_ECUDA);
   *out = p;
   return PIN_OK;
@@ -668,7 +754,7 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
   const size_t n3 = p->n3();
   const int r0 = p->nscales;  // the R = 0 multiplier set
   ArgsX ax{};
-  cudaError_t e = make_tmap_x(&ax.tm, phi, p->nx, p->ny, p->nhp, 1);
+  cudaError_t e = make_tmap_x(&ax.tm, phi, p->nx, p->ny, p->nhp, 1, p->tc_x);
   if (e != cudaSuccess) return e;
   ax.src = phi;
   ax.dst[0] = a0;
@@ -682,11 +768,11 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
   ax.nhp = p->nhp;
   ax.batch = 1;
   ax.err = p->err;
-  e = launch_x(p->nx, ax, p->stream);
+  e = launch_x(p->nx, p->tc_x, ax, p->stream);
   if (e != cudaSuccess) return e;
   // psi_x <- a1 (k_x), psi_y <- a0 (k_y), psi_z <- a0 (z: k_z); all times i
   ArgsY ay{};
-  e = make_tmap_y(&ay.tm, a0, p->nx, p->ny, p->nhp, p->field_elems, 1);
+  e = make_tmap_y(&ay.tm, a0, p->nx, p->ny, p->nhp, p->field_elems, 1, p->tc_y);
   if (e != cudaSuccess) return e;
   ay.src[0] = a0;
   ay.src[1] = a0 + p->field_elems;
@@ -708,7 +794,7 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
   ay.nhp = p->nhp;
   ay.batch = 1;
   ay.err = p->err;
-  e = launch_y(p->ny, ay, p->stream);
+  e = launch_y(p->ny, p->tc_y, ay, p->stream);
   if (e != cudaSuccess) return e;
   ArgsZ az{};
   for (int f = 0; f < 3; ++f) {
@@ -767,7 +853,7 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
   if (st == PIN_OK && e == cudaSuccess) {
     const int r0 = p->nscales;
     ArgsY ay{};
-    e = make_tmap_y(&ay.tm, V0, nx, ny, p->nhp, p->field_elems, 1);
+    e = make_tmap_y(&ay.tm, V0, nx, ny, p->nhp, p->field_elems, 1, p->tc_y);
     ay.src[0] = V0;
     ay.src[1] = V0;
     ay.src[2] = V0;
@@ -781,9 +867,9 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
     ay.nhp = p->nhp;
     ay.batch = 1;
     ay.err = p->err;
-    if (e == cudaSuccess) e = launch_y(ny, ay, p->stream);
+    if (e == cudaSuccess) e = launch_y(ny, p->tc_y, ay, p->stream);
     ArgsX ax{};
-    if (e == cudaSuccess) e = make_tmap_x(&ax.tm, spec(p, p->V, 1), nx, ny, p->nhp, 1);
+    if (e == cudaSuccess) e = make_tmap_x(&ax.tm, spec(p, p->V, 1), nx, ny, p->nhp, 1, p->tc_x);
     ax.src = spec(p, p->V, 1);
     ax.dst[0] = spec(p, p->V, 2);
     ax.nout = 1;
@@ -793,7 +879,7 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
     ax.nhp = p->nhp;
     ax.batch = 1;
     ax.err = p->err;
-    if (e == cudaSuccess) e = launch_x(nx, ax, p->stream);
+    if (e == cudaSuccess) e = launch_x(nx, p->tc_x, ax, p->stream);
     // 3) Phi2 = (3/7) S(k) / k^2 with S(k) = conj(T) (forward transform of real S), into U0
     if (e == cudaSuccess)
       e = launch_phi2(spec(p, p->V, 2), U0, nx, ny, nz, p->nhp, p->box, (float)(3.0 / 7.0 * (double)n3),
@@ -860,11 +946,81 @@ pin_status pin_profile(pin_plan_t p, int enable) {
     for (auto& e : p->events) PIN_CK(p, cudaEventCreate(&e));
   }
   p->profile = want;
-  // rebuild the graph with (or without) the event records
-  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-  if (p->graph) cudaGraphDestroy(p->graph);
-  p->graph_exec = nullptr;
-  p->graph = nullptr;
+  drop_graph(p);  // rebuilt with (or without) the event records
+  return PIN_OK;
+}
+
+pin_status pin_tile_options(int n, int* opts, int* count) {
+  if (!opts || !count) return PIN_EINVAL;
+  const int k = xy_tile_options(n, opts);
+  if (k == 0) return PIN_EINVAL;
+  *count = k;
+  return PIN_OK;
+}
+
+pin_status pin_get_tiles(pin_plan_t p, int* tc_x, int* tc_y) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!tc_x || !tc_y) return fail(p, PIN_EINVAL, "null output");
+  *tc_x = p->tc_x;
+  *tc_y = p->tc_y;
+  return PIN_OK;
+}
+
+pin_status pin_set_tiles(pin_plan_t p, int tc_x, int tc_y) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (tc_x == 0) tc_x = p->shape_x.tc;
+  if (tc_y == 0) tc_y = p->shape_y.tc;
+  if (!tile_allowed(p->nx, tc_x) || !tile_allowed(p->ny, tc_y))
+    return fail(p, PIN_EINVAL, "tile width is not one of pin_tile_options");
+  if (tc_x == p->tc_x && tc_y == p->tc_y) return PIN_OK;
+  return apply_tiles(p, tc_x, tc_y);
+}
+
+pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (reps < 1 || reps > 1000) return fail(p, PIN_EINVAL, "reps must be in 1..1000");
+  if (flags & ~PIN_TUNE_FORCE) return fail(p, PIN_EINVAL, "unknown flags");
+  const auto key = tune_key(p);
+  std::pair<int, int> best{0, 0};
+  bool cached = false;
+  if (!(flags & PIN_TUNE_FORCE)) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    // the passes only read Phi0 (zeros until a field is set) and write the
+    // U and V workspaces; F_max, the index and v_max are untouched
+    if (!p->ic_set) PIN_CK(p, cudaMemsetAsync(p->phi0, 0, p->field_elems * sizeof(float2), p->stream));
+    for (int pass = 0; pass < 2; ++pass) {
+      int opts[2];
+      const int k = xy_tile_options(pass ? p->ny : p->nx, opts);
+      float best_ms = 0.f;
+      for (int i = 0; i < k; ++i) {
+        float ms = 0.f;
+        st = time_pass(p, pass == 1, opts[i], reps, &ms);
+        if (st != PIN_OK) return st;
+        if (i == 0 || ms < best_ms) {
+          best_ms = ms;
+          (pass ? best.second : best.first) = opts[i];
+        }
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  if (best.first != p->tc_x || best.second != p->tc_y) {
+    st = apply_tiles(p, best.first, best.second);
+    if (st != PIN_OK) return st;
+  }
+  if (tc_x) *tc_x = p->tc_x;
+  if (tc_y) *tc_y = p->tc_y;
   return PIN_OK;
 }
 

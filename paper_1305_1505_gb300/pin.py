@@ -20,6 +20,7 @@ PIN_OK, PIN_EINVAL, PIN_ENOMEM, PIN_ECUDA, PIN_EBUSY, PIN_ETIMEOUT, PIN_ESTATE =
 PIN_CORR_NONE, PIN_CORR_SPHERE = 0, 1
 PIN_FP32_FALLBACK64 = 0
 PIN_C64, PIN_C128 = 0, 1
+PIN_TUNE_FORCE = 1
 
 MAX_SCALES = 64
 
@@ -55,8 +56,9 @@ class pin_stats(ctypes.Structure):
 EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_hessian",
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
-           "pin_fragment_order", "pin_displacements_2lpt", "pin_set_ic_seed", "pin_strerror",
-           "pin_last_error", "pin_destroy")
+           "pin_fragment_order", "pin_displacements_2lpt", "pin_set_ic_seed", "pin_tile_options",
+           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_strerror", "pin_last_error",
+           "pin_destroy")
 
 _lib = None
 
@@ -102,6 +104,15 @@ def load(path=None):
     L.pin_profile.restype = ctypes.c_int
     L.pin_pass_times.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     L.pin_pass_times.restype = ctypes.c_int
+    IP = ctypes.POINTER(ctypes.c_int)
+    L.pin_tile_options.argtypes = [ctypes.c_int, IP, IP]
+    L.pin_tile_options.restype = ctypes.c_int
+    L.pin_get_tiles.argtypes = [P, IP, IP]
+    L.pin_get_tiles.restype = ctypes.c_int
+    L.pin_set_tiles.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    L.pin_set_tiles.restype = ctypes.c_int
+    L.pin_autotune.argtypes = [P, ctypes.c_int, ctypes.c_int, IP, IP]
+    L.pin_autotune.restype = ctypes.c_int
     L.pin_collapse_times_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.c_int, P, P, P]
@@ -225,6 +236,34 @@ def pin_pass_times(plan):
     ms = (ctypes.c_double * 4)()
     _check(load().pin_pass_times(plan, ms), plan)
     return list(ms)
+
+
+def pin_tile_options(n):
+    """Tile widths (columns per block) the x/y pass over lines of n points can
+    run, the default first."""
+    opts = (ctypes.c_int * 2)()
+    k = ctypes.c_int(0)
+    _check(load().pin_tile_options(int(n), opts, ctypes.byref(k)))
+    return list(opts[:k.value])
+
+
+def pin_get_tiles(plan):
+    """(x-pass, y-pass) tile widths the plan runs."""
+    x, y = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().pin_get_tiles(plan, ctypes.byref(x), ctypes.byref(y)), plan)
+    return x.value, y.value
+
+
+def pin_set_tiles(plan, tc_x, tc_y):
+    _check(load().pin_set_tiles(plan, int(tc_x), int(tc_y)), plan)
+
+
+def pin_autotune(plan, reps=3, flags=0):
+    """Times the candidate tile widths of the x and y passes and keeps the
+    fastest (kept per grid shape for the process); returns (tc_x, tc_y)."""
+    x, y = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().pin_autotune(plan, int(reps), int(flags), ctypes.byref(x), ctypes.byref(y)), plan)
+    return x.value, y.value
 
 
 def pin_collapse_times_noalloc(delta_k_ptr, dtype, n, box, radii, correction, fmax_ptr, idx_ptr,
@@ -380,6 +419,20 @@ class Plan:
     def sync(self, timeout_s=None):
         st = pin_sync(self.handle, -1 if timeout_s is None else int(timeout_s * 1e9))
         _check(st, self.handle)
+
+    def tiles(self):
+        """(x-pass, y-pass) tile widths in use."""
+        return pin_get_tiles(self.handle)
+
+    def set_tiles(self, tc_x=0, tc_y=0):
+        """Forces tile widths (0: the default); each must be one of
+        pin_tile_options of the pass's line length."""
+        pin_set_tiles(self.handle, tc_x, tc_y)
+
+    def autotune(self, reps=3, force=False):
+        """Times the candidate tile widths on this plan and keeps the fastest;
+        returns (tc_x, tc_y)."""
+        return pin_autotune(self.handle, reps, PIN_TUNE_FORCE if force else 0)
 
     def stats(self):
         return pin_get_stats(self.handle)

@@ -64,3 +64,22 @@ def test_null_plan_calls_are_rejected():
     assert L.pin_sync(None, 0) == pin.PIN_EINVAL
     assert L.pin_kernels_per_call(None) == 0
     L.pin_destroy(None)
+
+
+def test_tile_options_without_gpu():
+    """Candidate x/y tile widths: the default first, then half of it while a
+    TMA box row stays at least 64 bytes (8 complex values); nothing for an
+    unsupported size; the plan-level calls reject a null plan."""
+    for n in (8, 16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768):
+        opts = pin.pin_tile_options(n)
+        assert 1 <= len(opts) <= 2 and all(t >= 8 for t in opts), (n, opts)
+        if len(opts) == 2:
+            assert opts[1] * 2 == opts[0], (n, opts)
+    assert pin.pin_tile_options(768) == [16, 8]
+    with pytest.raises(pin.PinError):
+        pin.pin_tile_options(100)
+    L = pin.load()
+    x = ctypes.c_int(0)
+    assert L.pin_get_tiles(None, ctypes.byref(x), ctypes.byref(x)) == pin.PIN_EINVAL
+    assert L.pin_set_tiles(None, 0, 0) == pin.PIN_EINVAL
+    assert L.pin_autotune(None, 3, 0, None, None) == pin.PIN_EINVAL
