@@ -126,7 +126,7 @@ TRAFFIC_SOURCES = ["kernels.cu", "kernels.cuh", "fft.cuh", "collapse.cuh", "pin.
 MEASURED_TRAFFIC = {
     # profiles/launch_list_768x40.md: dram bytes and warp instructions of the
     # fused z pass per launch, 768^3 x 40
-    ("k_pass_z", 768, False): {"sources": "ed55a84604a1a0da", "bytes_per_launch": 16.762e9,
+    ("k_pass_z", 768, False): {"sources": "431ae2b04bd8b0a6", "bytes_per_launch": 16.761e9,
                                "warp_inst_per_launch": 6.945e9},
 }
 
