@@ -15,8 +15,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _run(plan, vel=False):
+    """Every product that goes through the x/y passes: collapse times, the
+    deformation tensor, the Zel'dovich and second-order displacements (and
+    v_max with velocities)."""
     F, I = plan.collapse_times()
-    out = [F.clone(), I.clone(), plan.hessian(1).clone()]
+    out = [F.clone(), I.clone(), plan.hessian(1).clone(), plan.displacements().clone(),
+           plan.displacements_2lpt().clone()]
     if vel:
         out.append(plan.velocities().clone())
     return out

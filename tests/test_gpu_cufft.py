@@ -8,7 +8,8 @@ computed by cuFFT's complex-to-real transform with the inverse convention of
 the method (1/N^3 on the inverse), the Gaussian window W = exp(-k^2 R^2 / 2),
 k = 0 removed, and the odd factors k_i zero where their index is the Nyquist
 one (off-diagonal components and displacements), as in the readings of the
-filter."""
+filter; and the trace rule phi_xx + phi_yy + phi_zz = IDFT(W delta) within
+1e-5 of its rms."""
 import math
 
 import numpy as np
@@ -80,12 +81,20 @@ def _check(shape, box, d64_dev, radii, label):
         plan.set_ic(d64_dev.to(torch.complex64))
         # the path sees the FP32 spectrum: the checker transforms the same values
         d = d64_dev.to(torch.complex64).to(torch.complex128)
+        ks, _ = _wavenumbers(shape, box)
+        k2 = ks[0] ** 2 + ks[1] ** 2 + ks[2] ** 2
         for s, R in enumerate(radii):
             h = plan.hessian(s).double()
             ref, psi_ref = _cufft_fields(d, shape, box, R)
             rms = float(ref.pow(2).mean().sqrt())
             err = float((h - ref).abs().max())
             assert err < 2e-5 * rms, "%s R=%g: max |phi - cuFFT| = %.3g (rms %.3g)" % (label, R, err, rms)
+            # trace rule: phi_xx + phi_yy + phi_zz = IDFT(W delta) with k = 0 removed
+            wd = torch.exp(-0.5 * k2 * R * R) * torch.where(k2 == 0, torch.zeros_like(d), d)
+            tr_ref = torch.fft.irfftn(wd, s=shape)
+            trms = float(tr_ref.pow(2).mean().sqrt())
+            terr = float((h[0] + h[1] + h[2] - tr_ref).abs().max())
+            assert terr < 1e-5 * trms, "%s R=%g: trace off by %.3g (rms %.3g)" % (label, R, terr, trms)
         psi = plan.displacements().double()
         prms = float(psi_ref.pow(2).mean().sqrt())
         perr = float((psi - psi_ref).abs().max())
