@@ -69,10 +69,14 @@ class PinEngine:
     arrives), delta(k) generated on the device from the request's seed
     (pin_set_ic_seed), the whole radius loop, results copied to the host."""
 
-    def __init__(self, device=0):
+    def __init__(self, device=0, priority_from_n=0):
+        """priority_from_n > 0: requests with N at or above it run on a
+        high-priority stream (the device's block scheduler then serves their
+        kernels first), the rest on normal ones."""
         import torch
         self.torch = torch
         self.device = device
+        self.priority_from_n = int(priority_from_n)
 
     def warm(self, sizes, box_per_cell=2.0):
         """Loads the library and tunes the tile widths of each grid size on an
@@ -93,7 +97,8 @@ class PinEngine:
     def run(self, req, timeout_s=None):
         torch = self.torch
         torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream()
+        high = self.priority_from_n > 0 and req.n >= self.priority_from_n
+        stream = torch.cuda.Stream(priority=-1 if high else 0)
         plan = pin.Plan(req.n, req.box, req.radii, stream=stream)
         try:
             plan.autotune()  # the kept choice for this shape (timed once per process)
@@ -264,10 +269,12 @@ def main():
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=0.0, help="0: 80%% of free device memory")
+    ap.add_argument("--priority-from-n", type=int, default=0,
+                    help="grid size from which requests run on a high-priority stream (0: none)")
     args = ap.parse_args()
     free, _ = torch.cuda.mem_get_info()
     budget = int(args.budget_gb * 2 ** 30) if args.budget_gb > 0 else int(0.8 * free)
-    eng = PinEngine()
+    eng = PinEngine(priority_from_n=args.priority_from_n)
     tiles = eng.warm([64, 128, 256, 512])
     eng.run(Request(-1, 64, 128.0, 1, [8.0, 4.0]))  # warm up
     def measure(rate):
@@ -284,6 +291,7 @@ def main():
                         "box 2 Mpc/h per cell, 20-40 radii 40->2 Mpc/h, seed %d"
                         % (args.requests, args.seed),
             "tiles": {str(k): list(v) for k, v in tiles.items()},
+            "priority_from_n": args.priority_from_n,
             "nominal": measure(args.rate)}
     if args.stress_rate > 0:
         line["stress"] = measure(args.stress_rate)
