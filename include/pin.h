@@ -3,8 +3,8 @@
  * PINOCCHIO method (Monaco et al. 2013, Sec. 2.1.1 "Collapse times").
  *
  * The problem, as the paper states it: a Gaussian linear density field
- * delta_l on an N^3 grid of side L (Sec. 2.1.1, Eq. "deltal") is smoothed on a
- * set of radii R with a Gaussian filter; for each R a series of FFTs gives the
+ * delta_l on an N^3 grid of side L (Sec. 2.1.1, Eq. "deltal") is filtered with
+ * a Gaussian window at each of several radii R; for each R inverse FFTs give the
  * deformation tensor (Hessian of the peculiar potential), and per grid point
  * ("particle") the ellipsoidal truncation of third-order LPT with its
  * quasi-spherical correction gives the inverse collapse time F = 1/D(t_coll)
@@ -58,7 +58,7 @@ enum { PIN_C64 = 0, PIN_C128 = 1 };
 
 typedef struct {
   int nx, ny, nz;        /* grid, each in {8,16,32,48,64,96,128,192,256,384,512,768}; they
-                            may differ (the paper's code runs on non-cubic grids as well,
+                            may differ (non-cubic boxes are allowed by the paper's code,
                             Sec. 2.1.1); the cells are cubic */
   double box;            /* side along x in Mpc/h, > 0; the sides along y and z are
                             box ny / nx and box nz / nx */
@@ -129,8 +129,8 @@ pin_status pin_set_ic_seed(pin_plan_t p, uint64_t seed, const pin_spectrum* ps);
  * call returns when the results are in host memory. */
 pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, int on_device);
 
-/* v_max of Sec. 2.1.1: for each particle, the first derivative of the peculiar
- * potential smoothed on R_max, as the linear (Zel'dovich) displacement
+/* v_max of Sec. 2.1.1: for each particle, the gradient of the potential
+ * (smoothed on R_max), taken as the linear (Zel'dovich) displacement
  * psi_R(k) = i k W(kR) delta(k)/k^2 at the radius where F_max was reached
  * (zero where the particle never collapses), from the last
  * pin_collapse_times call of a plan created with velocities = 1.  Output

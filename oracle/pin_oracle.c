@@ -11,7 +11,7 @@
  *     1. T_ij(k) = (k_i k_j / k^2) W(kR) delta(k), W Gaussian (Sec. 2.1.1:
  *        smoothing with a Gaussian filter; the deformation tensor is the
  *        Hessian of the peculiar potential, with del^2 phi = delta).
- *     2. phi_ij(q) = inverse 3D DFT of T_ij ("a series of FFTs").
+ *     2. phi_ij(q) = inverse 3D DFT of T_ij.
  *     3. per grid point, eigenvalues lambda1 >= lambda2 >= lambda3 of phi_ij
  *        (principal axes of the ellipsoid).
  *     4. collapse of the first axis (orbit crossing) under the ellipsoidal
@@ -314,7 +314,7 @@ int or_hessian_points(const double* delta_half_ri, int n, double box, double rad
 
 /* Zel'dovich displacement of the field smoothed on radius R (Sec. 2.1.2:
  * particles and halos are displaced with the ZA, first-order LPT; Sec. 2.1.1:
- * v_max comes from the first derivative of the potential smoothed on R_max):
+ * v_max is the potential's gradient, smoothed on R_max):
  * x = q + psi with psi = -grad phi and del^2 phi = delta, i.e.
  * psi_i(k) = i k_i W(kR) delta(k) / k^2, so that delta = -div psi for R = 0.
  * A mode whose k_i sits on the Nyquist index is zeroed for component i (the

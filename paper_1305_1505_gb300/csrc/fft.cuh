@@ -1,6 +1,7 @@
-// Register-resident inverse DFTs and the two-level column FFT used by every
-// pass of the collapse-time path (Sec. 2.1.1: "for each smoothing radius the
-// code performs a series of FFTs to compute the deformation tensor").
+// Register-resident inverse DFTs and the line FFTs (two or three levels) used
+// by every pass of the collapse-time path: each smoothing radius needs the
+// deformation tensor in real space, i.e. inverse 3D transforms of the
+// filtered spectra (Sec. 2.1.1).
 //
 // Convention: inverse transforms, X[k] = sum_n x[n] exp(+2 pi i n k / N), no
 // normalisation here (the 1/N of each axis is folded into the per-axis
@@ -222,10 +223,10 @@ __device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { retur
 // on return v[m P1 + k2b] holds the pair (k1, k2a) = divmod(p + P m, P2).
 // fft_out_index gives the frequency of each slot.  All threads of the block
 // must call it; it synchronises once (twice more for three levels) and leaves
-// the exchange buffer in use (callers synchronise before writing s_x again).
-// WARP: every transform is held within one warp (P divides 32, transform c on
-// threads [c P, c P + P)) with an exchange region of its own, so the
-// exchanges need only warp-level synchronisation.
+// the exchange buffer in use (callers synchronise the block before writing
+// s_x again).  WARP: every transform is held within one warp (P divides 32,
+// transform c on threads [c P, c P + P)) with an exchange region of its own,
+// so those synchronisations are warp-level.
 template <int N, class Layout, bool WARP = false>
 __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c, float2* s_x,
                                          const float2* s_tw) {

@@ -6,8 +6,10 @@
 //             Hessian components (two per complex transform), then per grid
 //             point the eigenvalues, the collapse time F = 1/D_c and the
 //             running maximum F_max with its radius index, written in place.
-// Each thread block owns a tile of lines; every line is transformed with the
-// two-level register FFT of fft.cuh (one shared-memory exchange per line).
+// Each thread block owns a tile of lines; every line is transformed by the
+// register FFT of fft.cuh (two levels with one shared-memory exchange, or,
+// for 384 and 768 points, three levels with two).  The x and y passes run one
+// of two compiled tile widths, chosen per plan (pin_autotune).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

@@ -1,6 +1,6 @@
-"""Smoothing radii spaced in mass variance (Sec. 2.1.1: the radii are chosen
-so that the corresponding mass variances are logarithmically spaced by
-0.15 dex; 10 to 20 radii sample the trajectories).
+"""Smoothing radii spaced in mass variance (Sec. 2.1.1: successive radii
+differ by a fixed 0.15 dex step in the variance of the smoothed field, and
+10 to 20 of them suffice for the trajectories).
 
 Reading: sigma^2(R) is the expected variance of the field smoothed with the
 Gaussian window W = exp(-k^2 R^2 / 2) on the simulation grid itself,

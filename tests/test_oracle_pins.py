@@ -612,7 +612,7 @@ def test_trace_and_displacement_divergence_non_cubic(shape, radius):
     assert np.abs(div - lapl).max() < 1e-11 * np.abs(lapl).max()
 
 
-# ---- mass variance of the smoothed field (radius schedule) ----
+# ---- variance of the field after smoothing (radius schedule) ----
 
 @pytest.mark.parametrize("shape,radius", [((8, 8, 8), 0.0), ((8, 12, 16), 3.0), ((16, 8, 12), 7.5)])
 def test_sigma2_flat_spectrum_closed_form(shape, radius):
