@@ -222,10 +222,10 @@ pin_status pin_pass_times(pin_plan_t p, double* ms4);
  * launch; the first radius, the plan's mode) and keeps the fastest of each.
  * Only the plan's workspaces are written (Phi0 is zeroed first if no field
  * is set); F_max, the scale index and v_max are untouched.  Choices are kept
- * per (nx, ny, nz, batch, velocities) for the process: a later call for the
- * same shape applies the kept choice without timing unless flags has
+ * per (device, nx, ny, nz, batch, velocities) for the process: a later call
+ * for the same shape applies the kept choice without timing unless flags has
  * PIN_TUNE_FORCE.  The chosen widths go to *tc_x and *tc_y (either may be
- * NULL).  Not to be called while the plan's stream is being captured. */
+ * NULL).  PIN_ESTATE while the plan's stream is being captured. */
 #define PIN_TUNE_FORCE 1
 pin_status pin_tile_options(int n, int* opts, int* count);
 pin_status pin_get_tiles(pin_plan_t p, int* tc_x, int* tc_y);

@@ -436,13 +436,14 @@ pin_status finish_host(pin_plan_t p) {
 }
 
 // ------------------------------------------------------------ tile tuner --
-// Tile widths chosen by pin_autotune, per grid shape, batch and mode, shared
-// by every plan of the process.
+// Tile widths chosen by pin_autotune, per device, grid shape, batch and mode,
+// shared by every plan of the process.
+using TuneKey = std::tuple<int, int, int, int, int, int>;
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 
-std::tuple<int, int, int, int, int> tune_key(pin_plan_t p) {
-  return std::make_tuple(p->nx, p->ny, p->nz, p->batch, p->velocities ? 1 : 0);
+TuneKey tune_key(pin_plan_t p) {
+  return std::make_tuple(p->device, p->nx, p->ny, p->nz, p->batch, p->velocities ? 1 : 0);
 }
 
 bool tile_allowed(int n, int tc) {
@@ -983,6 +984,9 @@ pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y)
   if (st != PIN_OK) return st;
   if (reps < 1 || reps > 1000) return fail(p, PIN_EINVAL, "reps must be in 1..1000");
   if (flags & ~PIN_TUNE_FORCE) return fail(p, PIN_EINVAL, "unknown flags");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  PIN_CK(p, cudaStreamIsCapturing(p->stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return fail(p, PIN_ESTATE, "the plan's stream is being captured");
   const auto key = tune_key(p);
   std::pair<int, int> best{0, 0};
   bool cached = false;

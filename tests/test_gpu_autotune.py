@@ -85,3 +85,25 @@ def test_tuner_keeps_its_choice_and_rejects_bad_widths():
     finally:
         a.close()
         b.close()
+
+
+def test_tuner_refuses_inside_stream_capture():
+    """Timing cannot happen while the plan's stream records a graph: the call
+    returns PIN_ESTATE without enqueuing anything."""
+    import torch
+    s = torch.cuda.Stream()
+    plan = pin.Plan(32, 64.0, [4.0, 2.0], stream=s)
+    try:
+        x = torch.zeros(8, device="cuda")
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            x.add_(1.0)
+            with pytest.raises(pin.PinError) as e:
+                plan.autotune(force=True)
+        assert e.value.status == pin.PIN_ESTATE
+        g.replay()
+        torch.cuda.synchronize()
+        assert float(x.sum()) == 8.0
+        assert plan.autotune(reps=2, force=True) == plan.tiles()
+    finally:
+        plan.close()
