@@ -439,9 +439,10 @@ class Plan:
 
 
 def collapse_times(delta_k, radii, box, correction=PIN_CORR_SPHERE):
-    """One-shot: (F_max, scale_idx) for the half-spectrum delta_k."""
-    n = delta_k.shape[0]
-    plan = Plan(n, box, radii, correction)
+    """One-shot: (F_max, scale_idx) for the half-spectrum delta_k of shape
+    (nx, ny, nz//2+1) (every supported nz is even; cubic cells, box along x)."""
+    nx, ny, nh = delta_k.shape
+    plan = Plan((nx, ny, 2 * (nh - 1)), box, radii, correction)
     try:
         plan.set_ic(delta_k)
         f, i = plan.collapse_times()

@@ -85,3 +85,24 @@ def test_non_cubic_fragment_order():
     assert np.array_equal(nb.cpu().numpy().astype(np.int64), nbref)
     plan.close()
 
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 32, 16)])
+def test_one_shot_helper_matches_plan(shape):
+    """pin.collapse_times(delta_k, radii, box) reads the grid from the
+    half-spectrum's shape and gives the plan's results bit for bit."""
+    import torch
+    from paper_1305_1505_gb300 import pin
+    box = 2.0 * shape[0]
+    radii = ic.log_radii(2.0, box * min(shape) / shape[0] / 4, 4)
+    d32, _ = _field(shape, box, 83)
+    dk = torch.from_numpy(d32).cuda()
+    F1, I1 = pin.collapse_times(dk, radii, box)
+    plan = pin.Plan(shape, box, radii)
+    try:
+        plan.set_ic(dk)
+        F2, I2 = plan.collapse_times()
+        assert tuple(F1.shape) == shape
+        assert torch.equal(F1, F2) and torch.equal(I1, I2)
+    finally:
+        plan.close()
