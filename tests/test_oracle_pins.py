@@ -328,6 +328,60 @@ def test_first_root_degenerate_degrees():
     assert abs(got - 1.0) < 1e-6
 
 
+# --------------------------------------------- collapse entry points pins --
+
+def test_collapse_F_is_collapse_point_of_the_diagonal():
+    """collapse_F takes sorted eigenvalues; on a diagonal Hessian (no rotation
+    needed) it must equal collapse_point, whose pins above cover the model."""
+    rng = np.random.default_rng(31)
+    for _ in range(200):
+        lam = np.sort(rng.normal(size=3))[::-1]
+        for corr in (0, 1):
+            F, l = oracle.collapse_point(_h6(np.diag(lam)), correction=corr)
+            assert np.allclose(l, lam, rtol=0, atol=1e-15)
+            assert abs(oracle.collapse_F(lam, corr) - F) <= 1e-14 * max(1.0, abs(F))
+    # spheres: delta/x3 without the correction, delta/delta_c with it
+    for delta in (0.3, 1.7, 4.0):
+        lam = np.full(3, delta / 3)
+        assert abs(oracle.collapse_F(lam, 0) - delta / oracle.x3()) < 1e-12
+        assert abs(oracle.collapse_F(lam, 1) - delta / oracle.delta_c()) < 1e-12
+
+
+def test_collapse_slope_closed_forms():
+    """D a'(D) at the collapse root: 1 for one axis (a = D lambda1); for a
+    sphere of linear contrast x at collapse, x/3 + 2x^2/21 + 69x^3/1701 at
+    x = x3 (the derivative of the series that defines x3); 0 for a void."""
+    for l1 in (0.5, 2.0, 7.0):
+        assert abs(oracle.collapse_slope(np.array([l1, 0.0, 0.0])) - 1.0) < 1e-12
+    x = oracle.x3()
+    ref = x / 3 + 2 * x * x / 21 + 69 * x ** 3 / 1701
+    for delta in (0.8, 2.5):
+        assert abs(oracle.collapse_slope(np.full(3, delta / 3)) - ref) < 1e-10
+    assert oracle.collapse_slope(np.array([-0.1, -0.2, -0.3])) == 0.0
+
+
+def test_sampled_and_from_hessians_entry_points_equal_the_full_run():
+    """The two partial entry points (sampled grid points; a stack of given
+    Hessians) reproduce the full oracle run exactly at the same points: the
+    same FP64 arithmetic, only the bookkeeping differs."""
+    n, box = 16, 64.0
+    d = _field(n, box, 32)
+    radii = ic.log_radii(box / n, 16.0, 5)
+    full = oracle.collapse_times(d, box, radii)
+    q = np.random.default_rng(33).choice(n ** 3, size=300, replace=False)
+    sam = oracle.collapse_times_sampled(d, box, radii, q)
+    for k in ("fmax", "idx", "f2", "idx2"):
+        assert np.array_equal(sam[k], full[k][q]), k
+    hs = np.stack([oracle.hessian(d, box, R)[0].reshape(6, -1).T[q] for R in radii])
+    fh = oracle.collapse_from_hessians(hs)
+    for k in ("fmax", "idx"):
+        assert np.array_equal(fh[k], full[k][q]), k
+    # the runner-up and its index where a runner-up exists
+    ok = full["idx2"][q] >= 0
+    assert np.array_equal(fh["idx2"][ok], full["idx2"][q][ok])
+    assert np.array_equal(fh["f2"][ok], full["f2"][q][ok])
+
+
 # ------------------------------------------------------- running max pins --
 
 def test_running_max_is_first_strict_argmax():
