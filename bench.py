@@ -126,7 +126,7 @@ TRAFFIC_SOURCES = ["kernels.cu", "kernels.cuh", "fft.cuh", "collapse.cuh", "pin.
 MEASURED_TRAFFIC = {
     # profiles/launch_list_768x40.md: dram bytes and warp instructions of the
     # fused z pass per launch, 768^3 x 40
-    ("k_pass_z", 768, False): {"sources": "5143837fa5d9d8c6", "bytes_per_launch": 16.761e9,
+    ("k_pass_z", 768, False): {"sources": "e00300e503102fbe", "bytes_per_launch": 16.761e9,
                                "warp_inst_per_launch": 6.945e9},
 }
 
@@ -366,6 +366,11 @@ def run_ours(args):
                    "gbs": alg[nm] / (per_launch_ms[i] / 1e3) / 1e9 if alg[nm] else None,
                    "frac": alg[nm] / (per_launch_ms[i] / 1e3) / 1e9 / peak if alg[nm] else None}
               for i, nm in enumerate(names)}
+    # the whole radius loop: every pass's algorithmic bytes over the step time
+    step_bytes = S * sum(alg.values())
+    whole_step = {"alg_bytes_per_update": step_bytes / updates,
+                  "gbs": step_bytes / (ms / 1e3) / 1e9,
+                  "frac": step_bytes / (ms / 1e3) / 1e9 / peak}
     if ws > 1:
         dist.barrier()
     if rank == 0:
@@ -378,8 +383,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(_config(w), velocities=bool(args.velocities),
                            tiles={"x": tiles[0], "y": tiles[1], "tuned": not args.no_tune}),
-            "roofline": roofline(names[dom], per_launch_ms[dom], n, bool(args.velocities), fused,
-                                 achieved, peak, peak_kind, clocks, passes),
+            "roofline": dict(roofline(names[dom], per_launch_ms[dom], n, bool(args.velocities), fused,
+                                      achieved, peak, peak_kind, clocks, passes), step=whole_step),
             "cpu_baseline": cb,
             "e2e": None if args.no_e2e else {"value": updates * ws / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(d32.nbytes), "d2h_bytes_per_step": int(8 * n ** 3)},
