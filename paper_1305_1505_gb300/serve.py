@@ -11,6 +11,7 @@ the end of its radius loop; only F_max and the scale index come back.
 
 Failures are reported per request, never by a device trap:
   rejected  its footprint exceeds the whole budget (PIN_EBUSY semantics);
+  cancelled the server was closed while it waited in the queue;
   timeout   it waited in the queue, or its device work ran, past its deadline
             (the device work cannot be cancelled: its slot and memory are held
             until it drains, then released).
@@ -210,8 +211,12 @@ class Server:
             time.sleep(0.005)
 
     def close(self):
+        """Stops admitting: requests still queued are finished as "cancelled"
+        (their waiters wake up); admitted ones run to completion."""
         with self.lock:
             self._stop = True
+            while self.queue:
+                self._finish(self.queue.popleft(), "cancelled", error="server closed before admission")
             self.lock.notify_all()
         self._sched.join(timeout=5)
 

@@ -98,3 +98,15 @@ def test_workload_mix_is_seeded():
     assert all(20 <= x[4].size <= 40 for x in a)
     t = np.array([x[0] for x in a])
     assert np.all(np.diff(t) >= 0) and 50 < t[-1] < 150  # ~2 arrivals per second
+
+
+def test_close_cancels_queued_requests_and_lets_running_ones_finish():
+    eng = FakeEngine(dur=0.3)
+    srv = serve.Server(eng, budget_bytes=10 ** 9, max_slots=1)
+    reqs = [srv.submit(_req(i, 64)) for i in range(4)]
+    time.sleep(0.05)  # the first is admitted, the rest wait for the slot
+    srv.close()
+    for r in reqs[1:]:
+        assert r.wait(timeout=2.0) == "cancelled"
+    assert reqs[0].wait(timeout=2.0) == "done"
+    assert reqs[0].result == (64, 100)
