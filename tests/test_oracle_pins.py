@@ -604,6 +604,27 @@ def test_2lpt_two_crossed_waves_closed_form():
     assert np.allclose(div, -(3.0 / 7.0) * A * B * np.cos(k1 * X) * np.cos(k2 * Y), atol=1e-12)
 
 
+@pytest.mark.parametrize("shape", [(16, 8, 12), (12, 16, 8)])
+def test_2lpt_two_crossed_waves_non_cubic(shape):
+    """The crossed-wave closed form off the cube (cubic cells: the side along
+    an axis of m points is box m / nx), waves along x and z: pins the per-axis
+    wavenumbers of the second-order source and of its displacement."""
+    nx, ny, nz = shape
+    box = 48.0
+    cell = box / nx
+    X, Y, Z = np.meshgrid(np.arange(nx) * cell, np.arange(ny) * cell, np.arange(nz) * cell, indexing="ij")
+    k1, k3 = 2 * np.pi * 2 / box, 2 * np.pi * 1 / (box * nz / nx)
+    A, B = 0.6, 0.9
+    d = A * np.cos(k1 * X) + B * np.cos(k3 * Z)
+    psi2 = oracle.displacement_2lpt(_half_spectrum(d), box)
+    K2 = k1 ** 2 + k3 ** 2
+    sp, sm = np.sin(k1 * X + k3 * Z), np.sin(k1 * X - k3 * Z)
+    c = -(3.0 / 7.0) * A * B / 2 / K2
+    assert np.allclose(psi2[0], c * k1 * (sp + sm), atol=1e-12)
+    assert np.abs(psi2[1]).max() < 1e-12
+    assert np.allclose(psi2[2], c * k3 * (sp - sm), atol=1e-12)
+
+
 # ---- non-cubic grids (cubic cells: the side along an axis of m points is box m / nx) ----
 
 @pytest.mark.parametrize("shape,mode", [((8, 12, 16), (1, 2, 3)), ((16, 8, 12), (5, 1, 2)), ((12, 16, 8), (0, 7, 1)),
