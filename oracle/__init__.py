@@ -242,15 +242,14 @@ def collapse_from_hessians(h6s, correction=1):
 
 
 def fragment_order(F_max):
-    """Fragmentation front end (Sec. 2.1.2) on an (n, n, n) F_max field.
+    """Fragmentation front end (Sec. 2.1.2) on an (nx, ny, nz) F_max field.
     The particles are considered in descending F_max; equal values in
-    ascending particle index q = (x n + y) n + z (a reading: the paper states
-    no tie rule).  Returns (order, n_before): order[i] is the q of the i-th
+    ascending particle index q = (x ny + y) nz + z (a reading: the paper
+    states no tie rule).  Returns (order, n_before): order[i] is the q of the i-th
     particle considered; n_before[q] counts the six periodic neighbours of q
     (+-1 along each axis) whose rank in that order is below q's.  numpy's
     lexsort and roll serve as the sort and the shifts."""
     F = np.asarray(F_max, dtype=np.float64)
-    n = F.shape[0]
     flat = F.ravel()
     q = np.arange(flat.size)
     order = np.lexsort((q, -flat))  # last key is the primary one

@@ -514,25 +514,26 @@ def _brute_fragment(F):
     """Straight from the definitions: sort the (F, q) pairs by a key, and
     count for each particle the neighbours whose pair comes first by direct
     comparison (larger F, or equal F and smaller index)."""
-    n = F.shape[0]
+    nx, ny, nz = F.shape
     flat = [float(v) for v in F.ravel()]
-    order = sorted(range(n ** 3), key=lambda q: (-flat[q], q))
-    nb = np.zeros((n, n, n), dtype=np.int64)
-    for x in range(n):
-        for y in range(n):
-            for z in range(n):
-                q = (x * n + y) * n + z
+    order = sorted(range(nx * ny * nz), key=lambda q: (-flat[q], q))
+    nb = np.zeros((nx, ny, nz), dtype=np.int64)
+    for x in range(nx):
+        for y in range(ny):
+            for z in range(nz):
+                q = (x * ny + y) * nz + z
                 for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
-                    r = (((x + dx) % n) * n + (y + dy) % n) * n + (z + dz) % n
+                    r = (((x + dx) % nx) * ny + (y + dy) % ny) * nz + (z + dz) % nz
                     if flat[r] > flat[q] or (flat[r] == flat[q] and r < q):
                         nb[x, y, z] += 1
     return np.array(order), nb
 
 
-@pytest.mark.parametrize("n,levels", [(3, 0), (4, 5), (5, 3), (6, 0)])
-def test_fragment_order_brute_force(n, levels):
-    rng = np.random.default_rng(40 + n)
-    F = rng.random((n, n, n)).astype(np.float32)
+@pytest.mark.parametrize("shape,levels", [((3, 3, 3), 0), ((4, 4, 4), 5), ((5, 5, 5), 3), ((6, 6, 6), 0),
+                                          ((3, 5, 4), 4), ((6, 2, 3), 0), ((2, 4, 7), 2)])
+def test_fragment_order_brute_force(shape, levels):
+    rng = np.random.default_rng(40 + sum(shape))
+    F = rng.random(shape).astype(np.float32)
     if levels:  # many exact ties, including zeros (particles that never collapse)
         F = np.floor(F * levels).astype(np.float32) / levels
     order, nb = oracle.fragment_order(F)
