@@ -83,3 +83,36 @@ def test_tile_options_without_gpu():
     assert L.pin_get_tiles(None, ctypes.byref(x), ctypes.byref(x)) == pin.PIN_EINVAL
     assert L.pin_set_tiles(None, 0, 0) == pin.PIN_EINVAL
     assert L.pin_autotune(None, 3, 0, None, None) == pin.PIN_EINVAL
+
+
+def test_more_validation_and_footprint_without_gpu():
+    """Batch limits, flag values, missing radii; the footprint grows with the
+    batch and with velocities, and at 768^3 matches the workspace the layout
+    describes (10 padded spectra, F_max and index, tables, redo queue:
+    about 22.2 GB; with velocities 13 spectra and two 3 N^3 float arrays,
+    about 38.5 GB)."""
+    def fp(d):
+        return pin.pin_footprint_bytes(d)
+    base = pin.make_desc(768, 3072.0, [120.0, 4.0])
+    assert abs(fp(base) / 1e9 - 22.2) < 0.2
+    vel = pin.make_desc(768, 3072.0, [120.0, 4.0], velocities=True)
+    assert abs(fp(vel) / 1e9 - 38.5) < 0.2
+    four = pin.make_desc(768, 3072.0, [120.0, 4.0], batch=4)  # 4 x 768^3 < 2^31
+    assert fp(four) > 3.9 * fp(base)
+    assert fp(pin.make_desc(768, 3072.0, [1.0], batch=5)) == 0  # 5 x 768^3 >= 2^31
+    assert fp(pin.make_desc(8, 16.0, [1.0], batch=4096)) > 0
+    assert fp(pin.make_desc(8, 16.0, [1.0], batch=4097)) == 0
+    d = pin.make_desc(64, 100.0, [1.0])
+    d.velocities = 2
+    assert fp(d) == 0
+    d = pin.make_desc(64, 100.0, [1.0])
+    d.precision = 1
+    assert fp(d) == 0
+    d = pin.make_desc(64, 100.0, [1.0])
+    d.radii = None
+    assert fp(d) == 0
+    d = pin.make_desc(64, 100.0, [1.0])
+    d.nscales = 0
+    assert fp(d) == 0
+    assert fp(pin.make_desc(64, float("inf"), [1.0])) == 0
+    assert fp(pin.make_desc(64, 100.0, [0.0])) > 0  # R = 0 (no smoothing) is a valid radius
