@@ -13,7 +13,7 @@ unsmoothed variance cannot be exceeded.
 Host-side (numpy): it runs once per plan, before any device work.  Cells are
 cubic (box is the side along x), so k^2 is an integer multiple of
 (2 pi / (cell M))^2 with M = lcm(nx, ny, nz); the sum runs over the distinct
-integers with their multiplicities (a few 1e5 to 1e6 terms at 768^3).
+integers with their multiplicities (3.2e5 terms at 768^3).
 """
 import math
 
