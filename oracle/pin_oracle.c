@@ -20,7 +20,7 @@
  *     5. running maximum of F along the trajectory, F_max, and the index of
  *        the radius at which it was reached (R_max).
  *
- * The paper defers the formulas of steps 4 to earlier papers that are not
+ * The paper defers the formulas of step 4 to earlier papers that are not
  * available, so steps 1 and 4 follow a written reading:
  *   - filter: W = exp(-k^2 R^2 / 2), R the Gaussian sigma; signed wavenumber
  *     index in [-N/2, N/2); for i != j every mode whose k_i or k_j sits on the
