@@ -48,7 +48,9 @@ def lib():
                                        ctypes.c_double, _dp]
         L.or_collapse_times3.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_int, _dp, ctypes.c_int, _dp, _ip, _dp, _dp, _ip, _dp,
-                                         _dp]
+                                         _dp, _dp]
+        L.or_collapse_interval.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, _dp, _dp]
         L.or_eig3.argtypes = [_dp, _dp]
         L.or_axis_coeffs.argtypes = [_dp, ctypes.c_int, _dp]
         L.or_first_root.argtypes = [_dp]
@@ -186,9 +188,10 @@ def collapse_slope(lam):
 
 
 def collapse_times(delta_half, box, radii, correction=1, keep_all=False, velocities=False):
-    """Returns dict with fmax, idx (n^3), f2/idx2 (runner-up), slope, f_all
-    (S, n^3) when keep_all, and vmax (3, n^3: the smoothed displacement at the
-    radius of F_max) when velocities."""
+    """Returns dict with fmax, idx (n^3), f2/idx2 (runner-up), slope, hrms (S:
+    the grid's rms tensor norm at each radius), f_all (S, n^3) when keep_all,
+    and vmax (3, n^3: the smoothed displacement at the radius of F_max) when
+    velocities."""
     d = _c128(delta_half)
     nx, ny, nz = _grid(d)
     r = np.ascontiguousarray(radii, dtype=np.float64)
@@ -201,12 +204,13 @@ def collapse_times(delta_half, box, radii, correction=1, keep_all=False, velocit
     slope = np.empty(n3)
     f_all = np.empty((S, n3)) if keep_all else None
     vmax = np.empty((3, n3)) if velocities else None
+    hrms = np.empty(S)
     rc = lib().or_collapse_times3(_p(d.view(np.float64)), nx, ny, nz, box, S, _p(r), correction,
                                  _p(fmax), _p(idx, ctypes.c_int), _p(f_all), _p(f2),
-                                 _p(idx2, ctypes.c_int), _p(slope), _p(vmax))
+                                 _p(idx2, ctypes.c_int), _p(slope), _p(vmax), _p(hrms))
     if rc:
         raise ValueError("or_collapse_times failed: %d" % rc)
-    out = dict(fmax=fmax, idx=idx, f2=f2, idx2=idx2, slope=slope)
+    out = dict(fmax=fmax, idx=idx, f2=f2, idx2=idx2, slope=slope, hrms=hrms)
     if keep_all:
         out["f_all"] = f_all
     if velocities:
@@ -239,6 +243,36 @@ def collapse_from_hessians(h6s, correction=1):
     lib().or_collapse_from_hessians(_p(h), S, m, correction, _p(fmax), _p(idx, ctypes.c_int),
                                     _p(f2), _p(idx2, ctypes.c_int))
     return dict(fmax=fmax, idx=idx, f2=f2, idx2=idx2)
+
+
+def collapse_interval(h6s, hscale, u, correction=1):
+    """h6s: (S, npts, 6) Hessians, hscale: (S,) rms tensor norms -> (lo, hi),
+    each (S, npts): the range of F over eigenvalue errors of half-width
+    u (hscale[s] + max |lambda|) (or_collapse_interval)."""
+    h = np.ascontiguousarray(h6s, dtype=np.float64)
+    S, m, _ = h.shape
+    hs = np.ascontiguousarray(hscale, dtype=np.float64)
+    if hs.size != S:
+        raise ValueError("hscale needs one value per radius")
+    lo, hi = np.empty((S, m)), np.empty((S, m))
+    lib().or_collapse_interval(_p(h), _p(hs), S, m, correction, float(u), _p(lo), _p(hi))
+    return lo, hi
+
+
+def hessians_at(delta_half, box, radii, q_list):
+    """(S, npts, 6) Hessians at flat particle indices q for every radius: the
+    direct sum over modes for cubic grids, the full transform otherwise."""
+    d = _c128(delta_half)
+    nx, ny, nz = _grid(d)
+    q = np.ascontiguousarray(q_list, dtype=np.int64)
+    out = np.empty((len(radii), q.size, 6))
+    for s, R in enumerate(radii):
+        if nx == ny == nz:
+            out[s] = hessian_points(d, box, R, q)
+        else:
+            h, _ = hessian(d, box, R)
+            out[s] = h.reshape(6, -1)[:, q].T
+    return out
 
 
 def fragment_order(F_max):

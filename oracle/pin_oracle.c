@@ -538,7 +538,8 @@ double or_collapse_slope(const double* lam) {
 
 int or_collapse_times3(const double* delta_half_ri, int nx, int ny, int nz, double box, int nscales,
                        const double* radii, int correction, double* fmax, int* idx,
-                       double* f_all, double* f2, int* idx2, double* slope, double* vmax) {
+                       double* f_all, double* f2, int* idx2, double* slope, double* vmax,
+                       double* hrms) {
   if (nx < 2 || ny < 2 || nz < 2 || (nz & 1) || nscales < 1) return -1;
   const size_t n3 = (size_t)nx * ny * nz;
   double* h = malloc(sizeof(double) * 6 * n3);
@@ -556,6 +557,13 @@ int or_collapse_times3(const double* delta_half_ri, int nx, int ny, int nz, doub
     int rc = or_hessian3(delta_half_ri, nx, ny, nz, box, radii[s], h, NULL);
     if (!rc && vmax) rc = or_displacement3(delta_half_ri, nx, ny, nz, box, radii[s], psi);
     if (rc) { free(h); free(psi); return rc; }
+    if (hrms) {
+      /* rms over the grid of the Frobenius norm of the tensor at this radius */
+      double acc = 0.0;
+      for (size_t q = 0; q < n3; ++q)
+        for (int c = 0; c < 6; ++c) acc += (c < 3 ? 1.0 : 2.0) * h[c * n3 + q] * h[c * n3 + q];
+      hrms[s] = sqrt(acc / (double)n3);
+    }
 #pragma omp parallel for schedule(static)
     for (long long q = 0; q < (long long)n3; ++q) {
       double h6[6];
@@ -586,7 +594,7 @@ int or_collapse_times(const double* delta_half_ri, int n, double box, int nscale
                       double* f_all, double* f2, int* idx2, double* slope, double* vmax) {
   if (n < 2 || (n & 1) || nscales < 1) return -1;
   return or_collapse_times3(delta_half_ri, n, n, n, box, nscales, radii, correction, fmax, idx, f_all, f2,
-                            idx2, slope, vmax);
+                            idx2, slope, vmax, NULL);
 }
 
 int or_collapse_times_sampled(const double* delta_half_ri, int n, double box, int nscales,
@@ -633,5 +641,45 @@ void or_collapse_from_hessians(const double* h6s, int nscales, int npts, int cor
     }
     fmax[p] = best; idx[p] = bi;
     if (f2) { f2[p] = second; idx2[p] = si; }
+  }
+}
+
+/* ------------------------------------------------------- conditioning -- */
+
+/* How far F can move when the Hessian carries errors of the size single
+ * precision leaves in it.  For each radius s and point p (h6s is
+ * [nscales][npts][6]): the eigenvalues lambda of the point's tensor, a
+ * half-width d = u (hscale[s] + max_i |lambda_i|), and F evaluated at the 27
+ * eigenvalue triples lambda + d (a, b, c), a, b, c in {-1, 0, 1} (each triple
+ * re-sorted descending); lo and hi ([nscales][npts]) receive the smallest and
+ * largest of those F.  hscale[s] is the grid's rms tensor norm at that radius
+ * (transform errors scale with the field, not with the local value); the
+ * local term covers the eigenvalue solve.  Where F is smooth the interval is
+ * about d |grad F| wide; where the first crossing is near-tangent (F jumps
+ * under a small change of lambda) it spans the jump.  u = 0 gives
+ * lo = hi = or_collapse_F. */
+void or_collapse_interval(const double* h6s, const double* hscale, int nscales, int npts, int correction,
+                          double u, double* lo, double* hi) {
+#pragma omp parallel for schedule(static)
+  for (long long i = 0; i < (long long)nscales * npts; ++i) {
+    const int s = (int)(i / npts);
+    double lam[3];
+    or_eig3(h6s + (size_t)i * 6, lam);
+    double local = fmax(fabs(lam[0]), fabs(lam[2]));
+    double d = u * (hscale[s] + local);
+    double fmin = INFINITY, fmaxv = -INFINITY;
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b)
+        for (int c = -1; c <= 1; ++c) {
+          double l[3] = {lam[0] + a * d, lam[1] + b * d, lam[2] + c * d};
+          for (int x = 0; x < 3; ++x)
+            for (int y = x + 1; y < 3; ++y)
+              if (l[y] > l[x]) { double t = l[x]; l[x] = l[y]; l[y] = t; }
+          double F = or_collapse_F(l, correction);
+          if (F < fmin) fmin = F;
+          if (F > fmaxv) fmaxv = F;
+        }
+    lo[i] = fmin;
+    hi[i] = fmaxv;
   }
 }

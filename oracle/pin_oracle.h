@@ -28,7 +28,8 @@ int or_displacement3(const double* delta_half_ri, int nx, int ny, int nz, double
                      double* out3);
 int or_collapse_times3(const double* delta_half_ri, int nx, int ny, int nz, double box, int nscales,
                        const double* radii, int correction, double* fmax, int* idx,
-                       double* f_all, double* f2, int* idx2, double* slope, double* vmax);
+                       double* f_all, double* f2, int* idx2, double* slope, double* vmax,
+                       double* hrms);
 void or_eig3(const double* h6, double* lam);
 void or_axis_coeffs(const double* lam, int i, double* c);
 double or_first_root(const double* c);
@@ -44,6 +45,8 @@ int or_collapse_times_sampled(const double* delta_half_ri, int n, double box, in
                               const double* radii, int correction, int npts,
                               const long long* q_list, double* fmax, int* idx, double* f2,
                               int* idx2);
+void or_collapse_interval(const double* h6s, const double* hscale, int nscales, int npts, int correction,
+                          double u, double* lo, double* hi);
 void or_collapse_from_hessians(const double* h6s, int nscales, int npts, int correction,
                                double* fmax, int* idx, double* f2, int* idx2);
 

@@ -6,12 +6,22 @@ Scale index: equal on >= 99.99 % of particles; every other particle must be a
 near-tie (the oracle's F at the GPU's index is within the F tolerance of its
 own maximum).
 
-A particle that misses either rule is accepted only if the oracle, run on the
-GPU's own FP32 Hessians of that particle (all radii), reproduces the GPU's
-F_max within tolerance: the discrepancy then comes from the FP32 rounding of
-the transforms feeding an ill-conditioned collapse (a near-tangent crossing,
-where F jumps), not from the kernel's eigenvalue or root arithmetic.  Such
-particles must stay below 1e-4 of the grid (and are reported).
+Conditioning (a reading of the tolerance for an FP32 path): F is not a
+continuous function of the Hessian everywhere.  Where the first axis crossing
+is near-tangent, or the largest eigenvalue is a tiny fraction of the field's
+scale (F then goes as its cube root), a change of the Hessian at the size of
+single-precision rounding moves F by more than the tolerance.  So a particle
+that misses the rule above passes only if the ORACLE, on its own FP64
+Hessians of that particle at every radius (the direct sum over modes), finds
+it ill-conditioned and the GPU's result inside the oracle's range:
+  - per radius s, the range [lo_s, hi_s] of F over eigenvalue errors of
+    half-width U_FP32 (hrms_s + max |lambda|) (oracle.collapse_interval);
+  - F_gpu within [max_s lo_s - tol, max_s hi_s + tol] (the range of F_max);
+  - the GPU's radius index I able to hold the maximum: F_gpu within
+    [lo_I - tol, hi_I + tol] (or I = -1, F_gpu = 0, and max_s lo_s <= tol).
+Such conditioned particles must stay at or below 1e-4 of the grid (at least
+one is allowed); every parity test prints how many there were.  Nothing of
+the GPU's intermediate values enters the rule.
 """
 import numpy as np
 
@@ -19,6 +29,12 @@ from paper_1305_1505_gb300 import ic
 
 REL = 1e-4
 ABS_FRAC = 1e-4
+# Half-width of the eigenvalue errors the conditioning range allows, relative
+# to the field's rms tensor norm plus the local one: about 64 units of FP32
+# rounding (2^-24), above the measured transform error (a few 1e-7 of the rms
+# at 768 points) and the trigonometric eigenvalue error (about 1e-6 of the
+# matrix norm).
+U_FP32 = 4e-6
 
 
 def inputs(n, box, seed):
@@ -61,35 +77,49 @@ def classify(F_gpu, idx_gpu, F_or, idx_or, f2=None, idx2=None, f_all=None):
     return bad, rep
 
 
-def explain_with_gpu_hessians(plan, bad_q, F_gpu, nscales, rms, correction=1):
-    """Oracle collapse on the GPU's FP32 Hessians of the given particles."""
-    import torch
+def within_conditioning(F_gpu, I_gpu, lo, hi, tol):
+    """The conditioning rule for particles p (columns of lo/hi, (S, npts)):
+    True where the GPU's F_max and radius index lie inside the oracle's
+    range."""
+    F_gpu = np.asarray(F_gpu, dtype=np.float64)
+    I_gpu = np.asarray(I_gpu)
+    Lo, Hi = lo.max(axis=0), hi.max(axis=0)
+    ok = (F_gpu >= Lo - tol) & (F_gpu <= Hi + tol)
+    cols = np.arange(F_gpu.size)
+    Ic = np.clip(I_gpu, 0, lo.shape[0] - 1)
+    at_i = (F_gpu >= lo[Ic, cols] - tol) & (F_gpu <= hi[Ic, cols] + tol)
+    never = (I_gpu == -1) & (F_gpu == 0.0) & (Lo <= tol)
+    return ok & np.where(I_gpu >= 0, at_i, never)
+
+
+def conditioned(q_bad, F_gpu, I_gpu, d64, box, radii, hrms, correction, tol):
+    """Oracle-side conditioning of the particles q_bad: (ok mask, lo, hi)."""
     import oracle
-    q = torch.as_tensor(np.asarray(bad_q, dtype=np.int64), device="cuda")
-    hs = np.empty((nscales, len(bad_q), 6))
-    for s in range(nscales):
-        h = plan.hessian(s).reshape(6, -1)
-        hs[s] = h[:, q].T.double().cpu().numpy()
-    out = oracle.collapse_from_hessians(hs, correction)
-    F_gpu = np.asarray(F_gpu, dtype=np.float64).ravel()[bad_q]
-    ok = np.abs(F_gpu - out["fmax"]) <= tolerance(out["fmax"], rms)
-    return ok, out
+    h = oracle.hessians_at(d64, box, radii, q_bad)
+    lo, hi = oracle.collapse_interval(h, hrms, U_FP32, correction)
+    return within_conditioning(F_gpu, I_gpu, lo, hi, tol), lo, hi
 
 
-def assert_parity(plan, F, I, orc, nscales, correction=1, label=""):
-    """The whole rule: every particle within the F tolerance with an equal
-    or near-tie index, or explained by the oracle on the GPU's own FP32
-    Hessians (FP32 rounding of the transforms feeding an ill-conditioned
-    collapse), such particles below 1e-4 of the grid, and the index equal on
-    >= 99.99 % of particles."""
+def assert_parity(F, I, orc, d64, box, radii, correction=1, label=""):
+    """The whole rule: every particle within the F tolerance with an equal or
+    near-tie index, or (at most 1e-4 of the grid) ill-conditioned by the
+    oracle's own measure with the GPU's result inside the oracle's range; the
+    index equal on >= 99.99 % of particles.  d64, box, radii and correction
+    are the oracle's inputs of this run; orc its collapse_times result."""
     F = np.asarray(F).ravel()
     I = np.asarray(I).ravel()
     bad, rep = classify(F, I, orc["fmax"], orc["idx"], orc.get("f2"), orc.get("idx2"), orc.get("f_all"))
-    print("parity %s:" % label, rep, plan.stats())
     bq = np.nonzero(bad)[0]
+    rep["conditioned"] = int(bq.size)
+    print("parity %s:" % label, rep)
     if bq.size:
-        ok, _ = explain_with_gpu_hessians(plan, bq, F, nscales, rep["rms"], correction)
-        assert ok.all(), "unexplained mismatches at %s" % bq[~ok][:10]
+        tol = tolerance(orc["fmax"][bq], rep["rms"])
+        ok, lo, hi = conditioned(bq, F[bq], I[bq], d64, box, radii, orc["hrms"], correction, tol)
+        for j, q in enumerate(bq):
+            print("  conditioned q=%d: gpu F=%.7g idx=%d, oracle F=%.7g idx=%d, range [%.7g, %.7g] %s"
+                  % (q, F[q], I[q], orc["fmax"][q], orc["idx"][q], lo[:, j].max(), hi[:, j].max(),
+                     "inside" if ok[j] else "OUTSIDE"))
+        assert ok.all(), "mismatches outside the oracle's conditioning range at %s" % bq[~ok][:10]
         assert bq.size <= max(1, 1e-4 * F.size), "too many ill-conditioned particles: %d" % bq.size
     assert rep["idx_mismatch"] <= max(1, 1e-4 * F.size), rep
     return rep

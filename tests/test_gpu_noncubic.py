@@ -50,7 +50,7 @@ def test_non_cubic_collapse_hessian_displacement(shape):
     assert tuple(F.shape) == shape
     orc = oracle.collapse_times(d64, box, radii, keep_all=True, velocities=True)
     Fh, Ih = F.cpu().numpy().ravel(), I.cpu().numpy().ravel()
-    parity.assert_parity(plan, Fh, Ih, orc, len(radii), label=str(shape))
+    parity.assert_parity(Fh, Ih, orc, d64, box, radii, label=str(shape))
     # v_max: the displacement smoothed on R_max, where the indices agree
     v = plan.velocities().double().cpu().numpy().reshape(3, -1)
     same = I.cpu().numpy().ravel() == orc["idx"]

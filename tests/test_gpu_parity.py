@@ -3,7 +3,8 @@
 Grids span several tiles and a ragged tail of every pass (8^3 and 16^3 run
 lines in a single thread, 48^3 and 96^3 exercise the radix-3 transforms,
 64^3 is the 64^3 / 100 Mpc/h / 20-radius workload, 128^3 the 4 Mpc/h-cell,
-40-radius stand-in of the 768^3 run)."""
+40-radius stand-in of the 768^3 run, 256^3 the 512 Mpc/h / 30-radius
+workload, against the full oracle)."""
 import numpy as np
 import pytest
 
@@ -22,6 +23,7 @@ CASES = [
     (64, 100.0, 1, 20, 100.0 / 64, 15.0),
     (96, 192.0, 15, 12, 2.0, 40.0),
     (128, 512.0, 3, 40, 4.0, 120.0),
+    (256, 512.0, 2, 30, 2.0, 40.0),
 ]
 
 
@@ -39,19 +41,15 @@ def _run(n, box, seed, radii, correction=1, keep_all=None):
     plan.sync()
     keep = n <= 64 if keep_all is None else keep_all
     orc = oracle.collapse_times(d64, box, radii, correction=correction, keep_all=keep)
-    return plan, F.cpu().numpy().ravel(), I.cpu().numpy().ravel(), orc
-
-
-def _assert_parity(plan, F, I, orc, nscales, correction=1):
-    parity.assert_parity(plan, F, I, orc, nscales, correction)
+    return plan, F.cpu().numpy().ravel(), I.cpu().numpy().ravel(), orc, d64
 
 
 @pytest.mark.parametrize("case", CASES, ids=[str(c[0]) for c in CASES])
 def test_collapse_times_parity(case):
     n, box, seed, S, rmin, rmax = case
     radii = ic.log_radii(rmin, rmax, S)
-    plan, F, I, orc = _run(n, box, seed, radii)
-    _assert_parity(plan, F, I, orc, S)
+    plan, F, I, orc, d64 = _run(n, box, seed, radii)
+    parity.assert_parity(F, I, orc, d64, box, radii, label="%d^3" % n)
     # at least some particles collapse and some do not: the test is not vacuous
     assert (I >= 0).mean() > 0.05
 
@@ -59,8 +57,8 @@ def test_collapse_times_parity(case):
 def test_uncorrected_mode_parity():
     n, box, S = 32, 64.0, 8
     radii = ic.log_radii(2.0, 16.0, S)
-    plan, F, I, orc = _run(n, box, 21, radii, correction=0)
-    _assert_parity(plan, F, I, orc, S, correction=0)
+    plan, F, I, orc, d64 = _run(n, box, 21, radii, correction=0)
+    parity.assert_parity(F, I, orc, d64, box, radii, correction=0, label="uncorrected")
 
 
 @pytest.mark.parametrize("n,box,radius", [(16, 64.0, 3.0), (48, 96.0, 4.0), (64, 100.0, 1.5625),

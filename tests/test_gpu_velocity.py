@@ -22,7 +22,7 @@ def test_vmax_parity(n, box, S):
     v = plan.velocities().cpu().numpy().reshape(3, -1).astype(np.float64)
     F, I = F.cpu().numpy().ravel(), I.cpu().numpy().ravel()
     orc = oracle.collapse_times(d64, box, radii, velocities=True, keep_all=n <= 48)
-    parity.assert_parity(plan, F, I, orc, S, label="v_max %d^3" % n)
+    parity.assert_parity(F, I, orc, d64, box, radii, label="v_max %d^3" % n)
     same = I == orc["idx"]
     vo = orc["vmax"]
     for c in range(3):

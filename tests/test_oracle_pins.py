@@ -710,3 +710,78 @@ def test_sigma2_flat_spectrum_closed_form(shape, radius):
     ref = A / (L[0] * L[1] * L[2]) * (theta[0] * theta[1] * theta[2] - 1.0)
     got = oracle.sigma2(shape, box, radius, power=lambda k: np.full(k.shape, A))
     assert abs(got - ref) <= 1e-13 * ref
+
+
+# ------------------------------------------------- conditioning interval --
+
+def _rotated(lam, seed):
+    """h6 of R diag(lam) R^T for a random rotation R."""
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    a = q @ np.diag(lam) @ q.T
+    return np.array([a[0, 0], a[1, 1], a[2, 2], a[0, 1], a[0, 2], a[1, 2]])
+
+
+def test_collapse_interval_zero_width_is_collapse_F():
+    rng = np.random.default_rng(7)
+    lams = np.sort(rng.normal(scale=0.8, size=(20, 3)), axis=1)[:, ::-1]
+    h = np.stack([_rotated(l, i) for i, l in enumerate(lams)])[None]
+    for corr in (0, 1):
+        lo, hi = oracle.collapse_interval(h, [0.5], 0.0, corr)
+        ref = np.array([oracle.collapse_F(l, corr) for l in lams])
+        assert np.allclose(lo[0], ref, rtol=1e-12, atol=1e-13)
+        assert np.allclose(hi[0], ref, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("a", [0.3, 0.7, 1.2])
+def test_collapse_interval_contains_the_perturbed_spheres(a):
+    """A sphere lambda = (a, a, a) with half-width d = u (hscale + a): the
+    corners (a +- d)(1, 1, 1) are spheres, F = 3 (a +- d) / delta_c exactly
+    (corrected mode), so the interval must reach both."""
+    u, hs = 1e-3, 0.2
+    d = u * (hs + a)
+    lo, hi = oracle.collapse_interval(np.array([[[a, a, a, 0.0, 0.0, 0.0]]]), [hs], u, 1)
+    dc = oracle.delta_c()
+    assert hi[0, 0] >= 3 * (a + d) / dc - 1e-12
+    assert lo[0, 0] <= 3 * (a - d) / dc + 1e-12
+    # smooth there: the interval stays of the order of d |grad F|
+    assert hi[0, 0] - lo[0, 0] < 20 * d
+
+
+def _tangent_lambda1(l2, l3):
+    """lambda1 at which the axis-0 displacement a(D) has a local maximum equal
+    to 1 (a tangent first crossing), by bisection on the maximum's value; the
+    coefficients come from the oracle and the maximum from numpy's roots."""
+    def peak(t):
+        c1, c2, c3 = oracle.axis_coeffs(np.array([t, l2, l3]), 0)
+        r = np.roots([3 * c3, 2 * c2, c1])
+        r = np.sort(r[np.isreal(r)].real)
+        r = r[r > 0]
+        return (c1 * r[0] + c2 * r[0] ** 2 + c3 * r[0] ** 3) if r.size else np.inf
+    lo, hi = l2, 0.32
+    assert peak(lo) < 1 < peak(hi)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if peak(mid) < 1:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_collapse_interval_spans_a_tangent_jump():
+    """At a tangent first crossing F jumps: just above the tangent eigenvalue
+    the axis collapses at the tangent point, just below only much later.  A
+    tiny half-width must give an interval as wide as that jump; the same
+    half-width away from the tangency gives an interval of width ~d."""
+    l2, l3 = 0.2, -0.5
+    t = _tangent_lambda1(l2, l3)
+    above = oracle.collapse_F(np.array([t * (1 + 1e-7), l2, l3]), 0)
+    below = oracle.collapse_F(np.array([t * (1 - 1e-7), l2, l3]), 0)
+    jump = above - below
+    assert jump > 0.05 * above  # the jump is real
+    u = 1e-6
+    lo, hi = oracle.collapse_interval(np.array([[[t, l2, l3, 0, 0, 0]]]), [0.0], u, 0)
+    assert hi[0, 0] - lo[0, 0] >= 0.9 * jump
+    lo2, hi2 = oracle.collapse_interval(np.array([[[0.8 * t, l2, l3, 0, 0, 0]]]), [0.0], u, 0)
+    assert hi2[0, 0] - lo2[0, 0] < 1e-3 * jump
