@@ -245,20 +245,36 @@ pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y)
  * Inputs and outputs are device pointers owned by the caller: delta_k is the
  * half-spectrum (dtype PIN_C64 or PIN_C128, layout as for pin_set_ic), radii
  * the nscales radii in host memory, F_max and scale_idx the N^3 outputs, with
- * the meaning of pin_collapse_times.  Work is enqueued on `stream` (NULL: the
- * legacy default stream) and the call returns without waiting.
+ * the meaning of pin_collapse_times and the same values bit for bit (the same
+ * tables, kernels and FP64 redo capacity run).  Work is enqueued on `stream`
+ * (NULL: the legacy default stream) and the call returns without waiting for
+ * the kernels; the per-radius tables are copied in from a static host staging
+ * area on that stream, a copy from pageable memory that may wait for the
+ * stream's earlier work.
  *
- * The workspace is one static device array of about 11.3 MB, sized for
+ * The workspace is one static device array of 13.9 MB, sized for
  * n <= PIN_NOALLOC_MAX_N, which every GPU that loads this library holds until
  * the process exits.  Larger n returns PIN_EINVAL, as do the argument errors
  * of pin_plan.  The first call on a device sets that device up (looks up the
  * array's address, loads constant tables, sets kernel limits); make it before
  * any stream capture.  All calls share the array and it keeps the previous
- * call's contents (each call rewrites everything it reads); calls whose work
- * overlaps on the GPU race on it, so the caller must serialise them. */
+ * call's contents (each call rewrites everything it reads and clears its
+ * counters and error word); calls whose work overlaps on the GPU race on it,
+ * so the caller must serialise them. */
 pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype, int n, double box,
                                       int nscales, const double* radii, int correction,
                                       float* F_max, int32_t* scale_idx, void* stream);
+
+/* What the last pin_collapse_times_noalloc call on the current device
+ * recorded, read from the shared workspace without allocating; call it only
+ * after that call's stream has completed (otherwise the values are those of
+ * work still in flight).  *wait_failed = 1 when a transfer wait of the x or y
+ * pass gave up (its bounded wait ran out; the outputs are then invalid and the
+ * call returns PIN_ECUDA).  counters3[0] and [1]: particle-scales redone in
+ * FP64 for a near-degenerate eigenvalue pair and for a near-tangent root;
+ * counters3[2]: of those, kept at FP32 because the redo queue of a radius was
+ * full (as in pin_stats).  PIN_ESTATE if no call has run on this device. */
+pin_status pin_noalloc_status(int* wait_failed, uint64_t* counters3);
 
 const char* pin_strerror(pin_status s);
 const char* pin_last_error(pin_plan_t p);

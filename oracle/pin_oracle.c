@@ -42,7 +42,10 @@
  *       eps = (lambda1 - lambda3) / |mu1|,
  *     delta_c = (3/20)(12 pi)^(2/3) and x3 the root of
  *     x/3 + x^2/21 + 23 x^3 / 1701 = 1, so that a sphere gives exactly
- *     F = delta / delta_c (Sec. 2.1.1, spherical limit);
+ *     F = delta / delta_c (Sec. 2.1.1, spherical limit).  Parity unpinned:
+ *     correction width -- the tests fix the weight only at its ends (1 for a
+ *     sphere, ~0 for one axis); the width 0.1 and the exponent in between are
+ *     a project constant the paper does not fix;
  *   - F_max starts at 0 with index -1; an update needs F > F_max strictly.
  *
  * Parity against the real PINOCCHIO code is unpinned (no code or data of it

@@ -154,6 +154,22 @@ cudaError_t launch_roots(const ArgsZ& a, cudaStream_t st);
 cudaError_t launch_redo(const ArgsZ& a, cudaStream_t st);
 cudaError_t upload_constant_twiddles();  // per device
 
+// Host helpers shared by the plan path (pin.cu) and the allocation-free entry
+// point (noalloc.cu), so that both build identical tables:
+//   padded_half      kz stride of the padded half-spectra (n/2 + 1 rounded up
+//                    to a multiple of 4 complex values)
+//   correction_dcorr 1/delta_c - 1/x3 of the quasi-spherical correction
+//   fill_mult        {W, kW, k^2 W} / n of one axis at one radius ([3][n])
+//   fill_twiddles    the line transform's twiddles of one axis
+//   launch_load_phi0 Phi0 = delta / k^2 into the padded layout (C64 or C128
+//                    input, batch realisations back to back)
+int padded_half(int n);
+double correction_dcorr();
+void fill_mult(float* out, int n, double box, double radius);
+void fill_twiddles(float2* t, int n, const PassShape& sh);
+cudaError_t launch_load_phi0(const void* src, int dtype, int nx, int ny, int nz, int nhp, double box, int batch,
+                             float2* phi0, cudaStream_t st);
+
 // Seeded initial conditions on the device (ic_gpu.cu): batch cubic
 // half-spectra [n][n][n/2+1] complex64 into out, realisation b keyed by
 // keys_dev[b] (the splitmix64 of its seed), amplitude amp of P(k).

@@ -76,6 +76,110 @@ struct pin_plan_s {
   double len(int nax) const { return nax == nx ? box : box * nax / nx; }
 };
 
+namespace pin {
+
+// kz stride of the half-spectra: n/2 + 1 modes rounded up to a multiple of 4
+// complex values, so that every row starts on a 32-byte sector (column tiles
+// of the y pass then write whole sectors; rows also meet the 16-byte TMA
+// stride rule)
+int padded_half(int n) { return (n / 2 + 1 + 3) & ~3; }
+
+static double delta_c_value() { return 3.0 / 20.0 * std::pow(12.0 * M_PI, 2.0 / 3.0); }
+
+// Uncorrected spherical collapse root: x/3 + x^2/21 + 23 x^3/1701 = 1, Newton
+// from x = 2 (the function is increasing and convex on x > 0).
+static double x3_value() {
+  double x = 2.0;
+  for (int i = 0; i < 60; ++i) {
+    double f = x / 3.0 + x * x / 21.0 + 23.0 * x * x * x / 1701.0 - 1.0;
+    double d = 1.0 / 3.0 + 2.0 * x / 21.0 + 69.0 * x * x / 1701.0;
+    double nx = x - f / d;
+    if (nx == x) break;
+    x = nx;
+  }
+  return x;
+}
+
+double correction_dcorr() { return 1.0 / delta_c_value() - 1.0 / x3_value(); }
+
+// Per-axis multipliers for one radius: {W, k W, k^2 W} / n with
+// W = exp(-k^2 R^2 / 2), k = 2 pi s / L; k W is zero on the Nyquist index.
+void fill_mult(float* out, int n, double box, double radius) {
+  for (int i = 0; i < n; ++i) {
+    const int s = i < n / 2 ? i : i - n;
+    const double k = 2.0 * M_PI * s / box;
+    const double w = std::exp(-0.5 * k * k * radius * radius) / n;
+    out[0 * n + i] = (float)w;
+    out[1 * n + i] = (i == n / 2) ? 0.0f : (float)(k * w);
+    out[2 * n + i] = (float)(k * k * w);
+  }
+}
+
+// Twiddles of one axis: w_n^{p k1} in [k1][p] order; for a three-level line
+// (P = P1 P2) then w_P^{p1 k2a} in [k2a][p1] order.
+void fill_twiddles(float2* t, int n, const PassShape& sh) {
+  const int E = sh.E, P = sh.P, P1 = sh.P1, P2 = sh.P2;
+  for (int k1 = 0; k1 < E; ++k1)
+    for (int q = 0; q < P; ++q) {
+      const double ang = 2.0 * M_PI * (double)((long)q * k1 % n) / n;
+      t[(size_t)k1 * P + q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  if (P2 > 1)
+    for (int k2a = 0; k2a < P2; ++k2a)
+      for (int q1 = 0; q1 < P1; ++q1) {
+        const double ang = 2.0 * M_PI * (double)(q1 * k2a % P) / P;
+        t[(size_t)n + k2a * P1 + q1] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+      }
+}
+
+// Phi0(k) = delta(k) / k^2 into the padded layout (pad modes and k = 0
+// zero).  Cubic cells: the side along x is `box`, L_y = box ny / nx,
+// L_z = box nz / nx.
+__global__ void k_load_phi0(const void* src, int dtype, int nx, int ny, int nz, int nhp, double box, int batch,
+                            float2* phi0) {
+  const int nh = nz / 2 + 1;
+  const size_t total = (size_t)nx * ny * nhp * batch;
+  const double kfx = 2.0 * M_PI / box, kfy = 2.0 * M_PI / (ny == nx ? box : box * ny / nx),
+               kfz = 2.0 * M_PI / (nz == nx ? box : box * nz / nx);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int iz = (int)(i % nhp);
+    const size_t r = i / nhp;
+    const int iy = (int)(r % ny), ix = (int)((r / ny) % nx);  // r runs over realisations too
+    float2 out = make_float2(0.f, 0.f);
+    if (iz < nh) {
+      const size_t j = r * nh + iz;
+      float2 d;
+      if (dtype == PIN_C64) {
+        d = reinterpret_cast<const float2*>(src)[j];
+      } else {
+        const double2 dd = reinterpret_cast<const double2*>(src)[j];
+        d = make_float2((float)dd.x, (float)dd.y);
+      }
+      const double sx = ix < nx / 2 ? ix : ix - nx, sy = iy < ny / 2 ? iy : iy - ny;
+      const double sz = iz < nz / 2 ? iz : -(nz / 2);
+      const double kx = kfx * sx, ky = kfy * sy, kz = kfz * sz;
+      const double k2 = kx * kx + ky * ky + kz * kz;
+      if (k2 > 0.0) {
+        const float inv = (float)(1.0 / k2);
+        out = make_float2(d.x * inv, d.y * inv);
+      }
+    }
+    phi0[i] = out;
+  }
+}
+
+cudaError_t launch_load_phi0(const void* src, int dtype, int nx, int ny, int nz, int nhp, double box, int batch,
+                             float2* phi0, cudaStream_t st) {
+  const size_t total = (size_t)nx * ny * nhp * batch;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, 152 * 64);
+  k_load_phi0<<<blocks, threads, 0, st>>>(src, dtype, nx, ny, nz, nhp, box, batch, phi0);
+  return cudaGetLastError();
+}
+
+}  // namespace pin
+
 namespace {
 
 std::mutex g_init_mu;
@@ -102,28 +206,6 @@ pin_status cuda_fail(pin_plan_t p, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                               \
     if (e_ != cudaSuccess) return cuda_fail((p), e_, #call); \
   } while (0)
-
-// kz stride of the half-spectra: n/2 + 1 modes rounded up to a multiple of 4
-// complex values, so that every row starts on a 32-byte sector (column tiles
-// of the y pass then write whole sectors; rows also meet the 16-byte TMA
-// stride rule)
-int padded_half(int n) { return (n / 2 + 1 + 3) & ~3; }
-
-double delta_c_value() { return 3.0 / 20.0 * std::pow(12.0 * M_PI, 2.0 / 3.0); }
-
-// Uncorrected spherical collapse root: x/3 + x^2/21 + 23 x^3/1701 = 1, Newton
-// from x = 2 (the function is increasing and convex on x > 0).
-double x3_value() {
-  double x = 2.0;
-  for (int i = 0; i < 60; ++i) {
-    double f = x / 3.0 + x * x / 21.0 + 23.0 * x * x * x / 1701.0 - 1.0;
-    double d = 1.0 / 3.0 + 2.0 * x / 21.0 + 69.0 * x * x / 1701.0;
-    double nx = x - f / d;
-    if (nx == x) break;
-    x = nx;
-  }
-  return x;
-}
 
 bool validate(const pin_plan_desc* d, std::string* why) {
   if (!d) { *why = "null descriptor"; return false; }
@@ -159,54 +241,6 @@ size_t footprint(int nx, int ny, int nz, int nscales, int batch, bool velocities
   return spec * 8 * (velocities ? 13 : 10) + n3 * 8 + (velocities ? n3 * 24 : 0) +
          (size_t)(nscales + 1) * 3 * (nx + ny + nz) * 4 + (size_t)(nx + ny + nz + 3 * 64) * 8 + 64 +
          (size_t)redo_capacity((size_t)nx * ny * nz, batch) * sizeof(RedoEntry) + 16 + sizeof(int);
-}
-
-// Per-axis multipliers for one radius: {W, k W, k^2 W} / n with
-// W = exp(-k^2 R^2 / 2), k = 2 pi s / L; k W is zero on the Nyquist index.
-void fill_mult(float* out, int n, double box, double radius) {
-  for (int i = 0; i < n; ++i) {
-    const int s = i < n / 2 ? i : i - n;
-    const double k = 2.0 * M_PI * s / box;
-    const double w = std::exp(-0.5 * k * k * radius * radius) / n;
-    out[0 * n + i] = (float)w;
-    out[1 * n + i] = (i == n / 2) ? 0.0f : (float)(k * w);
-    out[2 * n + i] = (float)(k * k * w);
-  }
-}
-
-// Cubic cells: the side along x is `box`, L_y = box ny / nx, L_z = box nz / nx.
-__global__ void k_load_phi0(const void* src, int dtype, int nx, int ny, int nz, int nhp, double box, int batch,
-                            float2* phi0) {
-  const int nh = nz / 2 + 1;
-  const size_t total = (size_t)nx * ny * nhp * batch;
-  const double kfx = 2.0 * M_PI / box, kfy = 2.0 * M_PI / (ny == nx ? box : box * ny / nx),
-               kfz = 2.0 * M_PI / (nz == nx ? box : box * nz / nx);
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int iz = (int)(i % nhp);
-    const size_t r = i / nhp;
-    const int iy = (int)(r % ny), ix = (int)((r / ny) % nx);  // r runs over realisations too
-    float2 out = make_float2(0.f, 0.f);
-    if (iz < nh) {
-      const size_t j = r * nh + iz;
-      float2 d;
-      if (dtype == PIN_C64) {
-        d = reinterpret_cast<const float2*>(src)[j];
-      } else {
-        const double2 dd = reinterpret_cast<const double2*>(src)[j];
-        d = make_float2((float)dd.x, (float)dd.y);
-      }
-      const double sx = ix < nx / 2 ? ix : ix - nx, sy = iy < ny / 2 ? iy : iy - ny;
-      const double sz = iz < nz / 2 ? iz : -(nz / 2);
-      const double kx = kfx * sx, ky = kfy * sy, kz = kfz * sz;
-      const double k2 = kx * kx + ky * ky + kz * kz;
-      if (k2 > 0.0) {
-        const float inv = (float)(1.0 / k2);
-        out = make_float2(d.x * inv, d.y * inv);
-      }
-    }
-    phi0[i] = out;
-  }
 }
 
 pin_status ensure_device_init(pin_plan_t p) {
@@ -530,7 +564,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   p->shape_z = pass_shape(p->nz);
   p->spec_elems = (size_t)p->nx * p->ny * p->nhp;
   p->field_elems = p->spec_elems * p->batch;
-  p->dcorr = 1.0 / delta_c_value() - 1.0 / x3_value();
+  p->dcorr = correction_dcorr();
   p->redo_cap = redo_capacity(p->n3(), p->batch);
   auto bail = [&](pin_status s) {
     release(p);
@@ -578,24 +612,8 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
     fill_mult(m + 3 * (size_t)p->nx, p->ny, p->len(p->ny), R);
     fill_mult(m + 3 * (size_t)(p->nx + p->ny), p->nz, p->len(p->nz), R);
   }
-  // per axis: twiddles w_N^{p k1} in [k1][p] order; for a three-level line
-  // (P = P1 P2) then w_P^{p1 k2a} in [k2a][p1] order
   std::vector<float2> tw(tw_elems);
-  for (int a = 0; a < 3; ++a) {
-    const int n = ns[a], E = shapes[a]->E, P = shapes[a]->P, P1 = shapes[a]->P1, P2 = shapes[a]->P2;
-    float2* t = tw.data() + p->tw_off[a];
-    for (int k1 = 0; k1 < E; ++k1)
-      for (int q = 0; q < P; ++q) {
-        const double ang = 2.0 * M_PI * (double)((long)q * k1 % n) / n;
-        t[(size_t)k1 * P + q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-      }
-    if (P2 > 1)
-      for (int k2a = 0; k2a < P2; ++k2a)
-        for (int q1 = 0; q1 < P1; ++q1) {
-          const double ang = 2.0 * M_PI * (double)(q1 * k2a % P) / P;
-          t[(size_t)n + k2a * P1 + q1] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-        }
-  }
+  for (int a = 0; a < 3; ++a) fill_twiddles(tw.data() + p->tw_off[a], ns[a], *shapes[a]);
   if (cudaMemcpy(p->mult, mult.data(), mult_elems * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(p->counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -623,12 +641,7 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
     PIN_CK(p, cudaMemcpyAsync(p->V, delta_k, bytes, cudaMemcpyHostToDevice, p->stream));
     src = p->V;
   }
-  const size_t total = p->field_elems;
-  const int threads = 256;
-  const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, 152 * 64);
-  k_load_phi0<<<blocks, threads, 0, p->stream>>>(src, dtype, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch,
-                                                  p->phi0);
-  PIN_CK(p, cudaGetLastError());
+  PIN_CK(p, launch_load_phi0(src, dtype, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch, p->phi0, p->stream));
   if (!on_device) PIN_CK(p, cudaStreamSynchronize(p->stream));
   p->ic_set = true;
   return PIN_OK;
@@ -651,12 +664,7 @@ pin_status pin_set_ic_seed(pin_plan_t p, uint64_t seed, const pin_spectrum* ps) 
   PIN_CK(p, cudaMemcpyAsync(keys_dev, keys.data(), keys.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
                             p->stream));
   PIN_CK(p, generate_ic(p->nx, p->box, keys_dev, p->batch, amp, ps->ns, ps->gamma, field, p->stream));
-  const size_t total = p->field_elems;
-  const int threads = 256;
-  const unsigned blocks = (unsigned)std::min<size_t>((total + threads - 1) / threads, 152 * 64);
-  k_load_phi0<<<blocks, threads, 0, p->stream>>>(field, PIN_C64, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch,
-                                                  p->phi0);
-  PIN_CK(p, cudaGetLastError());
+  PIN_CK(p, launch_load_phi0(field, PIN_C64, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch, p->phi0, p->stream));
   PIN_CK(p, cudaStreamSynchronize(p->stream));  // the host key vector goes out of scope
   p->ic_set = true;
   return PIN_OK;

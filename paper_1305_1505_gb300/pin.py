@@ -57,8 +57,8 @@ EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times"
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
            "pin_fragment_order", "pin_displacements_2lpt", "pin_set_ic_seed", "pin_tile_options",
-           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_strerror", "pin_last_error",
-           "pin_destroy")
+           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_noalloc_status", "pin_strerror",
+           "pin_last_error", "pin_destroy")
 
 _lib = None
 
@@ -117,6 +117,8 @@ def load(path=None):
                                              ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.c_int, P, P, P]
     L.pin_collapse_times_noalloc.restype = ctypes.c_int
+    L.pin_noalloc_status.argtypes = [IP, ctypes.POINTER(ctypes.c_uint64)]
+    L.pin_noalloc_status.restype = ctypes.c_int
     L.pin_strerror.argtypes = [ctypes.c_int]
     L.pin_strerror.restype = ctypes.c_char_p
     L.pin_last_error.argtypes = [P]
@@ -277,6 +279,19 @@ def pin_collapse_times_noalloc(delta_k_ptr, dtype, n, box, radii, correction, fm
                                            int(correction), ctypes.c_void_p(fmax_ptr),
                                            ctypes.c_void_p(idx_ptr), ctypes.c_void_p(stream_ptr))
     _check(st)
+
+
+def pin_noalloc_status():
+    """(status, wait_failed, [eig redo, root redo, queue overflow]) recorded by
+    the last pin_collapse_times_noalloc on the current device; call after its
+    stream has completed.  status is PIN_ECUDA when a bounded transfer wait
+    gave up (its outputs are then invalid)."""
+    w = ctypes.c_int(0)
+    c = (ctypes.c_uint64 * 3)()
+    st = load().pin_noalloc_status(ctypes.byref(w), c)
+    if st not in (PIN_OK, PIN_ECUDA):
+        _check(st)
+    return st, w.value, list(c)
 
 
 def pin_strerror(status):
