@@ -232,6 +232,26 @@ pin_status pin_get_tiles(pin_plan_t p, int* tc_x, int* tc_y);
 pin_status pin_set_tiles(pin_plan_t p, int tc_x, int tc_y);
 pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y);
 
+/* Failure paths, exercised without any GPU fault (the paper has no
+ * counterpart; its code is an MPI job).
+ *
+ * pin_set_wait_budget: the budget, in SM clock cycles, of each bounded wait of
+ * the x and y passes for a staged transfer (0: the default, 2^31 cycles, about
+ * a second).  A block whose wait runs out waits once more, with the default
+ * budget, for its transfers in flight, sets the plan's error word and returns;
+ * the next pin_sync (or host-output call) reports PIN_ECUDA once ("results are
+ * invalid") and clears the word, so the plan stays usable.  A tiny budget
+ * makes the waits run out on purpose.  Waits for the plan's stream; PIN_EINVAL
+ * for a negative budget.
+ *
+ * pin_debug_fail_alloc: host-side allocation-failure injection.  With
+ * nth >= 0, the device allocation with index nth (counted from 0 over the
+ * allocations of later pin_plan calls of the process) fails as if the device
+ * were out of memory; pin_plan then returns PIN_ENOMEM and frees what it had
+ * allocated.  The injection is used up by that failure; nth < 0 cancels it. */
+pin_status pin_set_wait_budget(pin_plan_t p, int64_t cycles);
+void pin_debug_fail_alloc(int nth);
+
 /* Largest grid side the no-allocation entry point below accepts. */
 #define PIN_NOALLOC_MAX_N 64
 

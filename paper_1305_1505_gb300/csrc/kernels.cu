@@ -24,8 +24,10 @@ namespace pin {
 // ------------------------------------------------------ TMA + mbarrier --
 // Source tiles of the x and y passes are brought into shared memory by the
 // tensor memory accelerator (cp.async.bulk.tensor), completing on an mbarrier.
-// Every wait is bounded (about a second of SM clocks); a block that gives up
-// reports through the pass's error word and returns.
+// Every wait is bounded (the pass's wait budget, by default 2^31 SM clocks,
+// about a second); a block that gives up waits once more, with the full
+// default budget, for its copies in flight, reports through the pass's error
+// word and returns.
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
@@ -49,19 +51,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+constexpr long long kWaitDefault = 1ll << 31;  // SM clocks, about a second at 2 GHz
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > budget) return false;
   return true;
 }
 // Block-uniform wait: true when the staged tile has landed for every thread.
-// On a timeout the block waits once more (bounded) for its copies in flight,
-// records the error and the caller returns.
-__device__ __forceinline__ bool stage_ready(uint32_t bar, uint32_t parity, int* err) {
-  const bool ok = mbar_wait_bounded(bar, parity);
+// budget <= 0 selects the default.  On a timeout the block waits once more,
+// with the default budget, for its copies in flight (so that no block exits
+// with a transfer pending), records the error and the caller returns.
+__device__ __forceinline__ bool stage_ready(uint32_t bar, uint32_t parity, int* err, long long budget) {
+  const bool ok = mbar_wait_bounded(bar, parity, budget > 0 ? budget : kWaitDefault);
   if (__syncthreads_and(ok)) return true;
-  mbar_wait_bounded(bar, parity);
+  mbar_wait_bounded(bar, parity, kWaitDefault);
   if (threadIdx.x == 0) atomicExch(err, 1);
   return false;
 }
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N, TC>::xy) k_pass_
   if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
   uint32_t parity = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (!stage_ready(bar, parity, a.err)) return;
+    if (!stage_ready(bar, parity, a.err, a.wait_cycles)) return;
     parity ^= 1;
     const int col = (tile % tpr) * TC + c;
     const bool ok = col < ncols;
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(TC* Shape<N>::P, MinBlocks<N, TC>::xy) k_pass_
 #pragma unroll 1
     for (int o = 0; o < nout; ++o) {
       if (o == 0 || s_sel[o] != s_sel[o - 1]) {
-        if (!stage_ready(bar, parity, a.err)) return;
+        if (!stage_ready(bar, parity, a.err, a.wait_cycles)) return;
         parity ^= 1;
       }
       const float* mt = s_m + s_ym[o] * N + p;

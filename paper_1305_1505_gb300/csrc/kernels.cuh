@@ -35,6 +35,7 @@ struct ArgsX {
   int nhp;
   int batch;          // realisations stacked back to back (same N, radii)
   int* err;           // set to 1 if a TMA wait gave up (bounded wait)
+  long long wait_cycles;  // budget of a TMA wait in SM clocks; <= 0: the default (2^31)
 };
 
 // y pass (lines of length ny): dst[f] = zfac[f](kz) * IDFT_y(mult[ym[f]] *
@@ -63,6 +64,7 @@ struct ArgsY {
   int nhp;
   int batch;
   int* err;
+  long long wait_cycles;
 };
 
 // A particle whose FP32 collapse is ill-conditioned, finished in FP64 by the

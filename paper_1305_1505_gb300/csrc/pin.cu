@@ -8,6 +8,7 @@
 // pin_collapse_times replays one CUDA graph holding the whole radius loop.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -52,6 +53,7 @@ struct pin_plan_s {
   unsigned* redo_count = nullptr;
   unsigned redo_cap = 0;
   int* err = nullptr;                      // set by a pass whose bounded TMA wait gave up
+  long long wait_cycles = 0;               // TMA wait budget of the x/y passes (0: default)
   CUtensorMap tm_x{}, tm_y{};              // Phi0 -> x pass, U[3] -> y pass
   int tc_x = 0, tc_y = 0;                  // tile widths (columns per block) of the x and y passes
   bool ic_set = false;
@@ -228,6 +230,22 @@ bool validate(const pin_plan_desc* d, std::string* why) {
   return true;
 }
 
+// Host-side allocation-failure injection (pin_debug_fail_alloc): when
+// g_fail_alloc >= 0, the device allocation of pin_plan with that index
+// (counted from 0 over later pin_plan calls) fails as out of memory.
+std::atomic<int> g_fail_alloc{-1};
+
+cudaError_t plan_alloc(void** ptr, size_t bytes) {
+  int k = g_fail_alloc.load();
+  while (k >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+      if (k == 0) return cudaErrorMemoryAllocation;
+      break;
+    }
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
 // FP64 redo queue capacity: 1/64 of the grid (observed rate ~2e-4), at least 64 Ki.
 unsigned redo_capacity(size_t n3, int batch) {
   return (unsigned)std::max<size_t>(65536, n3 * batch / 64);
@@ -311,6 +329,7 @@ ArgsX radius_args_x(pin_plan_t p, int ms) {
   ax.nhp = p->nhp;
   ax.batch = p->batch;
   ax.err = p->err;
+  ax.wait_cycles = p->wait_cycles;
   return ax;
 }
 
@@ -355,6 +374,7 @@ ArgsY radius_args_y(pin_plan_t p, int ms, bool collapse) {
   ay.nhp = p->nhp;
   ay.batch = p->batch;
   ay.err = p->err;
+  ay.wait_cycles = p->wait_cycles;
   return ay;
 }
 
@@ -456,11 +476,15 @@ pin_status check_plan(pin_plan_t p) {
 }
 
 // After the plan's stream has drained: a pass that gave up a bounded wait
-// left its error word set.
+// left its error word set.  The error is reported once, by the first check
+// after it happened, and the word is cleared for the plan's later work.
 pin_status check_error_word(pin_plan_t p) {
   int err = 0;
   PIN_CK(p, cudaMemcpy(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (err) return fail(p, PIN_ECUDA, "a transfer wait in the x/y pass timed out; results are invalid");
+  if (err) {
+    PIN_CK(p, cudaMemset(p->err, 0, sizeof(int)));
+    return fail(p, PIN_ECUDA, "a transfer wait in the x/y pass timed out; results are invalid");
+  }
   return PIN_OK;
 }
 
@@ -589,18 +613,15 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
     p->tw_off[a] = tw_elems;
     tw_elems += (size_t)ns[a] + (shapes[a]->P2 > 1 ? shapes[a]->P : 0);
   }
-  if (cudaMalloc(&p->phi0, p->field_elems * 8) != cudaSuccess ||
-      cudaMalloc(&p->U, 3 * p->field_elems * 8) != cudaSuccess ||
-      cudaMalloc(&p->V, (p->velocities ? 9 : 6) * p->field_elems * 8) != cudaSuccess ||
-      (p->velocities && (cudaMalloc(&p->psi, 3 * n3 * 4) != cudaSuccess ||
-                         cudaMalloc(&p->vstate, 3 * n3 * 4) != cudaSuccess)) ||
-      cudaMalloc(&p->fmax, n3 * 4) != cudaSuccess || cudaMalloc(&p->idx, n3 * 4) != cudaSuccess ||
-      cudaMalloc(&p->mult, mult_elems * 4) != cudaSuccess ||
-      cudaMalloc(&p->tw, tw_elems * 8) != cudaSuccess ||
-      cudaMalloc(&p->counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMalloc(&p->redo_list, (size_t)p->redo_cap * sizeof(RedoEntry)) != cudaSuccess ||
-      cudaMalloc(&p->redo_count, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) {
+  auto A = [](auto** ptr, size_t bytes) { return plan_alloc(reinterpret_cast<void**>(ptr), bytes); };
+  if (A(&p->phi0, p->field_elems * 8) != cudaSuccess || A(&p->U, 3 * p->field_elems * 8) != cudaSuccess ||
+      A(&p->V, (p->velocities ? 9 : 6) * p->field_elems * 8) != cudaSuccess ||
+      (p->velocities && (A(&p->psi, 3 * n3 * 4) != cudaSuccess || A(&p->vstate, 3 * n3 * 4) != cudaSuccess)) ||
+      A(&p->fmax, n3 * 4) != cudaSuccess || A(&p->idx, n3 * 4) != cudaSuccess ||
+      A(&p->mult, mult_elems * 4) != cudaSuccess || A(&p->tw, tw_elems * 8) != cudaSuccess ||
+      A(&p->counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+      A(&p->redo_list, (size_t)p->redo_cap * sizeof(RedoEntry)) != cudaSuccess ||
+      A(&p->redo_count, sizeof(unsigned)) != cudaSuccess || A(&p->err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return bail(PIN_ENOMEM);
   }
@@ -777,6 +798,7 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
   ax.nhp = p->nhp;
   ax.batch = 1;
   ax.err = p->err;
+  ax.wait_cycles = p->wait_cycles;
   e = launch_x(p->nx, p->tc_x, ax, p->stream);
   if (e != cudaSuccess) return e;
   // psi_x <- a1 (k_x), psi_y <- a0 (k_y), psi_z <- a0 (z: k_z); all times i
@@ -803,6 +825,7 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
   ay.nhp = p->nhp;
   ay.batch = 1;
   ay.err = p->err;
+  ay.wait_cycles = p->wait_cycles;
   e = launch_y(p->ny, p->tc_y, ay, p->stream);
   if (e != cudaSuccess) return e;
   ArgsZ az{};
@@ -876,6 +899,7 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
     ay.nhp = p->nhp;
     ay.batch = 1;
     ay.err = p->err;
+    ay.wait_cycles = p->wait_cycles;
     if (e == cudaSuccess) e = launch_y(ny, p->tc_y, ay, p->stream);
     ArgsX ax{};
     if (e == cudaSuccess) e = make_tmap_x(&ax.tm, spec(p, p->V, 1), nx, ny, p->nhp, 1, p->tc_x);
@@ -888,6 +912,7 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
     ax.nhp = p->nhp;
     ax.batch = 1;
     ax.err = p->err;
+    ax.wait_cycles = p->wait_cycles;
     if (e == cudaSuccess) e = launch_x(nx, p->tc_x, ax, p->stream);
     // 3) Phi2 = (3/7) S(k) / k^2 with S(k) = conj(T) (forward transform of real S), into U0
     if (e == cudaSuccess)
@@ -1051,6 +1076,19 @@ pin_status pin_pass_times(pin_plan_t p, double* ms4) {
     }
   return PIN_OK;
 }
+
+pin_status pin_set_wait_budget(pin_plan_t p, int64_t cycles) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (cycles < 0) return fail(p, PIN_EINVAL, "the wait budget must be >= 0 (0: the default)");
+  if ((long long)cycles == p->wait_cycles) return PIN_OK;
+  PIN_CK(p, cudaStreamSynchronize(p->stream));
+  p->wait_cycles = (long long)cycles;
+  drop_graph(p);  // the captured launches carry the old budget
+  return PIN_OK;
+}
+
+void pin_debug_fail_alloc(int nth) { g_fail_alloc.store(nth < 0 ? -1 : nth); }
 
 const char* pin_strerror(pin_status s) {
   switch (s) {

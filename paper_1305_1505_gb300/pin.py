@@ -57,8 +57,8 @@ EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times"
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
            "pin_fragment_order", "pin_displacements_2lpt", "pin_set_ic_seed", "pin_tile_options",
-           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_noalloc_status", "pin_strerror",
-           "pin_last_error", "pin_destroy")
+           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_noalloc_status", "pin_set_wait_budget",
+           "pin_debug_fail_alloc", "pin_strerror", "pin_last_error", "pin_destroy")
 
 _lib = None
 
@@ -119,6 +119,10 @@ def load(path=None):
     L.pin_collapse_times_noalloc.restype = ctypes.c_int
     L.pin_noalloc_status.argtypes = [IP, ctypes.POINTER(ctypes.c_uint64)]
     L.pin_noalloc_status.restype = ctypes.c_int
+    L.pin_set_wait_budget.argtypes = [P, ctypes.c_int64]
+    L.pin_set_wait_budget.restype = ctypes.c_int
+    L.pin_debug_fail_alloc.argtypes = [ctypes.c_int]
+    L.pin_debug_fail_alloc.restype = None
     L.pin_strerror.argtypes = [ctypes.c_int]
     L.pin_strerror.restype = ctypes.c_char_p
     L.pin_last_error.argtypes = [P]
@@ -292,6 +296,17 @@ def pin_noalloc_status():
     if st not in (PIN_OK, PIN_ECUDA):
         _check(st)
     return st, w.value, list(c)
+
+
+def pin_set_wait_budget(plan, cycles):
+    """Budget (SM clocks) of the x/y passes' bounded transfer waits; 0 restores
+    the default (2^31 clocks)."""
+    _check(load().pin_set_wait_budget(plan, int(cycles)), plan)
+
+
+def pin_debug_fail_alloc(nth):
+    """Makes the nth later device allocation of pin_plan fail (nth < 0: off)."""
+    load().pin_debug_fail_alloc(int(nth))
 
 
 def pin_strerror(status):
