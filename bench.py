@@ -238,22 +238,120 @@ def cpu_baseline(nscales_total):
                                                        nscales_total, s["every"], dt)}
 
 
+# The smaller single-realisation workloads: 64^3 / 100 Mpc/h, seed 1, 20 radii
+# 15 -> 1.5625 Mpc/h (one cell), and 256^3 / 512 Mpc/h, seed 2, 30 radii
+# 40 -> 2 Mpc/h (one cell); the oracle's sample for each (every radius of the
+# small one, every tenth radius of the larger one).
+CONFIGS = {
+    "config1": dict(n=64, box=100.0, seed=1, nscales=20, r_min=100.0 / 64, r_max=15.0, every=1),
+    "config2": dict(n=256, box=512.0, seed=2, nscales=30, r_min=2.0, r_max=40.0, every=10),
+}
+
+
+def measure_config(c, steps, warmup, tune=True):
+    """Device-timed collapse updates/s of one workload (delta(k) resident),
+    K steps back to back after the warm-up, and the whole step's
+    algorithmic bytes over its time."""
+    import torch
+    from paper_1305_1505_gb300 import ic, pin
+    n, S = c["n"], c["nscales"]
+    radii = ic.log_radii(c["r_min"], c["r_max"], S)
+    stream = torch.cuda.Stream()
+    plan = pin.Plan(n, c["box"], radii, stream=stream)
+    plan.set_ic(torch.from_numpy(ic.delta_k(n, c["box"], c["seed"], dtype=np.complex64)).cuda())
+    tiles = plan.autotune(reps=5) if tune else plan.tiles()
+    F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    I = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
+    for _ in range(warmup):
+        pin.pin_collapse_times(plan.handle, F.data_ptr(), I.data_ptr(), 1)
+    plan.sync()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(steps):
+        pin.pin_collapse_times(plan.handle, F.data_ptr(), I.data_ptr(), 1)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = evs[0].elapsed_time(evs[-1]) / steps
+    fused = pin.pin_kernels_per_call(plan.handle) == 4 * S
+    alg = algorithmic_bytes(n, fused, False)
+    peak, peak_kind = _peaks()
+    step_bytes = S * sum(alg.values())
+    out = {"workload": "%d^3 grid, box %.0f Mpc/h, seed %d, %d radii %.4g->%.4g Mpc/h (log)"
+                       % (n, c["box"], c["seed"], S, c["r_max"], c["r_min"]),
+           "value": n ** 3 * S / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "best_ms_per_step": min(evs[i].elapsed_time(evs[i + 1]) for i in range(steps)),
+           "tiles": {"x": tiles[0], "y": tiles[1]},
+           "step_alg_bytes_per_update": step_bytes / (n ** 3 * S),
+           "step_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak, "hbm_peak_kind": peak_kind,
+           "gpu_launches": int(steps * pin.pin_kernels_per_call(plan.handle))}
+    plan.close()
+    return out
+
+
+def config_cpu_baseline(c):
+    """The oracle, as it stands, on a sample of the workload's radii."""
+    import oracle
+    from paper_1305_1505_gb300 import ic
+    radii = ic.log_radii(c["r_min"], c["r_max"], c["nscales"])[::c["every"]]
+    d = ic.delta_k(c["n"], c["box"], c["seed"], dtype=np.complex64).astype(np.complex128)
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.collapse_times(d, c["box"], radii)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": c["n"] ** 3 * radii.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "the same %d^3 field, %d of the %d radii (every %dth), FP64, %.1f s"
+                      % (c["n"], radii.size, c["nscales"], c["every"], dt)}
+
+
+def run_config(args, name):
+    """One JSON line for a smaller workload, with the oracle beside it."""
+    c = CONFIGS[name]
+    m = measure_config(c, args.steps, args.warmup, tune=not args.no_tune)
+    import torch
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        pass
+    line = {"metric": "collapse updates/s (particles x scales) at %d^3" % c["n"], "value": m["value"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": m["ms_per_step"], "best_ms_per_step": m["best_ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": m["workload"], "tiles": m["tiles"]},
+            "roofline": {"bound": "hbm", "kernel": "whole radius loop", "unit": "GB/s",
+                         "achieved": m["step_hbm_frac"] * _peaks()[0], "peak": _peaks()[0],
+                         "peak_kind": m["hbm_peak_kind"], "frac": m["step_hbm_frac"], "traffic": None,
+                         "alg_bytes_per_update": m["step_alg_bytes_per_update"]},
+            "cpu_baseline": None if args.no_cpu else config_cpu_baseline(c),
+            "gpu_launches": m["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     w = WORKLOAD
-    vals = []
+    vals, secs = [], []
     cb = None
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         cb = cpu_baseline(w["nscales"])
         if i >= args.warmup:
             vals.append(cb["value"])
+            secs.append(time.perf_counter() - t0)
     v = statistics.mean(vals)
+    # a step of the full 768^3 x 40 workload would take this long at the
+    # sampled rate; each timed step ran the bounded sample only
     ms = w["n"] ** 3 * w["nscales"] / v * 1e3
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "ms_per_step_extrapolated": True,
+            "sample_ms_per_step": 1e3 * statistics.mean(secs),
+            "extrapolation": "ms_per_step = 768^3 x 40 updates / the sampled updates/s; each step timed "
+                             "the oracle on the bounded sample named in cpu_baseline",
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(WORKLOAD),
             "cpu_baseline": cb,
@@ -291,11 +389,24 @@ def run_ours(args):
     radii = ic.log_radii(w["r_min"], w["r_max"], S)
     stream = torch.cuda.Stream()
     d32 = ic.delta_k(n, w["box"], w["seed"] + 1000 * rank if ws > 1 else w["seed"], dtype=np.complex64)
+    if not args.no_e2e:
+        # pinned host buffers of the end-to-end leg, allocated before the
+        # plan and reused by every step
+        hd = torch.from_numpy(d32).pin_memory()
+        hF = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+        hI = torch.empty((n, n, n), dtype=torch.int32).pin_memory()
     plan = pin.Plan(n, w["box"], radii, stream=stream, velocities=args.velocities)
     dk = torch.from_numpy(d32).cuda()
     plan.set_ic(dk)
     # x/y tile widths timed on this plan, outside the timed region
-    tiles = plan.tiles() if args.no_tune else plan.autotune(reps=5)
+    if args.schedule:
+        pin.pin_set_schedule(plan.handle, args.schedule)
+    if args.tiles:
+        tx, ty = (int(v) for v in args.tiles.split(","))
+        plan.set_tiles(tx, ty)
+        tiles = plan.tiles()
+    else:
+        tiles = plan.tiles() if args.no_tune else plan.autotune(reps=5)
     F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
     I = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
     pin.pin_profile(plan.handle, 1)
@@ -311,21 +422,24 @@ def run_ours(args):
         if ws > 1:
             dist.barrier()
 
-    pass_ms = np.zeros(4)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # K steps back to back on the plan's stream, no host synchronisation
+    # between them; an event between steps gives the best single step
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for i in range(args.steps):
             step()
-            pass_ms += np.array(pin.pin_pass_times(plan.handle))  # waits for the step
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize()
     barrier()
+    # per-pass device times of the last timed step (event records inside its
+    # graph, on the plan's stream), summed over its S radii
+    pass_ms = np.array(pin.pin_pass_times(plan.handle))
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     updates = n ** 3 * S
-    total_s, _ = replica_value(ev0.elapsed_time(ev1) / 1e3, updates * args.steps, ws, "cuda")
+    total_s, _ = replica_value(evs[0].elapsed_time(evs[-1]) / 1e3, updates * args.steps, ws, "cuda")
     ms = total_s * 1e3 / args.steps
     value = updates * ws / (ms / 1e3)
 
@@ -333,27 +447,38 @@ def run_ours(args):
     # F_max and scale index out, copies inside the timed region
     pin.pin_profile(plan.handle, 0)
     e2e_s = float("nan")
+    e2e_parts = None
     if not args.no_e2e:
-        hd = torch.from_numpy(d32).pin_memory()
-        hF = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
-        hI = torch.empty((n, n, n), dtype=torch.int32).pin_memory()
         e2e_steps = max(1, min(args.steps, 3))
         pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)
         pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)  # warm graph
         barrier()
+        t_ic, t_col = [], []
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)
-            pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)
+            ta = time.perf_counter()
+            pin.pin_set_ic(plan.handle, hd.data_ptr(), pin.PIN_C64, 0)  # H2D, Phi0, sync
+            tb = time.perf_counter()
+            pin.pin_collapse_times(plan.handle, hF.data_ptr(), hI.data_ptr(), 0)  # graph, D2H, sync
+            tc = time.perf_counter()
+            t_ic.append(tb - ta)
+            t_col.append(tc - tb)
         e2e_s = (time.perf_counter() - t0) / e2e_steps
+        ic_ms, col_ms = 1e3 * float(np.mean(t_ic)), 1e3 * float(np.mean(t_col))
+        d2h_ms = max(col_ms - ms, 1e-6)  # the graph itself takes ms (device-timed above)
+        e2e_parts = {"set_ic_ms": ic_ms, "collapse_host_out_ms": col_ms, "graph_ms": ms,
+                     "d2h_ms_est": d2h_ms, "h2d_gbs_incl_phi0": d32.nbytes / (ic_ms / 1e3) / 1e9,
+                     "d2h_gbs_est": 8 * n ** 3 / (d2h_ms / 1e3) / 1e9}
     barrier()
     if not args.no_e2e:
         e2e_s, _ = replica_value(e2e_s, updates, ws, "cuda")
     stats = plan.stats()
+    kernels_per_call = pin.pin_kernels_per_call(plan.handle)
+    pin_schedule = pin.pin_get_schedule(plan.handle)
 
     # roofline of the dominant pass (algorithmic bytes per launch, one launch per radius)
-    fused = pin.pin_kernels_per_call(plan.handle) == 4 * S
-    per_launch_ms = pass_ms / (args.steps * S)
+    fused = kernels_per_call == 4 * S
+    per_launch_ms = pass_ms / S
     alg = algorithmic_bytes(n, fused, bool(args.velocities))
     names = ["x", "y", "z", "roots"]
     if fused:
@@ -373,28 +498,37 @@ def run_ours(args):
                   "frac": step_bytes / (ms / 1e3) / 1e9 / peak}
     if ws > 1:
         dist.barrier()
+    plan.close()
+    configs = None
+    if rank == 0 and ws == 1 and not args.no_configs and not args.grid and not args.nscales:
+        # the smaller workloads, device-timed, after the main plan is gone
+        configs = {k: measure_config(c, max(3, args.steps), args.warmup, tune=not args.no_tune)
+                   for k, c in CONFIGS.items()}
     if rank == 0:
         clocks = clk.summary()
         cb = cpu_baseline(S) if ws == 1 and not args.no_cpu else None
         line = {
             "metric": METRIC if n == WORKLOAD["n"] else METRIC.replace("768^3", "%d^3" % n),
             "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "best_ms_per_step": min(step_ms),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(_config(w), velocities=bool(args.velocities),
-                           tiles={"x": tiles[0], "y": tiles[1], "tuned": not args.no_tune}),
+                           tiles={"x": tiles[0], "y": tiles[1], "tuned": not (args.no_tune or args.tiles)},
+                           schedule=pin_schedule),
             "roofline": dict(roofline(names[dom], per_launch_ms[dom], n, bool(args.velocities), fused,
                                       achieved, peak, peak_kind, clocks, passes), step=whole_step),
             "cpu_baseline": cb,
             "e2e": None if args.no_e2e else {"value": updates * ws / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": int(d32.nbytes), "d2h_bytes_per_step": int(8 * n ** 3)},
-            "gpu_launches": int(args.steps * pin.pin_kernels_per_call(plan.handle)),
+                    "h2d_bytes_per_step": int(d32.nbytes), "d2h_bytes_per_step": int(8 * n ** 3),
+                    "ms_per_step": e2e_s * 1e3, "parts": e2e_parts},
+            "gpu_launches": int(args.steps * kernels_per_call),
             "clocks": clocks,
             "fp64_redo": {"eig": stats["eig_fp64_redo"], "root": stats["root_fp64_redo"],
                           "particle_scales": int(stats["collapse_calls"]) * updates},
+            "configs": configs,
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
@@ -662,10 +796,18 @@ def main():
     ap.add_argument("--nscales", type=int, default=0, help="number of radii; default 40")
     ap.add_argument("--velocities", action="store_true",
                     help="also keep v_max (the displacement smoothed on R_max): 9 fields per radius")
-    ap.add_argument("--workload", default="paper", choices=["paper", "ensemble", "fragment", "2lpt"],
-                    help="paper: 768^3 x 40 (the metric); ensemble: 64 x 128^3 batched vs sequential; "
+    ap.add_argument("--workload", default="paper",
+                    choices=["paper", "config1", "config2", "ensemble", "fragment", "2lpt"],
+                    help="paper: 768^3 x 40 (the metric); config1: 64^3 x 20; config2: 256^3 x 30; "
+                         "ensemble: 64 x 128^3 batched vs sequential; "
                          "fragment: the fragmentation front end on the 768^3 F_max field; "
                          "2lpt: the second-order displacement of the 768^3 field")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="radius schedule (pin_set_schedule): 0 serial, 1 z(s) beside x(s+1), "
+                         "2 z(s) beside x and y of s+1")
+    ap.add_argument("--tiles", default="", help="force the x,y tile widths (e.g. 8,8) instead of tuning")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload: skip the smaller workloads measured after it")
     args = ap.parse_args()
     if args.workload == "ensemble":
         return run_ensemble(args)
@@ -673,6 +815,8 @@ def main():
         return run_fragment(args)
     if args.workload == "2lpt":
         return run_2lpt(args)
+    if args.workload in CONFIGS:
+        return run_config(args, args.workload)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

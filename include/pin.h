@@ -201,7 +201,9 @@ int pin_kernels_per_call(pin_plan_t p);
  * ms4[2] the z pass (c2r + eigenvalues; at N = 384 and 768 also the collapse
  * time and running max), ms4[3] the root pass (collapse time + running max, where it
  * is a kernel of its own) with the FP64 redo of the queued ill-conditioned
- * particles. */
+ * particles.  Each is measured on the stream its pass runs on; under an
+ * overlapped schedule (pin_set_schedule) the passes overlap, so the four sums
+ * exceed the call's time. */
 pin_status pin_profile(pin_plan_t p, int enable);
 pin_status pin_pass_times(pin_plan_t p, double* ms4);
 
@@ -231,6 +233,22 @@ pin_status pin_tile_options(int n, int* opts, int* count);
 pin_status pin_get_tiles(pin_plan_t p, int* tc_x, int* tc_y);
 pin_status pin_set_tiles(pin_plan_t p, int tc_x, int tc_y);
 pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y);
+
+/* Radius schedule of pin_collapse_times (the paper has no counterpart; its
+ * loop is sequential).  0 (default): the passes of each radius run in order on
+ * the plan's stream.  1: the z pass and FP64 redo of radius s run on a second,
+ * lower-priority stream while the x pass of radius s + 1 runs; the y pass of
+ * s + 1 waits for them.  2: the x and y passes of radius s + 1 both overlap the
+ * z pass of radius s, the y pass writing a second set of spectra (six more, nine
+ * with velocities: pin_footprint_bytes does not count them), and the y pass of
+ * s + 2 waits for the z pass of s.  Results are bit-identical in every
+ * schedule; only the time changes (the z pass is bound by instruction issue,
+ * the x/y passes by memory).  Needs a grid whose z pass computes the collapse
+ * times itself (nz = 384 or 768), else PIN_EINVAL.  Waits for the plan's
+ * stream; the next call re-captures its graph.  PIN_ENOMEM (plan unchanged)
+ * when the second set of spectra does not fit. */
+pin_status pin_set_schedule(pin_plan_t p, int schedule);
+int pin_get_schedule(pin_plan_t p);
 
 /* Failure paths, exercised without any GPU fault (the paper has no
  * counterpart; its code is an MPI job).

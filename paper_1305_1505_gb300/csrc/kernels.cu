@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "collapse.cuh"
+#include "collapse_x2.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
 
@@ -51,9 +52,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 constexpr long long kWaitDefault = 1ll << 31;  // SM clocks, about a second at 2 GHz
+// try_wait may suspend the thread for a while before it reports "not yet", so
+// budgets below kWaitPoll clocks poll with the non-blocking test_wait instead.
+constexpr long long kWaitPoll = 1ll << 16;
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget) {
   const long long t0 = clock64();
+  if (budget < kWaitPoll) {
+    while (!mbar_test_wait(bar, parity))
+      if (clock64() - t0 > budget) return false;
+    return true;
+  }
   while (!mbar_try_wait(bar, parity))
     if (clock64() - t0 > budget) return false;
   return true;
@@ -424,6 +443,108 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
         a.out[0][(size_t)gl * N + z] =
             h[0] * h[1] + h[0] * h[2] + h[1] * h[2] - h[3] * h[3] - h[4] * h[4] - h[5] * h[5];
       }
+    } else if constexpr (FUSE && PIN_Z_ILP % 2 == 0) {
+      // eigenvalues, collapse time and running maximum of PIN_Z_ILP particles
+      // per thread and iteration, held two by two in the lanes of packed
+      // pairs (NPR independent pairs, so that their dependency chains
+      // interleave)
+      constexpr int NPR = PIN_Z_ILP / 2;
+      const CollapseConsts<float> ccf{a.dcorr_f, a.correction};
+      for (int pt0 = tid; pt0 < kPts; pt0 += 2 * NPR * nthreads) {
+        int q[NPR][2], lz[NPR][2];
+        bool valid[NPR][2];
+        float fm[NPR][2];
+        float2 lam[NPR][3];
+#pragma unroll
+        for (int r = 0; r < NPR; ++r) {
+          float2 h[6];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int pt = pt0 + (2 * r + u) * nthreads;
+            const int l = pt / N, z = pt % N;
+            const int gl = blockIdx.x * LINES + l;
+            valid[r][u] = pt < kPts && gl < nlines;
+            q[r][u] = gl * N + z;  // < 2^31: checked at plan creation
+            lz[r][u] = (l * NF) * kFS + z;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+              const float v = valid[r][u] ? s_f[lz[r][u] + f * kFS] : 0.f;
+              if (u) h[f].y = v;
+              else h[f].x = v;
+            }
+          }
+          const float2 rabs = eig3_x2(h, lam[r]);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            fm[r][u] = valid[r][u] ? a.fmax[q[r][u]] : 0.f;
+            if (valid[r][u] && (u ? rabs.y : rabs.x) > 1.f - a.tau_eig) {
+              atomicAdd(a.counters + 0, 1ull);
+              const unsigned slot = atomicAdd(a.redo_count, 1u);
+              if (slot < a.redo_cap) {
+                RedoEntry e;
+                e.q = q[r][u];
+#pragma unroll
+                for (int f = 0; f < 6; ++f) e.h[f] = u ? h[f].y : h[f].x;
+                e.kind = 0;
+                a.redo_list[slot] = e;
+                if constexpr (NP == 5) {
+#pragma unroll
+                  for (int cpt = 0; cpt < 3; ++cpt)
+                    a.psi_out[cpt * total + q[r][u]] = s_f[lz[r][u] + (6 + cpt) * kFS];
+                }
+                valid[r][u] = false;  // the redo kernel updates this particle
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                  if (u) lam[r][k].y = 0.f;
+                  else lam[r][k].x = 0.f;
+                }
+              } else {
+                atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 eigenvalues
+              }
+            }
+          }
+        }
+        CollapseStateX2 csx[NPR];
+#pragma unroll
+        for (int r = 0; r < NPR; ++r) collapse_main_x2(lam[r], ccf, csx[r]);
+#pragma unroll
+        for (int r = 0; r < NPR; ++r)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            CollapseState<float> cs = lane_state(csx[r], u);
+            if (cs.need[0] || cs.need[1]) collapse_rare<float>(cs);
+            if (!valid[r][u]) continue;
+            const int qq = q[r][u];
+            const float F = cs.best + cs.corr;
+            if (cs.kappa < a.tau_root) {
+              atomicAdd(a.counters + 1, 1ull);
+              const unsigned slot = atomicAdd(a.redo_count, 1u);
+              if (slot < a.redo_cap) {
+                RedoEntry e;
+                e.q = qq;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) e.h[k] = u ? lam[r][k].y : lam[r][k].x;
+                e.h[3] = e.h[4] = e.h[5] = 0.f;
+                e.kind = 1;
+                a.redo_list[slot] = e;
+                if constexpr (NP == 5) {
+#pragma unroll
+                  for (int cpt = 0; cpt < 3; ++cpt) a.psi_out[cpt * total + qq] = s_f[lz[r][u] + (6 + cpt) * kFS];
+                }
+                continue;
+              }
+              atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
+            }
+            if (F > fm[r][u]) {
+              a.fmax[qq] = F;
+              a.idx[qq] = a.scale;
+              if constexpr (NP == 5) {
+#pragma unroll
+                for (int cpt = 0; cpt < 3; ++cpt) a.vstate[cpt * total + qq] = s_f[lz[r][u] + (6 + cpt) * kFS];
+              }
+            }
+          }
+      }
     } else if constexpr (FUSE) {
       // eigenvalues, collapse time and running maximum, PIN_Z_ILP particles
       // per thread and iteration
@@ -647,6 +768,63 @@ __global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
   const float* L2 = a.lam_out + 2 * (size_t)total;
   CollapseConsts<float> ccf{a.dcorr_f, a.correction};
   const int stride = gridDim.x * blockDim.x;
+  if constexpr (U == 2) {
+    // two particles per thread in the lanes of packed pairs
+    for (int q0 = blockIdx.x * blockDim.x + threadIdx.x; q0 < total; q0 += 2 * stride) {
+      float2 lam[3];
+      float fm[2];
+      bool valid[2];
+      int q[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        q[u] = q0 + u * stride;
+        const bool in = q[u] < total;
+        float l0 = in ? __ldg(L0 + q[u]) : 0.f, l1 = in ? __ldg(L1 + q[u]) : 0.f, l2 = in ? __ldg(L2 + q[u]) : 0.f;
+        fm[u] = in ? a.fmax[q[u]] : 0.f;
+        valid[u] = in && !isnan(l0);  // NaN: queued by the z pass
+        if (!valid[u]) l0 = l1 = l2 = 0.f;
+        if (u) {
+          lam[0].y = l0; lam[1].y = l1; lam[2].y = l2;
+        } else {
+          lam[0].x = l0; lam[1].x = l1; lam[2].x = l2;
+        }
+      }
+      CollapseStateX2 csx;
+      collapse_main_x2(lam, ccf, csx);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        CollapseState<float> cs = lane_state(csx, u);
+        if (cs.need[0] || cs.need[1]) collapse_rare<float>(cs);
+        if (!valid[u]) continue;
+        const float F = cs.best + cs.corr;
+        if (cs.kappa < a.tau_root) {
+          atomicAdd(a.counters + 1, 1ull);
+          const unsigned slot = atomicAdd(a.redo_count, 1u);
+          if (slot < a.redo_cap) {
+            RedoEntry e;
+            e.q = q[u];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) e.h[k] = u ? lam[k].y : lam[k].x;
+            e.h[3] = e.h[4] = e.h[5] = 0.f;
+            e.kind = 1;
+            a.redo_list[slot] = e;
+            continue;  // the redo kernel updates this particle
+          }
+          atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
+        }
+        if (F > fm[u]) {
+          a.fmax[q[u]] = F;
+          a.idx[q[u]] = a.scale;
+          if constexpr (VEL) {
+#pragma unroll
+            for (int cpt = 0; cpt < 3; ++cpt)
+              a.vstate[(size_t)cpt * total + q[u]] = a.psi_out[(size_t)cpt * total + q[u]];
+          }
+        }
+      }
+    }
+    return;
+  }
   for (int q0 = blockIdx.x * blockDim.x + threadIdx.x; q0 < total; q0 += U * stride) {
     float lam[U][3], fm[U];
     bool valid[U];

@@ -62,7 +62,14 @@ struct pin_plan_s {
   uint64_t calls = 0;
   double dcorr = 0.0;
   bool profile = false;             // graph carries per-pass event records
-  std::vector<cudaEvent_t> events;  // 5 per radius: before x, after x, y, z, roots+redo
+  std::vector<cudaEvent_t> events;  // 7 per radius: x begin/end, y begin/end, z begin/end, redo end
+  // radius schedule (pin_set_schedule): 0 serial; 1 the z pass and redo of
+  // radius s on a second stream while the x pass of s + 1 runs; 2 also the y
+  // pass of s + 1, into a second set of V spectra
+  int sched = 0;
+  cudaStream_t s_xy = nullptr, s_z = nullptr;  // high / low priority streams of the overlapped schedule
+  float2* V2 = nullptr;                        // second V buffer (schedule 2)
+  std::vector<cudaEvent_t> cap_ev;             // fork/join events of the overlapped capture
   std::string last_error;
   size_t tw_off[3] = {0, 0, 0};  // per-axis twiddle tables within tw (x, y, z)
   size_t n3() const { return (size_t)nx * ny * nz; }
@@ -301,6 +308,13 @@ void release(pin_plan_t p) {
   cudaFree(p->err);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   p->events.clear();
+  cudaFree(p->V2);
+  p->V2 = nullptr;
+  for (cudaEvent_t e : p->cap_ev) cudaEventDestroy(e);
+  p->cap_ev.clear();
+  if (p->s_xy) cudaStreamDestroy(p->s_xy);
+  if (p->s_z) cudaStreamDestroy(p->s_z);
+  p->s_xy = p->s_z = nullptr;
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   p->graph_exec = nullptr;
   p->graph = nullptr;
@@ -339,7 +353,8 @@ ArgsX radius_args_x(pin_plan_t p, int ms) {
 // With the velocities of a collapse call, the smoothed displacement
 // psi = i k W Phi0 shares the y transforms of xz (psi_x: z factor W), zz
 // (psi_z: z factor k W) and yz (psi_y: z factor W).
-ArgsY radius_args_y(pin_plan_t p, int ms, bool collapse) {
+ArgsY radius_args_y(pin_plan_t p, int ms, bool collapse, float2* vbuf = nullptr) {
+  if (!vbuf) vbuf = p->V;
   static const int vout[6] = {0, 3, 4, 1, 2, 5};
   static const int sel[6] = {2, 1, 1, 0, 0, 0};
   static const int ym[6] = {0, 1, 0, 2, 0, 1};
@@ -348,20 +363,20 @@ ArgsY radius_args_y(pin_plan_t p, int ms, bool collapse) {
   ay.tm = p->tm_y;
   for (int f = 0; f < 3; ++f) ay.src[f] = spec(p, p->U, f);
   for (int o = 0; o < 6; ++o) {
-    ay.dst[o] = spec(p, p->V, vout[o]);
+    ay.dst[o] = spec(p, vbuf, vout[o]);
     ay.sel[o] = sel[o];
     ay.ym[o] = ym[o];
     ay.zm[o] = zm[o];
     ay.muli[o] = 0;
   }
   if (p->velocities && collapse) {
-    ay.dst2[2] = spec(p, p->V, 6);
+    ay.dst2[2] = spec(p, vbuf, 6);
     ay.zm2[2] = 0;
     ay.muli2[2] = 1;
-    ay.dst2[4] = spec(p, p->V, 8);
+    ay.dst2[4] = spec(p, vbuf, 8);
     ay.zm2[4] = 1;
     ay.muli2[4] = 1;
-    ay.dst2[5] = spec(p, p->V, 7);
+    ay.dst2[5] = spec(p, vbuf, 7);
     ay.zm2[5] = 0;
     ay.muli2[5] = 1;
   }
@@ -378,30 +393,52 @@ ArgsY radius_args_y(pin_plan_t p, int ms, bool collapse) {
   return ay;
 }
 
+// Where the passes of one radius of the collapse loop run: the x and y passes
+// on xs, the z pass and the FP64 redo on zs, the y outputs in vbuf; the y pass
+// first waits for y_wait (if set), y_done is recorded after it (and zs waits
+// for it), z_done after the redo.  The serial schedule is xs = zs = the
+// plan's stream, vbuf = V, no events.
+struct RadiusSched {
+  cudaStream_t xs, zs;
+  float2* vbuf;
+  cudaEvent_t y_wait, y_done, z_done;
+};
+
 // Filter-and-transform passes of one radius (mult set `ms`), ending in the
 // collapse update (dump and source null), a dump of the six real components,
 // or the 2LPT source field S of every particle (source, batch 1).
-pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, float* source = nullptr) {
+pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, float* source = nullptr,
+                          const RadiusSched* sched = nullptr) {
   const bool collapse = dump == nullptr && source == nullptr;
+  const RadiusSched rs = sched ? *sched : RadiusSched{p->stream, p->stream, p->V, nullptr, nullptr, nullptr};
   const bool rec = p->profile && collapse && !p->events.empty();
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 0], p->stream, cudaEventRecordExternal));
+  auto mark = [&](int k, cudaStream_t st) {
+    return rec ? cudaEventRecordWithFlags(p->events[7 * scale + k], st, cudaEventRecordExternal) : cudaSuccess;
+  };
+  PIN_CK(p, mark(0, rs.xs));
   const ArgsX ax = radius_args_x(p, ms);
-  PIN_CK(p, launch_x(p->nx, p->tc_x, ax, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 1], p->stream, cudaEventRecordExternal));
+  PIN_CK(p, launch_x(p->nx, p->tc_x, ax, rs.xs));
+  PIN_CK(p, mark(1, rs.xs));
+  if (rs.y_wait) PIN_CK(p, cudaStreamWaitEvent(rs.xs, rs.y_wait, 0));
 
-  const ArgsY ay = radius_args_y(p, ms, collapse);
-  PIN_CK(p, launch_y(p->ny, p->tc_y, ay, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 2], p->stream, cudaEventRecordExternal));
+  PIN_CK(p, mark(2, rs.xs));
+  const ArgsY ay = radius_args_y(p, ms, collapse, rs.vbuf);
+  PIN_CK(p, launch_y(p->ny, p->tc_y, ay, rs.xs));
+  PIN_CK(p, mark(3, rs.xs));
+  if (rs.y_done) {
+    PIN_CK(p, cudaEventRecord(rs.y_done, rs.xs));
+    PIN_CK(p, cudaStreamWaitEvent(rs.zs, rs.y_done, 0));
+  }
 
   ArgsZ az{};
   const int nf = (p->velocities && collapse) ? 9 : 6;
-  for (int f = 0; f < nf; ++f) az.src[f] = spec(p, p->V, f);
+  for (int f = 0; f < nf; ++f) az.src[f] = spec(p, rs.vbuf, f);
   az.nfields = nf;
   az.psi_out = p->psi;
   az.vstate = (p->velocities && collapse) ? p->vstate : nullptr;
   az.nlines = p->nx * p->ny * p->batch;
   az.npart = az.nlines * p->nz;
-  az.lam_out = reinterpret_cast<float*>(p->U);  // the x-pass spectra are free by now
+  az.lam_out = reinterpret_cast<float*>(p->U);  // the x-pass spectra are free by now (serial schedule)
   az.tw = p->twz();
   az.nhp = p->nhp;
   az.fmax = p->fmax;
@@ -420,17 +457,19 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
     for (int f = 0; f < 6; ++f) az.out[f] = dump[f];
   if (source) {
     az.out[0] = source;
-    PIN_CK(p, launch_z_source(p->nz, az, p->stream));
+    PIN_CK(p, launch_z_source(p->nz, az, rs.zs));
     return PIN_OK;
   }
-  if (!dump) PIN_CK(p, cudaMemsetAsync(p->redo_count, 0, sizeof(unsigned), p->stream));
-  PIN_CK(p, launch_z(p->nz, az, dump != nullptr, p->stream));
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 3], p->stream, cudaEventRecordExternal));
+  PIN_CK(p, mark(4, rs.zs));
+  if (!dump) PIN_CK(p, cudaMemsetAsync(p->redo_count, 0, sizeof(unsigned), rs.zs));
+  PIN_CK(p, launch_z(p->nz, az, dump != nullptr, rs.zs));
+  PIN_CK(p, mark(5, rs.zs));
   if (!dump) {
-    if (!z_fuses_roots(p->nz)) PIN_CK(p, launch_roots(az, p->stream));
-    PIN_CK(p, launch_redo(az, p->stream));
+    if (!z_fuses_roots(p->nz)) PIN_CK(p, launch_roots(az, rs.zs));
+    PIN_CK(p, launch_redo(az, rs.zs));
   }
-  if (rec) PIN_CK(p, cudaEventRecordWithFlags(p->events[5 * scale + 4], p->stream, cudaEventRecordExternal));
+  PIN_CK(p, mark(6, rs.zs));
+  if (rs.z_done) PIN_CK(p, cudaEventRecord(rs.z_done, rs.zs));
   return PIN_OK;
 }
 
@@ -439,10 +478,32 @@ pin_status enqueue_collapse(pin_plan_t p) {
   PIN_CK(p, cudaMemsetAsync(p->fmax, 0, n3 * sizeof(float), p->stream));
   PIN_CK(p, cudaMemsetAsync(p->idx, 0xFF, n3 * sizeof(int), p->stream));
   if (p->velocities) PIN_CK(p, cudaMemsetAsync(p->vstate, 0, 3 * n3 * sizeof(float), p->stream));
+  if (p->sched == 0) {
+    for (int s = 0; s < p->nscales; ++s) {
+      pin_status st = enqueue_radius(p, s, s, nullptr);
+      if (st != PIN_OK) return st;
+    }
+    return PIN_OK;
+  }
+  // Overlapped schedule: the x and y passes of radius s + 1 run on s_xy while
+  // the z pass and the redo of radius s run on s_z.  The y pass of radius s
+  // overwrites the V buffer that the z pass of radius s - nbuf read, so it
+  // waits for that z pass; the x pass of s writes only U, which the y pass of
+  // s - 1 (earlier on s_xy) has finished reading.  cap_ev: [0] fork,
+  // [1 + 2 s] y_done of s, [2 + 2 s] z_done of s.
+  const int nbuf = p->sched == 2 ? 2 : 1;
+  PIN_CK(p, cudaEventRecord(p->cap_ev[0], p->stream));
+  PIN_CK(p, cudaStreamWaitEvent(p->s_xy, p->cap_ev[0], 0));
+  PIN_CK(p, cudaStreamWaitEvent(p->s_z, p->cap_ev[0], 0));
   for (int s = 0; s < p->nscales; ++s) {
-    pin_status st = enqueue_radius(p, s, s, nullptr);
+    RadiusSched rs{p->s_xy, p->s_z, (nbuf == 2 && (s & 1)) ? p->V2 : p->V,
+                   s >= nbuf ? p->cap_ev[2 + 2 * (s - nbuf)] : nullptr, p->cap_ev[1 + 2 * s], p->cap_ev[2 + 2 * s]};
+    pin_status st = enqueue_radius(p, s, s, nullptr, nullptr, &rs);
     if (st != PIN_OK) return st;
   }
+  // join: the plan's stream continues after the last redo and the last y pass
+  PIN_CK(p, cudaStreamWaitEvent(p->stream, p->cap_ev[2 + 2 * (p->nscales - 1)], 0));
+  PIN_CK(p, cudaStreamWaitEvent(p->stream, p->cap_ev[1 + 2 * (p->nscales - 1)], 0));
   return PIN_OK;
 }
 
@@ -458,7 +519,9 @@ pin_status ensure_graph(pin_plan_t p) {
   }
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaStreamEndCapture");
   p->graph = g;
-  e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+  // the overlapped schedule's kernel nodes carry the priorities of their
+  // capture streams (x/y passes above the z pass)
+  e = cudaGraphInstantiateWithFlags(&p->graph_exec, g, p->sched ? cudaGraphInstantiateFlagUseNodePriority : 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
     p->graph = nullptr;
@@ -976,7 +1039,7 @@ pin_status pin_profile(pin_plan_t p, int enable) {
   if (want == p->profile) return PIN_OK;
   PIN_CK(p, cudaStreamSynchronize(p->stream));
   if (want && p->events.empty()) {
-    p->events.resize(5 * (size_t)p->nscales, nullptr);
+    p->events.resize(7 * (size_t)p->nscales, nullptr);
     for (auto& e : p->events) PIN_CK(p, cudaEventCreate(&e));
   }
   p->profile = want;
@@ -1068,14 +1131,51 @@ pin_status pin_pass_times(pin_plan_t p, double* ms4) {
   if (!p->profile || p->events.empty() || p->calls == 0) return fail(p, PIN_ESTATE, "profiling is off or nothing ran");
   PIN_CK(p, cudaStreamSynchronize(p->stream));
   ms4[0] = ms4[1] = ms4[2] = ms4[3] = 0.0;
+  // events per radius: x begin/end, y begin/end, z begin/end, redo end
+  static const int from[4] = {0, 2, 4, 5}, to[4] = {1, 3, 5, 6};
   for (int s = 0; s < p->nscales; ++s)
     for (int k = 0; k < 4; ++k) {
       float ms = 0.f;
-      PIN_CK(p, cudaEventElapsedTime(&ms, p->events[5 * s + k], p->events[5 * s + k + 1]));
+      PIN_CK(p, cudaEventElapsedTime(&ms, p->events[7 * s + from[k]], p->events[7 * s + to[k]]));
       ms4[k] += ms;
     }
   return PIN_OK;
 }
+
+pin_status pin_set_schedule(pin_plan_t p, int schedule) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (schedule < 0 || schedule > 2) return fail(p, PIN_EINVAL, "schedule must be 0, 1 or 2");
+  if (schedule && !z_fuses_roots(p->nz))
+    return fail(p, PIN_EINVAL, "the overlapped schedules need a z pass that computes the collapse times (nz 384, 768)");
+  if (schedule == p->sched) return PIN_OK;
+  PIN_CK(p, cudaStreamSynchronize(p->stream));
+  if (schedule && !p->s_xy) {
+    int least = 0, greatest = 0;
+    PIN_CK(p, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    PIN_CK(p, cudaStreamCreateWithPriority(&p->s_xy, cudaStreamNonBlocking, greatest));
+    PIN_CK(p, cudaStreamCreateWithPriority(&p->s_z, cudaStreamNonBlocking, least));
+    p->cap_ev.assign(1 + 2 * (size_t)p->nscales, nullptr);
+    for (auto& e : p->cap_ev) PIN_CK(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  if (schedule == 2 && !p->V2) {
+    cudaError_t e = plan_alloc(reinterpret_cast<void**>(&p->V2), (size_t)(p->velocities ? 9 : 6) * p->field_elems * 8);
+    if (e != cudaSuccess) {
+      p->V2 = nullptr;
+      cudaGetLastError();
+      return fail(p, PIN_ENOMEM, "no device memory for the second V buffer of schedule 2");
+    }
+  }
+  if (schedule != 2 && p->V2) {
+    cudaFree(p->V2);
+    p->V2 = nullptr;
+  }
+  p->sched = schedule;
+  drop_graph(p);
+  return PIN_OK;
+}
+
+int pin_get_schedule(pin_plan_t p) { return p ? p->sched : -1; }
 
 pin_status pin_set_wait_budget(pin_plan_t p, int64_t cycles) {
   pin_status st = check_plan(p);

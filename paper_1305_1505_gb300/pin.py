@@ -57,7 +57,8 @@ EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times"
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
            "pin_fragment_order", "pin_displacements_2lpt", "pin_set_ic_seed", "pin_tile_options",
-           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_noalloc_status", "pin_set_wait_budget",
+           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_noalloc_status", "pin_set_schedule",
+           "pin_get_schedule", "pin_set_wait_budget",
            "pin_debug_fail_alloc", "pin_strerror", "pin_last_error", "pin_destroy")
 
 _lib = None
@@ -119,6 +120,10 @@ def load(path=None):
     L.pin_collapse_times_noalloc.restype = ctypes.c_int
     L.pin_noalloc_status.argtypes = [IP, ctypes.POINTER(ctypes.c_uint64)]
     L.pin_noalloc_status.restype = ctypes.c_int
+    L.pin_set_schedule.argtypes = [P, ctypes.c_int]
+    L.pin_set_schedule.restype = ctypes.c_int
+    L.pin_get_schedule.argtypes = [P]
+    L.pin_get_schedule.restype = ctypes.c_int
     L.pin_set_wait_budget.argtypes = [P, ctypes.c_int64]
     L.pin_set_wait_budget.restype = ctypes.c_int
     L.pin_debug_fail_alloc.argtypes = [ctypes.c_int]
@@ -296,6 +301,16 @@ def pin_noalloc_status():
     if st not in (PIN_OK, PIN_ECUDA):
         _check(st)
     return st, w.value, list(c)
+
+
+def pin_set_schedule(plan, schedule):
+    """Radius schedule: 0 serial, 1 z(s) beside x(s+1), 2 z(s) beside x and
+    y of s+1 (second V buffer)."""
+    _check(load().pin_set_schedule(plan, int(schedule)), plan)
+
+
+def pin_get_schedule(plan):
+    return load().pin_get_schedule(plan)
 
 
 def pin_set_wait_budget(plan, cycles):

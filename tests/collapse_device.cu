@@ -1,13 +1,37 @@
-// Device build of the CUDA path's per-particle arithmetic (csrc/collapse.cuh)
-// behind a host function, so that GPU tests can compare it with the oracle
-// one particle at a time.
+// Device build of the CUDA path's per-particle arithmetic (csrc/collapse.cuh,
+// and the two-particle packed form of csrc/collapse_x2.cuh) behind a host
+// function, so that GPU tests can compare it with the oracle particle by
+// particle.  use_float: 0 FP64, 1 FP32 one particle per thread, 2 FP32 packed
+// pairs (thread i evaluates particles i and i + n/2, n even).
 #include <cuda_runtime.h>
 
 #include "collapse.cuh"
+#include "collapse_x2.cuh"
 
 __global__ void k_eval(const double* lam, const double* h, int n, int corr, double dcorr, int use_float,
                        double* F, double* kap, double* eig) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (use_float == 2) {
+    const int m = n / 2;
+    if (i >= m) return;
+    const int j[2] = {i, i + m};
+    float2 l[3], hf[6], le[3];
+    for (int k = 0; k < 3; ++k) l[k] = make_float2((float)lam[3 * j[0] + k], (float)lam[3 * j[1] + k]);
+    for (int k = 0; k < 6; ++k) hf[k] = make_float2((float)h[6 * j[0] + k], (float)h[6 * j[1] + k]);
+    pin::CollapseConsts<float> cc{(float)dcorr, corr};
+    float2 k2;
+    const float2 f = pin::collapse_from_eigs_x2(l, cc, k2);
+    F[j[0]] = f.x;
+    F[j[1]] = f.y;
+    kap[j[0]] = k2.x;
+    kap[j[1]] = k2.y;
+    pin::eig3_x2(hf, le);
+    for (int k = 0; k < 3; ++k) {
+      eig[3 * j[0] + k] = le[k].x;
+      eig[3 * j[1] + k] = le[k].y;
+    }
+    return;
+  }
   if (i >= n) return;
   if (use_float) {
     float l[3] = {(float)lam[3 * i], (float)lam[3 * i + 1], (float)lam[3 * i + 2]};

@@ -33,6 +33,10 @@ def lib():
 
 
 def _eval(L, lam, h, corr, use_float):
+    if use_float == 2 and lam.shape[0] % 2:  # pairs need an even count
+        lam, h = np.vstack([lam, lam[:1]]), np.vstack([h, h[:1]])
+        F, kap, eig = _eval(L, lam, h, corr, use_float)
+        return F[:-1], kap[:-1], eig[:-1]
     n = lam.shape[0]
     lam = np.ascontiguousarray(lam, dtype=np.float64)
     h = np.ascontiguousarray(h, dtype=np.float64)
@@ -43,7 +47,8 @@ def _eval(L, lam, h, corr, use_float):
     return F, kap, eig
 
 
-def test_device_collapse_and_eigen_vs_oracle(lib):
+@pytest.mark.parametrize("mode", [1, 2], ids=["fp32", "fp32_pairs"])
+def test_device_collapse_and_eigen_vs_oracle(lib, mode):
     rng = np.random.default_rng(3)
     n = 20000
     lam = -np.sort(-rng.normal(size=(n, 3)) * 0.6, axis=1)
@@ -53,7 +58,7 @@ def test_device_collapse_and_eigen_vs_oracle(lib):
     F64, _, e64 = _eval(lib, lam, h, 1, 0)
     assert np.abs(F64 - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
     assert np.abs(e64 - ref_eig).max() <= 1e-12 * np.abs(h).max()
-    F32, kap, e32 = _eval(lib, lam, h, 1, 1)
+    F32, kap, e32 = _eval(lib, lam, h, 1, mode)
     ok = kap >= 1e-3
     err = np.abs(F32 - ref)
     bad = np.nonzero(ok & (err > 1e-4 * np.abs(ref) + 1e-6))[0]
@@ -83,12 +88,13 @@ def _special_eigenvalues(rng):
     return lam
 
 
-def test_device_collapse_special_cases(lib):
+@pytest.mark.parametrize("mode", [1, 2], ids=["fp32", "fp32_pairs"])
+def test_device_collapse_special_cases(lib, mode):
     lam = _special_eigenvalues(np.random.default_rng(11))
     h = np.zeros((lam.shape[0], 6))
     h[:, :3] = lam
     ref = np.array([oracle.collapse_F(l, c) for l in lam for c in (1,)])
-    F32, kap, _ = _eval(lib, lam, h, 1, 1)
+    F32, kap, _ = _eval(lib, lam, h, 1, mode)
     assert np.all(np.isfinite(kap)) and np.all(np.isfinite(F32))
     scale = np.abs(lam).max(axis=1)
     ok = kap >= 1e-3

@@ -62,22 +62,27 @@ def test_injected_allocation_failure_leaves_nothing_allocated():
     n, box = 64, 128.0
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
-    for vel in (False, True):
-        allocs = 15 if vel else 13
-        for nth in range(allocs):
-            free0, _ = torch.cuda.mem_get_info()
-            pin.pin_debug_fail_alloc(nth)
-            with pytest.raises(pin.PinError) as e:
-                pin.Plan(n, box, [8.0, 4.0], stream=stream, velocities=vel)
-            assert e.value.status == pin.PIN_ENOMEM, (vel, nth)
-            free1, _ = torch.cuda.mem_get_info()
-            assert free1 == free0, (vel, nth, free0 - free1)
-        # one past the last allocation: the injection is not reached, the plan
-        # is made, and the pending injection is cancelled
-        pin.pin_debug_fail_alloc(allocs)
-        plan = pin.Plan(n, box, [8.0, 4.0], stream=stream, velocities=vel)
+    try:
+        for vel in (False, True):
+            # the plan's device arrays: Phi0, U, V, [psi, v state,] F_max, index,
+            # multipliers, twiddles, counters, redo queue, its count, error word
+            allocs = 13 if vel else 11
+            for nth in range(allocs):
+                free0, _ = torch.cuda.mem_get_info()
+                pin.pin_debug_fail_alloc(nth)
+                with pytest.raises(pin.PinError) as e:
+                    pin.Plan(n, box, [8.0, 4.0], stream=stream, velocities=vel)
+                assert e.value.status == pin.PIN_ENOMEM, (vel, nth)
+                free1, _ = torch.cuda.mem_get_info()
+                assert free1 == free0, (vel, nth, free0 - free1)
+            # one past the last allocation: the injection is not reached and the
+            # plan is made; the pending injection is then cancelled
+            pin.pin_debug_fail_alloc(allocs)
+            plan = pin.Plan(n, box, [8.0, 4.0], stream=stream, velocities=vel)
+            pin.pin_debug_fail_alloc(-1)
+            plan.set_ic(torch.from_numpy(parity.inputs(n, box, 9)[0]).cuda())
+            F, I = plan.collapse_times()
+            assert (I >= 0).float().mean() > 0.05
+            plan.close()
+    finally:
         pin.pin_debug_fail_alloc(-1)
-        plan.set_ic(torch.from_numpy(parity.inputs(n, box, 9)[0]).cuda())
-        F, I = plan.collapse_times()
-        assert (I >= 0).float().mean() > 0.05
-        plan.close()
