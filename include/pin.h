@@ -53,7 +53,7 @@ typedef enum {
 } pin_status;
 
 enum { PIN_CORR_NONE = 0, PIN_CORR_SPHERE = 1 };
-enum { PIN_FP32_FALLBACK64 = 0 };
+enum { PIN_FP32_FALLBACK64 = 0, PIN_FP64 = 1 };
 enum { PIN_C64 = 0, PIN_C128 = 1 };
 
 typedef struct {
@@ -70,7 +70,12 @@ typedef struct {
   int correction;        /* PIN_CORR_SPHERE (quasi-spherical correction, default) or
                             PIN_CORR_NONE (pure ellipsoidal 3LPT truncation) */
   int precision;         /* PIN_FP32_FALLBACK64: FP32 FFTs and collapse, FP64 redo of
-                            near-degenerate eigenvalues and near-tangent roots */
+                            near-degenerate eigenvalues and near-tangent roots.
+                            PIN_FP64: a slow all-FP64 loop for checking (filter, line
+                            transforms, eigenvalues, collapse and running maximum in
+                            double; pin_collapse_times_f64 returns F_max in FP64); batch 1,
+                            no velocities; only the collapse-time calls use it, the
+                            other calls of the plan run in FP32 */
   void* stream;          /* cudaStream_t to run on, or NULL for a plan-owned stream */
   int batch;             /* number of realisations B processed together (0 or 1: one);
                             they share N, box, radii and correction.  Inputs and outputs
@@ -128,6 +133,11 @@ pin_status pin_set_ic_seed(pin_plan_t p, uint64_t seed, const pin_spectrum* ps);
  * returns (use pin_sync or the stream).  on_device = 0: host pointers; the
  * call returns when the results are in host memory. */
 pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, int on_device);
+
+/* pin_collapse_times of a PIN_FP64 plan with F_max in double precision
+ * (F_max: N^3 doubles; scale_idx as in pin_collapse_times).  PIN_EINVAL for a
+ * plan of another precision. */
+pin_status pin_collapse_times_f64(pin_plan_t p, double* F_max, int32_t* scale_idx, int on_device);
 
 /* v_max of Sec. 2.1.1: for each particle, the gradient of the potential
  * (smoothed on R_max), taken as the linear (Zel'dovich) displacement
@@ -233,6 +243,15 @@ pin_status pin_tile_options(int n, int* opts, int* count);
 pin_status pin_get_tiles(pin_plan_t p, int* tc_x, int* tc_y);
 pin_status pin_set_tiles(pin_plan_t p, int tc_x, int tc_y);
 pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y);
+
+/* Replaces the plan's radius list (1..64 radii, as in pin_plan_desc) without
+ * touching its device workspace, so that one plan serves requests with other
+ * radii: a server keeps plans per grid size and reuses them.  Waits for the
+ * plan's stream, then uploads the new filter tables.  The graph captured for
+ * a radius count is kept, so returning to a count seen before needs no new
+ * capture.  The next pin_collapse_times uses the new radii; pin_hessian's scale
+ * index refers to them.  PIN_EINVAL for a bad list (plan unchanged). */
+pin_status pin_set_radii(pin_plan_t p, int nscales, const double* radii);
 
 /* Radius schedule of pin_collapse_times (the paper has no counterpart; its
  * loop is sequential).  0 (default): the passes of each radius run in order on

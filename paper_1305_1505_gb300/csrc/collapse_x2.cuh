@@ -18,33 +18,11 @@
 #include <cuda_runtime.h>
 
 #include "collapse.cuh"
+#include "packed.cuh"
 
 namespace pin {
 namespace x2 {
 
-__device__ __forceinline__ unsigned long long bits(float2 a) { return *reinterpret_cast<unsigned long long*>(&a); }
-__device__ __forceinline__ float2 unbits(unsigned long long a) { return *reinterpret_cast<float2*>(&a); }
-__device__ __forceinline__ float2 add(float2 a, float2 b) {
-  unsigned long long r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(bits(a)), "l"(bits(b)));
-  return unbits(r);
-}
-__device__ __forceinline__ float2 sub(float2 a, float2 b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(bits(a)), "l"(bits(b)));
-  return unbits(r);
-}
-__device__ __forceinline__ float2 mul(float2 a, float2 b) {
-  unsigned long long r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(bits(a)), "l"(bits(b)));
-  return unbits(r);
-}
-__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(bits(a)), "l"(bits(b)), "l"(bits(c)));
-  return unbits(r);
-}
-__device__ __forceinline__ float2 splat(float s) { return make_float2(s, s); }
 // per-lane helpers
 __device__ __forceinline__ float2 sqrt_approx(float2 a) {
   return make_float2(M<float>::sqrt_approx(a.x), M<float>::sqrt_approx(a.y));
@@ -165,9 +143,11 @@ struct CollapseStateX2 {
   unsigned need;   // bit (2 a + lane): axis a + 1 of that lane may collapse first
 };
 
-// collapse_main<float> for two particles.
-__device__ __forceinline__ void collapse_main_x2(const float2 lam[3], const CollapseConsts<float>& cc,
-                                                 CollapseStateX2& st) {
+// First part of collapse_main<float> for two particles: the coefficients of
+// the three axes (c0 for the axis of the largest eigenvalue, st.c for the
+// others) and the quasi-spherical correction term st.corr.
+__device__ __forceinline__ void collapse_prep_x2(const float2 lam[3], const CollapseConsts<float>& cc,
+                                                 CollapseStateX2& st, float2 c0[3]) {
   using namespace x2;
   const float2 mu1 = add(add(lam[0], lam[1]), lam[2]);
   const float2 mu3 = mul(mul(lam[0], lam[1]), lam[2]);
@@ -179,17 +159,15 @@ __device__ __forceinline__ void collapse_main_x2(const float2 lam[3], const Coll
   const float2 k37 = splat(3.0f / 7.0f), k1084 = splat(10.0f / 84.0f);
   const float2 nmu3 = mul(mu3, splat(-1.0f / 9.0f));
   // axis i: c1 = lam_i, c2 = (3/7) e_i, c3 = (10/84)(lam_i (e_j + e_k) + e_i (lam_j + lam_k)) - mu3/9
-  const float2 c02 = fma(k1084, fma(e0, s12, mul(lam[0], add(e1, e2))), nmu3);
+  c0[0] = lam[0];
+  c0[1] = mul(k37, e0);
+  c0[2] = fma(k1084, fma(e0, s12, mul(lam[0], add(e1, e2))), nmu3);
   st.c[0][0] = lam[1];
   st.c[0][1] = mul(k37, e1);
   st.c[0][2] = fma(k1084, fma(e1, s02, mul(lam[1], add(e2, e0))), nmu3);
   st.c[1][0] = lam[2];
   st.c[1][1] = mul(k37, e2);
   st.c[1][2] = fma(k1084, fma(e2, s01, mul(lam[2], add(e0, e1))), nmu3);
-  st.best = largest_root_iter_x2(lam[0], mul(k37, e0), c02, st.kappa);
-  const unsigned n0 = no_root_from_x2(st.c[0][0], st.c[0][1], st.c[0][2], st.best);
-  const unsigned n1 = no_root_from_x2(st.c[1][0], st.c[1][1], st.c[1][2], st.best);
-  st.need = (~n0 & 3u) | ((~n1 & 3u) << 2);
   // quasi-spherical correction: z = eps / 0.1
   const float2 num = mul(splat(10.0f), sub(lam[0], lam[2]));
   const float2 z = div(num, make_float2(mu1.x > 0.0f ? mu1.x : 1.0f, mu1.y > 0.0f ? mu1.y : 1.0f));
@@ -198,6 +176,39 @@ __device__ __forceinline__ void collapse_main_x2(const float2 lam[3], const Coll
   const float2 cw = mul(mul(mu1, splat(cc.dcorr)), w);
   st.corr.x = (cc.correction && mu1.x > 0.0f) ? cw.x : 0.0f;
   st.corr.y = (cc.correction && mu1.y > 0.0f) ? cw.y : 0.0f;
+}
+
+// Second part: the largest root of the axis-0 cubic (st.best, st.kappa) and
+// the exact test whether the two other axes may collapse first (st.need).
+__device__ __forceinline__ void collapse_root_x2(const float2 c0[3], CollapseStateX2& st) {
+  st.best = largest_root_iter_x2(c0[0], c0[1], c0[2], st.kappa);
+  const unsigned n0 = no_root_from_x2(st.c[0][0], st.c[0][1], st.c[0][2], st.best);
+  const unsigned n1 = no_root_from_x2(st.c[1][0], st.c[1][1], st.c[1][2], st.best);
+  st.need = (~n0 & 3u) | ((~n1 & 3u) << 2);
+}
+
+// collapse_main<float> for two particles.
+__device__ __forceinline__ void collapse_main_x2(const float2 lam[3], const CollapseConsts<float>& cc,
+                                                 CollapseStateX2& st) {
+  float2 c0[3];
+  collapse_prep_x2(lam, cc, st, c0);
+  collapse_root_x2(c0, st);
+}
+
+// Which lanes cannot reach F > fm (bit 0 / bit 1): F = max_i F_i + corr with
+// F_i >= 0 the largest root of axis i (clamped at 0), so F < fm when
+// t = fm - corr >= 0 and no axis cubic has a real root at or above t.  The
+// test runs at t (1 - 1e-5), below t by more than the FP32 error of a root, so
+// that a lane it clears could not have been updated by the full computation
+// (nor by its FP64 redo).  Exact up to rounding, like no_root_from.
+__device__ __forceinline__ unsigned cannot_beat_x2(const float2 c0[3], const CollapseStateX2& st, float2 fm) {
+  using namespace x2;
+  const float2 t = mul(sub(fm, st.corr), splat(1.0f - 1e-5f));
+  const unsigned a0 = no_root_from_x2(c0[0], c0[1], c0[2], t);
+  const unsigned a1 = no_root_from_x2(st.c[0][0], st.c[0][1], st.c[0][2], t);
+  const unsigned a2 = no_root_from_x2(st.c[1][0], st.c[1][1], st.c[1][2], t);
+  const unsigned nonneg = (t.x >= 0.0f ? 1u : 0u) | (t.y >= 0.0f ? 2u : 0u);
+  return a0 & a1 & a2 & nonneg;
 }
 
 // One lane of a pair state as the scalar state of collapse.cuh (for the rare

@@ -15,13 +15,21 @@
 // twiddle w_N^{p k1} one shared-memory exchange hands every thread E/P values
 // of k1 with all P values of p, and level 2 is E/P length-P DFTs, again in
 // registers.  One shared-memory round trip per line and transform.
+//
+// Complex additions and the radix-2/3/4 butterflies use the packed FP32x2
+// instructions (packed.cuh): the real and imaginary parts of a complex value
+// are the two lanes of one register pair, and the multiplications by i in the
+// radix-3 and radix-4 butterflies become a lane swap and one packed fma with
+// a (-s, s) constant.
 #pragma once
 #include <cuda_runtime.h>
 
+#include "packed.cuh"
+
 namespace pin {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return x2::add(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return x2::sub(a, b); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -63,24 +71,27 @@ template <> struct DFT<2> {
 
 template <> struct DFT<3> {
   __device__ __forceinline__ static void run(float2 (&v)[3]) {
-    // w = exp(2 pi i / 3) = -1/2 + i sqrt(3)/2
+    // w = exp(2 pi i / 3) = -1/2 + i sqrt(3)/2:
+    // X1 = m + i h d, X2 = m - i h d with m = a - s/2, s = v1 + v2, d = v1 - v2,
+    // and i h d = swap(d) * (-h, h)
     const float h = 0.86602540378443864676f;
-    float2 a = v[0], s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
-    float2 m = make_float2(fmaf(-0.5f, s.x, a.x), fmaf(-0.5f, s.y, a.y));
+    const float2 a = v[0], s = cadd(v[1], v[2]), ds = x2::swap(csub(v[1], v[2]));
+    const float2 m = x2::fma(s, x2::splat(-0.5f), a);
     v[0] = cadd(a, s);
-    v[1] = make_float2(m.x - h * d.y, m.y + h * d.x);
-    v[2] = make_float2(m.x + h * d.y, m.y - h * d.x);
+    v[1] = x2::fma(ds, make_float2(-h, h), m);
+    v[2] = x2::fma(ds, make_float2(h, -h), m);
   }
 };
 
 template <> struct DFT<4> {
   __device__ __forceinline__ static void run(float2 (&v)[4]) {
-    float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    float2 s13 = cadd(v[1], v[3]), d13 = cmuli(csub(v[1], v[3]));
+    // X1 = d02 + i t, X3 = d02 - i t with t = v1 - v3, i t = swap(t) * (-1, 1)
+    const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const float2 s13 = cadd(v[1], v[3]), ts = x2::swap(csub(v[1], v[3]));
     v[0] = cadd(s02, s13);
     v[2] = csub(s02, s13);
-    v[1] = cadd(d02, d13);
-    v[3] = csub(d02, d13);
+    v[1] = x2::fma(ts, make_float2(-1.f, 1.f), d02);
+    v[3] = x2::fma(ts, make_float2(1.f, -1.f), d02);
   }
 };
 

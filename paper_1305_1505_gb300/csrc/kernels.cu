@@ -504,16 +504,27 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
             }
           }
         }
+        // lanes that cannot beat their running maximum (the radii run
+        // smallest first, so most particles reach F_max early) or that the
+        // FP64 redo finishes skip the root solve; a pair solves only if one of
+        // its lanes needs it
         CollapseStateX2 csx[NPR];
+        unsigned done[NPR];
 #pragma unroll
-        for (int r = 0; r < NPR; ++r) collapse_main_x2(lam[r], ccf, csx[r]);
+        for (int r = 0; r < NPR; ++r) {
+          float2 c0[3];
+          collapse_prep_x2(lam[r], ccf, csx[r], c0);
+          done[r] = cannot_beat_x2(c0, csx[r], make_float2(fm[r][0], fm[r][1])) | (valid[r][0] ? 0u : 1u) |
+                    (valid[r][1] ? 0u : 2u);
+          if (done[r] != 3u) collapse_root_x2(c0, csx[r]);
+        }
 #pragma unroll
         for (int r = 0; r < NPR; ++r)
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
+            if ((done[r] >> u) & 1u) continue;
             CollapseState<float> cs = lane_state(csx[r], u);
             if (cs.need[0] || cs.need[1]) collapse_rare<float>(cs);
-            if (!valid[r][u]) continue;
             const int qq = q[r][u];
             const float F = cs.best + cs.corr;
             if (cs.kappa < a.tau_root) {
@@ -535,7 +546,7 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
               }
               atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
             }
-            if (F > fm[r][u]) {
+            if (F > fm[r][u] || (F == fm[r][u] && F > 0.f && a.scale < a.idx[qq])) {
               a.fmax[qq] = F;
               a.idx[qq] = a.scale;
               if constexpr (NP == 5) {
@@ -625,7 +636,7 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
             }
             atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
           }
-          if (F > fm[u]) {
+          if (F > fm[u] || (F == fm[u] && F > 0.f && a.scale < a.idx[q[u]])) {
             a.fmax[q[u]] = F;
             a.idx[q[u]] = a.scale;
             if constexpr (NP == 5) {
@@ -790,12 +801,16 @@ __global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
         }
       }
       CollapseStateX2 csx;
-      collapse_main_x2(lam, ccf, csx);
+      float2 c0[3];
+      collapse_prep_x2(lam, ccf, csx, c0);
+      const unsigned done = cannot_beat_x2(c0, csx, make_float2(fm[0], fm[1])) | (valid[0] ? 0u : 1u) |
+                            (valid[1] ? 0u : 2u);
+      if (done != 3u) collapse_root_x2(c0, csx);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
+        if ((done >> u) & 1u) continue;
         CollapseState<float> cs = lane_state(csx, u);
         if (cs.need[0] || cs.need[1]) collapse_rare<float>(cs);
-        if (!valid[u]) continue;
         const float F = cs.best + cs.corr;
         if (cs.kappa < a.tau_root) {
           atomicAdd(a.counters + 1, 1ull);
@@ -812,7 +827,7 @@ __global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
           }
           atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
         }
-        if (F > fm[u]) {
+        if (F > fm[u] || (F == fm[u] && F > 0.f && a.scale < a.idx[q[u]])) {
           a.fmax[q[u]] = F;
           a.idx[q[u]] = a.scale;
           if constexpr (VEL) {
@@ -823,8 +838,7 @@ __global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
         }
       }
     }
-    return;
-  }
+  } else {
   for (int q0 = blockIdx.x * blockDim.x + threadIdx.x; q0 < total; q0 += U * stride) {
     float lam[U][3], fm[U];
     bool valid[U];
@@ -866,7 +880,7 @@ __global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
         }
         atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
       }
-      if (F > fm[u]) {
+      if (F > fm[u] || (F == fm[u] && F > 0.f && a.scale < a.idx[q[u]])) {
         a.fmax[q[u]] = F;
         a.idx[q[u]] = a.scale;
         if constexpr (VEL) {
@@ -876,6 +890,7 @@ __global__ void __launch_bounds__(256) k_roots(ArgsZ a) {
         }
       }
     }
+  }
   }
 }
 
@@ -909,7 +924,8 @@ __global__ void __launch_bounds__(128) k_redo64(ArgsZ a) {
       lam[2] = h[2];
     }
     const float F = (float)collapse_from_eigs<double>(lam, ccd, kap);
-    if (F > a.fmax[e.q]) {
+    const float fm = a.fmax[e.q];
+    if (F > fm || (F == fm && F > 0.f && a.scale < a.idx[e.q])) {
       a.fmax[e.q] = F;
       a.idx[e.q] = a.scale;
       if (a.vstate) {

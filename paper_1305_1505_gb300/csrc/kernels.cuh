@@ -172,6 +172,17 @@ void fill_twiddles(float2* t, int n, const PassShape& sh);
 cudaError_t launch_load_phi0(const void* src, int dtype, int nx, int ny, int nz, int nhp, double box, int batch,
                              float2* phi0, cudaStream_t st);
 
+// All-FP64 loop of a PIN_FP64 plan (fp64.cu): device bytes of its workspace
+// (FP64 half-spectrum, one full complex cube, the tensor, F_max), the input
+// as an FP64 half-spectrum, the whole radius loop into fmax / idx (N^3 each,
+// strict running maximum from 0 / -1), and the FP32 copy of F_max.
+size_t fp64_workspace_bytes(int nx, int ny, int nz);
+cudaError_t fp64_load(const void* src, int dtype, int nx, int ny, int nz, double2* d64, cudaStream_t st);
+cudaError_t fp64_collapse(const double2* d64, int nx, int ny, int nz, double box, int nscales, const double* radii,
+                          int correction, double dcorr, double2* work, double* h6, double* fmax, int* idx,
+                          cudaStream_t st);
+cudaError_t fp64_cast(const double* in, size_t n3, float* out, cudaStream_t st);
+
 // Seeded initial conditions on the device (ic_gpu.cu): batch cubic
 // half-spectra [n][n][n/2+1] complex64 into out, realisation b keyed by
 // keys_dev[b] (the splitmix64 of its seed), amplitude amp of P(k).

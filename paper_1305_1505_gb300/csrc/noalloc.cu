@@ -26,6 +26,7 @@
 // pin_collapse_times bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -153,7 +154,12 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
   static const int sel[6] = {2, 1, 1, 0, 0, 0};
   static const int ym[6] = {0, 1, 0, 2, 0, 1};
   static const int zm[6] = {0, 0, 1, 0, 2, 1};
-  for (int s = 0; s < nscales; ++s) {
+  // the plan path's order: ascending radius, equal radii by index
+  int order[kMaxScales];
+  for (int s = 0; s < nscales; ++s) order[s] = s;
+  std::stable_sort(order, order + nscales, [&](int a, int b) { return radii[a] < radii[b]; });
+  for (int k = 0; k < nscales; ++k) {
+    const int s = order[k];
     const float* m = mult + (size_t)s * 3 * n;
     pin::ArgsX ax{};
     ax.tm = tm_x;

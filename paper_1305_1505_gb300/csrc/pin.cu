@@ -8,6 +8,7 @@
 // pin_collapse_times replays one CUDA graph holding the whole radius loop.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -33,6 +34,7 @@ struct pin_plan_s {
   bool velocities = false; // keep the smoothed displacement at R_max (v_max)
   double box = 0.0;
   std::vector<double> radii;
+  std::vector<int> order;  // radius indices by ascending radius (ties: index), the loop's order
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -46,7 +48,7 @@ struct pin_plan_s {
   float* vstate = nullptr;  // [3][npart] displacement at R_max (velocities)
   float* fmax = nullptr;
   int* idx = nullptr;
-  float* mult = nullptr;  // (nscales + 1) x 3 x n; the last set has R = 0
+  float* mult = nullptr;  // kMaxScales + 1 sets of 3 x n; set kMaxScales has R = 0
   float2* tw = nullptr;
   unsigned long long* counters = nullptr;  // [0] eig redo, [1] root redo, [2] queue overflow
   RedoEntry* redo_list = nullptr;          // FP64 redo queue, reused by every radius
@@ -59,6 +61,11 @@ struct pin_plan_s {
   bool ic_set = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // graphs captured for other radius lists (pin_set_radii), keyed by the order
+  // their loop runs the radius indices in (the tables are read from device
+  // memory, so a graph serves every list with that order); cleared with the
+  // current graph
+  std::map<std::vector<int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graph_cache;
   uint64_t calls = 0;
   double dcorr = 0.0;
   bool profile = false;             // graph carries per-pass event records
@@ -69,6 +76,12 @@ struct pin_plan_s {
   int sched = 0;
   cudaStream_t s_xy = nullptr, s_z = nullptr;  // high / low priority streams of the overlapped schedule
   float2* V2 = nullptr;                        // second V buffer (schedule 2)
+  // PIN_FP64 plans: FP64 half-spectrum, one full complex cube, the tensor,
+  // F_max in FP64 (fp64.cu)
+  double2* d64 = nullptr;
+  double2* w64 = nullptr;
+  double* h64 = nullptr;
+  double* fmax64 = nullptr;
   std::vector<cudaEvent_t> cap_ev;             // fork/join events of the overlapped capture
   std::string last_error;
   size_t tw_off[3] = {0, 0, 0};  // per-axis twiddle tables within tw (x, y, z)
@@ -226,7 +239,11 @@ bool validate(const pin_plan_desc* d, std::string* why) {
   for (int s = 0; s < d->nscales; ++s)
     if (!(d->radii[s] >= 0.0) || !std::isfinite(d->radii[s])) { *why = "radii must be finite and >= 0"; return false; }
   if (d->correction != PIN_CORR_NONE && d->correction != PIN_CORR_SPHERE) { *why = "bad correction mode"; return false; }
-  if (d->precision != PIN_FP32_FALLBACK64) { *why = "bad precision mode"; return false; }
+  if (d->precision != PIN_FP32_FALLBACK64 && d->precision != PIN_FP64) { *why = "bad precision mode"; return false; }
+  if (d->precision == PIN_FP64 && ((d->batch > 1) || d->velocities)) {
+    *why = "PIN_FP64 needs batch 1 and no velocities";
+    return false;
+  }
   if (d->velocities != 0 && d->velocities != 1) { *why = "velocities must be 0 or 1"; return false; }
   const long long b = d->batch <= 0 ? 1 : d->batch;
   if (b > 4096) { *why = "batch must be in 1..4096"; return false; }
@@ -260,11 +277,17 @@ unsigned redo_capacity(size_t n3, int batch) {
 
 int batch_of(const pin_plan_desc* d) { return d->batch <= 0 ? 1 : d->batch; }
 
-size_t footprint(int nx, int ny, int nz, int nscales, int batch, bool velocities) {
+// multiplier sets of a plan: one per radius (at most 64, pin_set_radii may
+// change the list), then the R = 0 set of the unsmoothed products
+constexpr int kMaxScales = 64;
+
+size_t footprint(int nx, int ny, int nz, int nscales, int batch, bool velocities, bool fp64) {
+  (void)nscales;
   const size_t spec = (size_t)nx * ny * padded_half(nz) * batch;
   const size_t n3 = (size_t)nx * ny * nz * batch;
-  return spec * 8 * (velocities ? 13 : 10) + n3 * 8 + (velocities ? n3 * 24 : 0) +
-         (size_t)(nscales + 1) * 3 * (nx + ny + nz) * 4 + (size_t)(nx + ny + nz + 3 * 64) * 8 + 64 +
+  return (fp64 ? fp64_workspace_bytes(nx, ny, nz) : 0) + spec * 8 * (velocities ? 13 : 10) + n3 * 8 +
+         (velocities ? n3 * 24 : 0) +
+         (size_t)(kMaxScales + 1) * 3 * (nx + ny + nz) * 4 + (size_t)(nx + ny + nz + 3 * 64) * 8 + 64 +
          (size_t)redo_capacity((size_t)nx * ny * nz, batch) * sizeof(RedoEntry) + 16 + sizeof(int);
 }
 
@@ -290,9 +313,10 @@ pin_status ensure_device_init(pin_plan_t p) {
   return PIN_OK;
 }
 
+void drop_graph(pin_plan_t p);
+
 void release(pin_plan_t p) {
-  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-  if (p->graph) cudaGraphDestroy(p->graph);
+  drop_graph(p);
   cudaFree(p->phi0);
   cudaFree(p->U);
   cudaFree(p->V);
@@ -310,6 +334,14 @@ void release(pin_plan_t p) {
   p->events.clear();
   cudaFree(p->V2);
   p->V2 = nullptr;
+  cudaFree(p->d64);
+  cudaFree(p->w64);
+  cudaFree(p->h64);
+  cudaFree(p->fmax64);
+  p->d64 = nullptr;
+  p->w64 = nullptr;
+  p->h64 = nullptr;
+  p->fmax64 = nullptr;
   for (cudaEvent_t e : p->cap_ev) cudaEventDestroy(e);
   p->cap_ev.clear();
   if (p->s_xy) cudaStreamDestroy(p->s_xy);
@@ -327,6 +359,37 @@ void drop_graph(pin_plan_t p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   p->graph_exec = nullptr;
   p->graph = nullptr;
+  for (auto& kv : p->graph_cache) {
+    cudaGraphExecDestroy(kv.second.second);
+    cudaGraphDestroy(kv.second.first);
+  }
+  p->graph_cache.clear();
+}
+
+// The order the radius loop runs in: ascending radius, equal radii by index.
+// F_max is a maximum over radii, and the kernels break ties of F towards the
+// lower radius index whatever the order, so every order gives the same
+// results; smallest radii first makes most particles reach their F_max early,
+// after which the z pass skips the root solve of radii that cannot beat it.
+void set_order(pin_plan_t p) {
+  p->order.resize(p->nscales);
+  for (int s = 0; s < p->nscales; ++s) p->order[s] = s;
+  std::stable_sort(p->order.begin(), p->order.end(), [&](int a, int b) { return p->radii[a] < p->radii[b]; });
+}
+
+// Multiplier sets of the plan's radii (host copy, uploaded by the caller):
+// set s < nscales for radius s, set kMaxScales for R = 0.
+std::vector<float> mult_table(pin_plan_t p) {
+  std::vector<float> mult((size_t)(kMaxScales + 1) * p->mult_set(), 0.0f);
+  for (int s = 0; s <= kMaxScales; ++s) {
+    if (s < kMaxScales && s >= p->nscales) continue;
+    const double R = s < p->nscales ? p->radii[s] : 0.0;
+    float* m = mult.data() + (size_t)s * p->mult_set();
+    fill_mult(m, p->nx, p->len(p->nx), R);
+    fill_mult(m + 3 * (size_t)p->nx, p->ny, p->len(p->ny), R);
+    fill_mult(m + 3 * (size_t)(p->nx + p->ny), p->nz, p->len(p->nz), R);
+  }
+  return mult;
 }
 
 // x pass of one radius (mult set `ms`): Phi0 -> U[0..2] with the x factors
@@ -479,7 +542,8 @@ pin_status enqueue_collapse(pin_plan_t p) {
   PIN_CK(p, cudaMemsetAsync(p->idx, 0xFF, n3 * sizeof(int), p->stream));
   if (p->velocities) PIN_CK(p, cudaMemsetAsync(p->vstate, 0, 3 * n3 * sizeof(float), p->stream));
   if (p->sched == 0) {
-    for (int s = 0; s < p->nscales; ++s) {
+    for (int k = 0; k < p->nscales; ++k) {
+      const int s = p->order[k];
       pin_status st = enqueue_radius(p, s, s, nullptr);
       if (st != PIN_OK) return st;
     }
@@ -489,15 +553,17 @@ pin_status enqueue_collapse(pin_plan_t p) {
   // the z pass and the redo of radius s run on s_z.  The y pass of radius s
   // overwrites the V buffer that the z pass of radius s - nbuf read, so it
   // waits for that z pass; the x pass of s writes only U, which the y pass of
-  // s - 1 (earlier on s_xy) has finished reading.  cap_ev: [0] fork,
-  // [1 + 2 s] y_done of s, [2 + 2 s] z_done of s.
+  // s - 1 (earlier on s_xy) has finished reading.  Steps k run the radii in
+  // the plan's order; cap_ev: [0] fork, [1 + 2 k] y_done of step k,
+  // [2 + 2 k] z_done of step k.
   const int nbuf = p->sched == 2 ? 2 : 1;
   PIN_CK(p, cudaEventRecord(p->cap_ev[0], p->stream));
   PIN_CK(p, cudaStreamWaitEvent(p->s_xy, p->cap_ev[0], 0));
   PIN_CK(p, cudaStreamWaitEvent(p->s_z, p->cap_ev[0], 0));
-  for (int s = 0; s < p->nscales; ++s) {
-    RadiusSched rs{p->s_xy, p->s_z, (nbuf == 2 && (s & 1)) ? p->V2 : p->V,
-                   s >= nbuf ? p->cap_ev[2 + 2 * (s - nbuf)] : nullptr, p->cap_ev[1 + 2 * s], p->cap_ev[2 + 2 * s]};
+  for (int k = 0; k < p->nscales; ++k) {
+    const int s = p->order[k];
+    RadiusSched rs{p->s_xy, p->s_z, (nbuf == 2 && (k & 1)) ? p->V2 : p->V,
+                   k >= nbuf ? p->cap_ev[2 + 2 * (k - nbuf)] : nullptr, p->cap_ev[1 + 2 * k], p->cap_ev[2 + 2 * k]};
     pin_status st = enqueue_radius(p, s, s, nullptr, nullptr, &rs);
     if (st != PIN_OK) return st;
   }
@@ -625,7 +691,7 @@ extern "C" {
 size_t pin_footprint_bytes(const pin_plan_desc* d) {
   std::string why;
   if (!validate(d, &why)) return 0;
-  return footprint(d->nx, d->ny, d->nz, d->nscales, batch_of(d), d->velocities != 0);
+  return footprint(d->nx, d->ny, d->nz, d->nscales, batch_of(d), d->velocities != 0, d->precision == PIN_FP64);
 }
 
 pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
@@ -642,6 +708,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   p->box = d->box;
   p->nscales = d->nscales;
   p->radii.assign(d->radii, d->radii + d->nscales);
+  set_order(p);
   p->correction = d->correction;
   p->precision = d->precision;
   p->batch = batch_of(d);
@@ -667,7 +734,7 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
     p->own_stream = true;
   }
   const size_t n3 = p->n3() * p->batch;
-  const size_t mult_elems = (size_t)(p->nscales + 1) * p->mult_set();
+  const size_t mult_elems = (size_t)(kMaxScales + 1) * p->mult_set();
   // twiddle tables of the three axes, back to back
   const PassShape* shapes[3] = {&p->shape_x, &p->shape_y, &p->shape_z};
   const int ns[3] = {p->nx, p->ny, p->nz};
@@ -684,18 +751,15 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
       A(&p->mult, mult_elems * 4) != cudaSuccess || A(&p->tw, tw_elems * 8) != cudaSuccess ||
       A(&p->counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       A(&p->redo_list, (size_t)p->redo_cap * sizeof(RedoEntry)) != cudaSuccess ||
-      A(&p->redo_count, sizeof(unsigned)) != cudaSuccess || A(&p->err, sizeof(int)) != cudaSuccess) {
+      A(&p->redo_count, sizeof(unsigned)) != cudaSuccess || A(&p->err, sizeof(int)) != cudaSuccess ||
+      (p->precision == PIN_FP64 &&
+       (A(&p->d64, (size_t)p->nx * p->ny * (p->nz / 2 + 1) * 16) != cudaSuccess ||
+        A(&p->w64, n3 * 16) != cudaSuccess || A(&p->h64, 6 * n3 * 8) != cudaSuccess ||
+        A(&p->fmax64, n3 * 8) != cudaSuccess))) {
     cudaGetLastError();
     return bail(PIN_ENOMEM);
   }
-  std::vector<float> mult(mult_elems);
-  for (int s = 0; s <= p->nscales; ++s) {
-    const double R = s < p->nscales ? p->radii[s] : 0.0;  // the last set has R = 0
-    float* m = mult.data() + (size_t)s * p->mult_set();
-    fill_mult(m, p->nx, p->len(p->nx), R);
-    fill_mult(m + 3 * (size_t)p->nx, p->ny, p->len(p->ny), R);
-    fill_mult(m + 3 * (size_t)(p->nx + p->ny), p->nz, p->len(p->nz), R);
-  }
+  const std::vector<float> mult = mult_table(p);
   std::vector<float2> tw(tw_elems);
   for (int a = 0; a < 3; ++a) fill_twiddles(tw.data() + p->tw_off[a], ns[a], *shapes[a]);
   if (cudaMemcpy(p->mult, mult.data(), mult_elems * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -726,6 +790,7 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
     src = p->V;
   }
   PIN_CK(p, launch_load_phi0(src, dtype, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch, p->phi0, p->stream));
+  if (p->d64) PIN_CK(p, fp64_load(src, dtype, p->nx, p->ny, p->nz, p->d64, p->stream));
   if (!on_device) PIN_CK(p, cudaStreamSynchronize(p->stream));
   p->ic_set = true;
   return PIN_OK;
@@ -749,8 +814,19 @@ pin_status pin_set_ic_seed(pin_plan_t p, uint64_t seed, const pin_spectrum* ps) 
                             p->stream));
   PIN_CK(p, generate_ic(p->nx, p->box, keys_dev, p->batch, amp, ps->ns, ps->gamma, field, p->stream));
   PIN_CK(p, launch_load_phi0(field, PIN_C64, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch, p->phi0, p->stream));
+  if (p->d64) PIN_CK(p, fp64_load(field, PIN_C64, p->nx, p->ny, p->nz, p->d64, p->stream));
   PIN_CK(p, cudaStreamSynchronize(p->stream));  // the host key vector goes out of scope
   p->ic_set = true;
+  return PIN_OK;
+}
+
+// The FP64 radius loop of a PIN_FP64 plan into fmax64 / idx, and its FP32
+// copy into fmax (kept for the calls that read F_max, e.g. the fragment order).
+pin_status run_fp64(pin_plan_t p) {
+  const size_t n3 = p->n3();
+  PIN_CK(p, fp64_collapse(p->d64, p->nx, p->ny, p->nz, p->box, p->nscales, p->radii.data(), p->correction, p->dcorr,
+                          p->w64, p->h64, p->fmax64, p->idx, p->stream));
+  PIN_CK(p, fp64_cast(p->fmax64, n3, p->fmax, p->stream));
   return PIN_OK;
 }
 
@@ -759,12 +835,33 @@ pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, in
   if (st != PIN_OK) return st;
   if (!F_max || !scale_idx) return fail(p, PIN_EINVAL, "null output");
   if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
-  st = ensure_graph(p);
+  if (p->precision == PIN_FP64) {
+    st = run_fp64(p);
+  } else {
+    st = ensure_graph(p);
+    if (st == PIN_OK) PIN_CK(p, cudaGraphLaunch(p->graph_exec, p->stream));
+  }
   if (st != PIN_OK) return st;
-  PIN_CK(p, cudaGraphLaunch(p->graph_exec, p->stream));
   const size_t n3 = p->n3() * p->batch;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   PIN_CK(p, cudaMemcpyAsync(F_max, p->fmax, n3 * 4, kind, p->stream));
+  PIN_CK(p, cudaMemcpyAsync(scale_idx, p->idx, n3 * 4, kind, p->stream));
+  p->calls++;
+  if (!on_device) return finish_host(p);
+  return PIN_OK;
+}
+
+pin_status pin_collapse_times_f64(pin_plan_t p, double* F_max, int32_t* scale_idx, int on_device) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!F_max || !scale_idx) return fail(p, PIN_EINVAL, "null output");
+  if (p->precision != PIN_FP64) return fail(p, PIN_EINVAL, "pin_collapse_times_f64 needs a PIN_FP64 plan");
+  if (!p->ic_set) return fail(p, PIN_ESTATE, "pin_set_ic has not been called");
+  st = run_fp64(p);
+  if (st != PIN_OK) return st;
+  const size_t n3 = p->n3();
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  PIN_CK(p, cudaMemcpyAsync(F_max, p->fmax64, n3 * 8, kind, p->stream));
   PIN_CK(p, cudaMemcpyAsync(scale_idx, p->idx, n3 * 4, kind, p->stream));
   p->calls++;
   if (!on_device) return finish_host(p);
@@ -845,7 +942,7 @@ pin_status pin_hessian(pin_plan_t p, int scale, float* out6, int on_device) {
 // out = [3][N^3].
 static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float2* b0, float* out) {
   const size_t n3 = p->n3();
-  const int r0 = p->nscales;  // the R = 0 multiplier set
+  const int r0 = kMaxScales;  // the R = 0 multiplier set
   ArgsX ax{};
   cudaError_t e = make_tmap_x(&ax.tm, phi, p->nx, p->ny, p->nhp, 1, p->tc_x);
   if (e != cudaSuccess) return e;
@@ -939,14 +1036,14 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
   float2* V0 = spec(p, p->V, 0);
   float* S = reinterpret_cast<float*>(U0);  // nx ny nz floats fit in one padded spectrum
   // 1) the unsmoothed deformation tensor, reduced per particle to the source S
-  st = enqueue_radius(p, p->nscales, 0, nullptr, S);
+  st = enqueue_radius(p, kMaxScales, 0, nullptr, S);
   // 2) T = inverse-sign transform of S: z into V0, y into V1, x into V2; the
   //    R = 0 multipliers scale each y line by 1/ny, each x line by 1/nx and
   //    the y outputs by 1/nz (z factor), so T / (nx ny nz) arrives in V2
   cudaError_t e = cudaSuccess;
   if (st == PIN_OK) e = launch_fwd_z(nz, S, V0, nx * ny, p->nhp, p->twz(), p->stream);
   if (st == PIN_OK && e == cudaSuccess) {
-    const int r0 = p->nscales;
+    const int r0 = kMaxScales;
     ArgsY ay{};
     e = make_tmap_y(&ay.tm, V0, nx, ny, p->nhp, p->field_elems, 1, p->tc_y);
     ay.src[0] = V0;
@@ -1039,7 +1136,7 @@ pin_status pin_profile(pin_plan_t p, int enable) {
   if (want == p->profile) return PIN_OK;
   PIN_CK(p, cudaStreamSynchronize(p->stream));
   if (want && p->events.empty()) {
-    p->events.resize(7 * (size_t)p->nscales, nullptr);
+    p->events.resize(7 * (size_t)kMaxScales, nullptr);
     for (auto& e : p->events) PIN_CK(p, cudaEventCreate(&e));
   }
   p->profile = want;
@@ -1142,6 +1239,37 @@ pin_status pin_pass_times(pin_plan_t p, double* ms4) {
   return PIN_OK;
 }
 
+pin_status pin_set_radii(pin_plan_t p, int nscales, const double* radii) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (nscales < 1 || nscales > kMaxScales) return fail(p, PIN_EINVAL, "nscales must be in 1..64");
+  if (!radii) return fail(p, PIN_EINVAL, "null radii");
+  for (int s = 0; s < nscales; ++s)
+    if (!(radii[s] >= 0.0) || !std::isfinite(radii[s])) return fail(p, PIN_EINVAL, "radii must be finite and >= 0");
+  PIN_CK(p, cudaStreamSynchronize(p->stream));  // no work in flight reads the old tables
+  const std::vector<int> old_order = p->order;
+  p->nscales = nscales;
+  p->radii.assign(radii, radii + nscales);
+  set_order(p);
+  if (p->order != old_order) {
+    // keep the current graph for its order; take a kept one for the new order
+    if (p->graph_exec) {
+      p->graph_cache[old_order] = {p->graph, p->graph_exec};
+      p->graph = nullptr;
+      p->graph_exec = nullptr;
+    }
+    auto it = p->graph_cache.find(p->order);
+    if (it != p->graph_cache.end()) {
+      p->graph = it->second.first;
+      p->graph_exec = it->second.second;
+      p->graph_cache.erase(it);
+    }
+  }
+  const std::vector<float> mult = mult_table(p);
+  PIN_CK(p, cudaMemcpy(p->mult, mult.data(), (size_t)nscales * p->mult_set() * sizeof(float), cudaMemcpyHostToDevice));
+  return PIN_OK;
+}
+
 pin_status pin_set_schedule(pin_plan_t p, int schedule) {
   pin_status st = check_plan(p);
   if (st != PIN_OK) return st;
@@ -1155,7 +1283,7 @@ pin_status pin_set_schedule(pin_plan_t p, int schedule) {
     PIN_CK(p, cudaDeviceGetStreamPriorityRange(&least, &greatest));
     PIN_CK(p, cudaStreamCreateWithPriority(&p->s_xy, cudaStreamNonBlocking, greatest));
     PIN_CK(p, cudaStreamCreateWithPriority(&p->s_z, cudaStreamNonBlocking, least));
-    p->cap_ev.assign(1 + 2 * (size_t)p->nscales, nullptr);
+    p->cap_ev.assign(1 + 2 * (size_t)kMaxScales, nullptr);
     for (auto& e : p->cap_ev) PIN_CK(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   if (schedule == 2 && !p->V2) {

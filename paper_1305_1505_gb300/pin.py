@@ -18,7 +18,7 @@ from . import build as _build
 
 PIN_OK, PIN_EINVAL, PIN_ENOMEM, PIN_ECUDA, PIN_EBUSY, PIN_ETIMEOUT, PIN_ESTATE = range(7)
 PIN_CORR_NONE, PIN_CORR_SPHERE = 0, 1
-PIN_FP32_FALLBACK64 = 0
+PIN_FP32_FALLBACK64, PIN_FP64 = 0, 1
 PIN_C64, PIN_C128 = 0, 1
 PIN_TUNE_FORCE = 1
 
@@ -53,11 +53,12 @@ class pin_stats(ctypes.Structure):
 
 
 # every symbol include/pin.h declares
-EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_hessian",
+EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times", "pin_collapse_times_f64",
+           "pin_hessian",
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
            "pin_fragment_order", "pin_displacements_2lpt", "pin_set_ic_seed", "pin_tile_options",
-           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_noalloc_status", "pin_set_schedule",
+           "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_noalloc_status", "pin_set_radii", "pin_set_schedule",
            "pin_get_schedule", "pin_set_wait_budget",
            "pin_debug_fail_alloc", "pin_strerror", "pin_last_error", "pin_destroy")
 
@@ -83,6 +84,8 @@ def load(path=None):
     L.pin_set_ic.restype = ctypes.c_int
     L.pin_collapse_times.argtypes = [P, P, P, ctypes.c_int]
     L.pin_collapse_times.restype = ctypes.c_int
+    L.pin_collapse_times_f64.argtypes = [P, P, P, ctypes.c_int]
+    L.pin_collapse_times_f64.restype = ctypes.c_int
     L.pin_velocities.argtypes = [P, P, ctypes.c_int]
     L.pin_velocities.restype = ctypes.c_int
     L.pin_fragment_order.argtypes = [P, P, P, ctypes.c_int]
@@ -120,6 +123,8 @@ def load(path=None):
     L.pin_collapse_times_noalloc.restype = ctypes.c_int
     L.pin_noalloc_status.argtypes = [IP, ctypes.POINTER(ctypes.c_uint64)]
     L.pin_noalloc_status.restype = ctypes.c_int
+    L.pin_set_radii.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.pin_set_radii.restype = ctypes.c_int
     L.pin_set_schedule.argtypes = [P, ctypes.c_int]
     L.pin_set_schedule.restype = ctypes.c_int
     L.pin_get_schedule.argtypes = [P]
@@ -161,14 +166,15 @@ def grid_shape(n):
     return nx, ny, nz
 
 
-def make_desc(n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1, velocities=False):
+def make_desc(n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1, velocities=False,
+              precision=PIN_FP32_FALLBACK64):
     """n: the grid side, or (nx, ny, nz) for a non-cubic grid (cubic cells:
     box is the side along x)."""
     r = np.ascontiguousarray(radii, dtype=np.float64)
     nx, ny, nz = grid_shape(n)
     d = pin_plan_desc(nx, ny, nz, float(box), int(r.size),
                       r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(correction),
-                      PIN_FP32_FALLBACK64, ctypes.c_void_p(stream) if stream else None, int(batch),
+                      int(precision), ctypes.c_void_p(stream) if stream else None, int(batch),
                       1 if velocities else 0)
     d._radii_keepalive = r
     return d
@@ -194,6 +200,11 @@ def pin_set_ic(plan, delta_k_ptr, dtype, on_device):
 def pin_collapse_times(plan, fmax_ptr, idx_ptr, on_device):
     _check(load().pin_collapse_times(plan, ctypes.c_void_p(fmax_ptr), ctypes.c_void_p(idx_ptr),
                                      int(on_device)), plan)
+
+
+def pin_collapse_times_f64(plan, fmax_ptr, idx_ptr, on_device):
+    _check(load().pin_collapse_times_f64(plan, ctypes.c_void_p(fmax_ptr), ctypes.c_void_p(idx_ptr),
+                                         int(on_device)), plan)
 
 
 def pin_velocities(plan, out_ptr, on_device):
@@ -303,6 +314,11 @@ def pin_noalloc_status():
     return st, w.value, list(c)
 
 
+def pin_set_radii(plan, radii):
+    r = np.ascontiguousarray(radii, dtype=np.float64)
+    _check(load().pin_set_radii(plan, int(r.size), r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), plan)
+
+
 def pin_set_schedule(plan, schedule):
     """Radius schedule: 0 serial, 1 z(s) beside x(s+1), 2 z(s) beside x and
     y of s+1 (second V buffer)."""
@@ -342,7 +358,7 @@ class Plan:
     """Owns one pin plan; methods take torch tensors (device or host)."""
 
     def __init__(self, n, box, radii, correction=PIN_CORR_SPHERE, stream=None, batch=1,
-                 velocities=False):
+                 velocities=False, precision=PIN_FP32_FALLBACK64):
         """n: grid side, or (nx, ny, nz) for a non-cubic grid with cubic cells
         (box is the side along x)."""
         import torch
@@ -354,7 +370,8 @@ class Plan:
         self.batch = int(batch)
         self.radii = np.ascontiguousarray(radii, dtype=np.float64)
         s = stream.cuda_stream if stream is not None else None
-        self._desc = make_desc(self.shape, self.box, self.radii, correction, s, self.batch, velocities)
+        self._desc = make_desc(self.shape, self.box, self.radii, correction, s, self.batch, velocities,
+                               precision)
         self.handle = pin_plan(self._desc)
 
     def __del__(self):
@@ -388,6 +405,12 @@ class Plan:
         if t.is_cuda:
             self.sync()
 
+    def set_radii(self, radii):
+        """Replaces the radius list (the plan's workspace is kept)."""
+        r = np.ascontiguousarray(radii, dtype=np.float64)
+        pin_set_radii(self.handle, r)
+        self.radii = r
+
     def set_ic_seed(self, seed, ns=0.96, gamma=0.21, sigma8=0.8):
         """delta(k) generated on the device from `seed` (realisation b of a
         batch: seed + b), the seeded field of the input module."""
@@ -411,6 +434,16 @@ class Plan:
         if sync and fmax.is_cuda:
             self.sync()
         return fmax, idx
+
+    def collapse_times_f64(self):
+        """(F_max float64, scale_idx int32) of a PIN_FP64 plan, on the device."""
+        import torch
+        F = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        I = torch.empty(self.shape, dtype=torch.int32, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        pin_collapse_times_f64(self.handle, F.data_ptr(), I.data_ptr(), 1)
+        self.sync()
+        return F, I
 
     def velocities(self):
         """(3, [batch,] n, n, n) displacement at R_max of the last collapse_times."""

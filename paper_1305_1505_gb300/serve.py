@@ -5,9 +5,12 @@ A request asks for the collapse times of one realisation (grid N, box L,
 seed, radii).  The server keeps a FIFO queue; a request is admitted as soon
 as a slot is free and its workspace (pin_footprint_bytes) fits in what is
 left of the memory budget, so requests that arrive while others are running
-start on their own streams and their work overlaps on the device.  Each
-request's delta(k) and running-F state stay on the device from pin_set_ic to
-the end of its radius loop; only F_max and the scale index come back.
+start on their own streams and their work overlaps on the device.  The
+engine runs each request on a pooled plan of its grid size (no device
+allocation, free or graph capture per request once the pool is warm).  Each
+request's delta(k) and running-F state stay on the device from its seeded
+generation to the end of its radius loop; only F_max and the scale index come
+back, into page-locked host memory.
 
 Failures are reported per request, never by a device trap:
   rejected  its footprint exceeds the whole budget (PIN_EBUSY semantics);
@@ -63,68 +66,132 @@ class Request:
         return self.n ** 3 * self.radii.size
 
 
-class PinEngine:
-    """Runs one request on the GPU: a plan on a stream of its own, the x/y
-    tile widths the tuner chose for its grid size (pin_autotune keeps one
-    choice per shape for the process; `warm` makes them before traffic
-    arrives), delta(k) generated on the device from the request's seed
-    (pin_set_ic_seed), the whole radius loop, results copied to the host."""
+class _Slot:
+    """A pooled plan of one grid size with everything a request needs: its
+    stream, device outputs and page-locked host outputs."""
+    __slots__ = ("key", "plan", "stream", "F", "I", "hF", "hI")
 
-    def __init__(self, device=0, priority_from_n=0):
-        """priority_from_n > 0: requests with N at or above it run on a
-        high-priority stream (the device's block scheduler then serves their
-        kernels first), the rest on normal ones."""
+
+class PinEngine:
+    """Runs requests on the GPU from a pool of plans per grid size (and box).
+
+    A request takes an idle plan of its size (a new one is made only when none
+    is idle), switches it to its radii (pin_set_radii: the workspace stays, the
+    graph of a radius count is captured once), generates its delta(k) on the
+    device from its seed (pin_set_ic_seed), runs the whole radius loop and
+    copies F_max and the index into the plan's page-locked host buffers, all on
+    the plan's stream.  After warm-up no request allocates or frees device
+    memory, so no request pays a cudaMalloc, the device-wide synchronisation of
+    a cudaFree, or a graph capture.  The result arrays are views of the plan's
+    host buffers: the plan returns to the pool when the request is released
+    (Request.release, called by the server once the result has been handed on,
+    or by the caller when it keeps the request)."""
+
+    def __init__(self, device=0, priority_from_n=0, pool_per_size=4):
+        """priority_from_n > 0: plans for N at or above it run on high-priority
+        streams (the device's block scheduler then serves their kernels first),
+        the rest on normal ones.  pool_per_size: idle plans kept per size."""
         import torch
         self.torch = torch
         self.device = device
         self.priority_from_n = int(priority_from_n)
+        self.pool_per_size = int(pool_per_size)
+        self.pool = collections.defaultdict(list)
+        self.lock = threading.Lock()
+        self.plans_made = 0
 
-    def warm(self, sizes, box_per_cell=2.0):
-        """Loads the library and tunes the tile widths of each grid size on an
-        idle device (a plan per size, timed alone, then freed)."""
-        self.torch.cuda.set_device(self.device)
+    def _make(self, n, box):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        high = self.priority_from_n > 0 and n >= self.priority_from_n
+        s = _Slot()
+        s.key = (int(n), float(box))
+        s.stream = torch.cuda.Stream(priority=-1 if high else 0)
+        s.plan = pin.Plan(n, box, [8.0, 4.0], stream=s.stream)
+        s.plan.autotune()  # the kept choice for this shape (timed once per process)
+        s.F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        s.I = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
+        s.hF = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+        s.hI = torch.empty((n, n, n), dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        with self.lock:
+            self.plans_made += 1
+        return s
+
+    def warm(self, sizes, box_per_cell=2.0, per_size=1):
+        """Loads the library, tunes the tile widths of each grid size on an
+        idle device and fills the pool with per_size plans of each size.
+        Returns the tile widths per size."""
         out = {}
         for n in sizes:
-            plan = pin.Plan(n, box_per_cell * n, [8.0, 4.0])
-            try:
-                out[int(n)] = plan.autotune(reps=3)
-            finally:
-                plan.close()
+            slots = [self._make(n, box_per_cell * n) for _ in range(per_size)]
+            out[int(n)] = slots[0].plan.tiles()
+            for s in slots:
+                self._release(s)
         return out
+
+    def _acquire(self, n, box):
+        with self.lock:
+            idle = self.pool[(int(n), float(box))]
+            if idle:
+                return idle.pop()
+        return self._make(n, box)
+
+    def _release(self, slot):
+        with self.lock:
+            idle = self.pool[slot.key]
+            if len(idle) < self.pool_per_size:
+                idle.append(slot)
+                return
+        slot.plan.close()
+
+    def close(self):
+        with self.lock:
+            slots = [s for v in self.pool.values() for s in v]
+            self.pool.clear()
+        for s in slots:
+            s.plan.close()
 
     def footprint(self, req):
         return pin.pin_footprint_bytes(pin.make_desc(req.n, req.box, req.radii))
 
     def run(self, req, timeout_s=None):
+        """Returns (F_max, scale_idx, release): numpy views of the plan's host
+        buffers and the callable that hands the plan back to the pool."""
         torch = self.torch
         torch.cuda.set_device(self.device)
-        high = self.priority_from_n > 0 and req.n >= self.priority_from_n
-        stream = torch.cuda.Stream(priority=-1 if high else 0)
-        plan = pin.Plan(req.n, req.box, req.radii, stream=stream)
+        slot = self._acquire(req.n, req.box)
+        ok = False
         try:
-            plan.autotune()  # the kept choice for this shape (timed once per process)
-            n = req.n
-            F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
-            I = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
-            torch.cuda.current_stream().synchronize()
+            plan = slot.plan
+            plan.set_radii(req.radii)
             pin.pin_set_ic_seed(plan.handle, req.seed)
-            pin.pin_collapse_times(plan.handle, F.data_ptr(), I.data_ptr(), 1)
+            pin.pin_collapse_times(plan.handle, slot.F.data_ptr(), slot.I.data_ptr(), 1)
+            with torch.cuda.stream(slot.stream):  # after the radius loop, on the plan's stream
+                slot.hF.copy_(slot.F, non_blocking=True)
+                slot.hI.copy_(slot.I, non_blocking=True)
             st = pin.pin_sync(plan.handle, -1 if timeout_s is None else int(timeout_s * 1e9))
             if st == pin.PIN_ETIMEOUT:
-                plan.sync()  # the device work cannot be cancelled: drain before freeing
+                plan.sync()  # the device work cannot be cancelled: drain before reuse
                 raise TimeoutError("device work exceeded the request deadline")
             pin._check(st, plan.handle)
-            return F.cpu().numpy(), I.cpu().numpy()
+            ok = True
+            return slot.hF.numpy(), slot.hI.numpy(), (lambda: self._release(slot))
         finally:
-            plan.close()
+            if not ok:
+                self._release(slot)
 
 
 class Server:
     """FIFO admission by memory footprint and slot count; one worker thread
     per admitted request."""
 
-    def __init__(self, engine, budget_bytes, max_slots=4):
+    def __init__(self, engine, budget_bytes, max_slots=4, keep_results=True):
+        """keep_results: copy each result into arrays of the request (False:
+        drop it; latency is measured to the result's arrival in host memory
+        either way)."""
         self.engine = engine
+        self.keep_results = bool(keep_results)
         self.budget = int(budget_bytes)
         self.max_slots = int(max_slots)
         self.queue = collections.deque()
@@ -187,17 +254,28 @@ class Server:
         remaining = None
         if req.deadline is not None:
             remaining = max(0.0, req.deadline - (time.perf_counter() - req.arrival))
+        release = None
+        t_done = None
         try:
             res = self.engine.run(req, remaining)
+            t_done = time.perf_counter()
+            if isinstance(res, tuple) and len(res) == 3 and callable(res[2]):
+                res, release = res[:2], res[2]  # views of a pooled plan's buffers
+                res = tuple(np.array(a) for a in res) if self.keep_results else None
             status, err = "done", None
         except TimeoutError as e:
             res, status, err = None, "timeout", str(e)
         except Exception as e:  # reported per request
             res, status, err = None, "failed", "%s: %s" % (type(e).__name__, e)
+        finally:
+            if release is not None:
+                release()
         with self.lock:
             self.in_use -= req.footprint
             self.running -= 1
             self._finish(req, status, res, err)
+            if t_done is not None:
+                req.t_done = t_done
             self.lock.notify_all()
 
     def drain(self, timeout=None):
@@ -264,10 +342,47 @@ def replay(server_factory, stream, realtime=True):
     return reqs, wall, srv
 
 
-def main():
+def measure_serving(requests=600, rate=2.0, seed=5, slots=4, budget_bytes=0, priority_from_n=0,
+                    stress_rate=0.0):
+    """The mixed request stream served with `slots` concurrent requests and
+    one at a time, on the same engine and plan pool; latency p50/p99 and
+    throughput of both (a dict).  budget_bytes 0: 80 % of free device memory."""
     import torch
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(budget_bytes) if budget_bytes > 0 else int(0.8 * free)
+    eng = PinEngine(priority_from_n=priority_from_n, pool_per_size=slots)
+    sizes = [64, 128, 256, 512]
+    tiles = eng.warm(sizes, per_size=slots)
+    for n in sizes:  # first launch of each size, outside the measurement
+        _, _, rel = eng.run(Request(-1, n, 2.0 * n, 1, [8.0, 4.0]))
+        rel()
+    made0 = eng.plans_made
+
+    def one(rate_):
+        stream = workload(requests, seed, rate_)
+        served, wall_s, srv = replay(lambda: Server(eng, budget, slots, keep_results=False), stream)
+        plain, wall_p, _ = replay(lambda: Server(eng, budget, 1, keep_results=False), stream)
+        return {"rate_per_s": rate_,
+                "served": dict(_stats(served, wall_s), slots=slots, peak_running=srv.peak_running,
+                               budget_bytes=budget),
+                "plain_one_at_a_time": _stats(plain, wall_p)}
+
+    out = {"metric": "served collapse-time requests: latency p50/p99 and throughput",
+           "workload": "%d requests, Poisson arrivals (mean %g/s), N in {64,128,256,512} (.4/.3/.2/.1), "
+                       "box 2 Mpc/h per cell, 20-40 radii 40->2 Mpc/h, seed %d" % (requests, rate, seed),
+           "tiles": {str(k): list(v) for k, v in tiles.items()},
+           "priority_from_n": priority_from_n,
+           "nominal": one(rate)}
+    if stress_rate > 0:
+        out["stress"] = one(stress_rate)
+    out["plans_made_during_traffic"] = eng.plans_made - made0
+    eng.close()
+    return out
+
+
+def main():
     ap = argparse.ArgumentParser(description="serve a Poisson stream of mixed collapse-time requests")
-    ap.add_argument("--requests", type=int, default=120)
+    ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--rate", type=float, default=2.0, help="mean arrivals per second")
     ap.add_argument("--stress-rate", type=float, default=0.0,
                     help="also replay the same mix at this rate (0: skip), to load the device")
@@ -277,29 +392,8 @@ def main():
     ap.add_argument("--priority-from-n", type=int, default=0,
                     help="grid size from which requests run on a high-priority stream (0: none)")
     args = ap.parse_args()
-    free, _ = torch.cuda.mem_get_info()
-    budget = int(args.budget_gb * 2 ** 30) if args.budget_gb > 0 else int(0.8 * free)
-    eng = PinEngine(priority_from_n=args.priority_from_n)
-    tiles = eng.warm([64, 128, 256, 512])
-    eng.run(Request(-1, 64, 128.0, 1, [8.0, 4.0]))  # warm up
-    def measure(rate):
-        stream = workload(args.requests, args.seed, rate)
-        served, wall_s, srv = replay(lambda: Server(eng, budget, args.slots), stream)
-        plain, wall_p, _ = replay(lambda: Server(eng, budget, 1), stream)
-        return {"rate_per_s": rate,
-                "served": dict(_stats(served, wall_s), slots=args.slots,
-                               peak_running=srv.peak_running, budget_bytes=budget),
-                "plain_one_at_a_time": _stats(plain, wall_p)}
-
-    line = {"metric": "served collapse-time requests: latency p50/p99 and throughput",
-            "workload": "%d requests, Poisson arrivals, N in {64,128,256,512} (.4/.3/.2/.1), "
-                        "box 2 Mpc/h per cell, 20-40 radii 40->2 Mpc/h, seed %d"
-                        % (args.requests, args.seed),
-            "tiles": {str(k): list(v) for k, v in tiles.items()},
-            "priority_from_n": args.priority_from_n,
-            "nominal": measure(args.rate)}
-    if args.stress_rate > 0:
-        line["stress"] = measure(args.stress_rate)
+    line = measure_serving(args.requests, args.rate, args.seed, args.slots, int(args.budget_gb * 2 ** 30),
+                           args.priority_from_n, args.stress_rate)
     print(json.dumps(line), flush=True)
 
 

@@ -43,18 +43,18 @@ def inputs(n, box, seed):
     return d32, d32.astype(np.complex128)
 
 
-def tolerance(f_or, rms):
-    return REL * np.abs(f_or) + ABS_FRAC * rms
+def tolerance(f_or, rms, rel=REL, abs_frac=ABS_FRAC):
+    return rel * np.abs(f_or) + abs_frac * rms
 
 
-def classify(F_gpu, idx_gpu, F_or, idx_or, f2=None, idx2=None, f_all=None):
+def classify(F_gpu, idx_gpu, F_or, idx_or, f2=None, idx2=None, f_all=None, rel=REL, abs_frac=ABS_FRAC):
     """Returns (bad_mask, report) under the F and index rules."""
     F_gpu = np.asarray(F_gpu, dtype=np.float64).ravel()
     idx_gpu = np.asarray(idx_gpu).ravel()
     F_or = np.asarray(F_or, dtype=np.float64).ravel()
     idx_or = np.asarray(idx_or).ravel()
     rms = float(np.sqrt(np.mean(F_or ** 2))) if F_or.size else 0.0
-    tol = tolerance(F_or, rms)
+    tol = tolerance(F_or, rms, rel, abs_frac)
     err = np.abs(F_gpu - F_or)
     f_bad = err > tol
     mism = idx_gpu != idx_or
@@ -92,29 +92,32 @@ def within_conditioning(F_gpu, I_gpu, lo, hi, tol):
     return ok & np.where(I_gpu >= 0, at_i, never)
 
 
-def conditioned(q_bad, F_gpu, I_gpu, d64, box, radii, hrms, correction, tol):
+def conditioned(q_bad, F_gpu, I_gpu, d64, box, radii, hrms, correction, tol, u=U_FP32):
     """Oracle-side conditioning of the particles q_bad: (ok mask, lo, hi)."""
     import oracle
     h = oracle.hessians_at(d64, box, radii, q_bad)
-    lo, hi = oracle.collapse_interval(h, hrms, U_FP32, correction)
+    lo, hi = oracle.collapse_interval(h, hrms, u, correction)
     return within_conditioning(F_gpu, I_gpu, lo, hi, tol), lo, hi
 
 
-def assert_parity(F, I, orc, d64, box, radii, correction=1, label=""):
+def assert_parity(F, I, orc, d64, box, radii, correction=1, label="", rel=REL, abs_frac=ABS_FRAC, u=U_FP32):
     """The whole rule: every particle within the F tolerance with an equal or
     near-tie index, or (at most 1e-4 of the grid) ill-conditioned by the
     oracle's own measure with the GPU's result inside the oracle's range; the
     index equal on >= 99.99 % of particles.  d64, box, radii and correction
-    are the oracle's inputs of this run; orc its collapse_times result."""
+    are the oracle's inputs of this run; orc its collapse_times result.
+    rel, abs_frac and u set the tolerance and the conditioning half-width
+    (the FP32 path's by default)."""
     F = np.asarray(F).ravel()
     I = np.asarray(I).ravel()
-    bad, rep = classify(F, I, orc["fmax"], orc["idx"], orc.get("f2"), orc.get("idx2"), orc.get("f_all"))
+    bad, rep = classify(F, I, orc["fmax"], orc["idx"], orc.get("f2"), orc.get("idx2"), orc.get("f_all"),
+                        rel, abs_frac)
     bq = np.nonzero(bad)[0]
     rep["conditioned"] = int(bq.size)
     print("parity %s:" % label, rep)
     if bq.size:
-        tol = tolerance(orc["fmax"][bq], rep["rms"])
-        ok, lo, hi = conditioned(bq, F[bq], I[bq], d64, box, radii, orc["hrms"], correction, tol)
+        tol = tolerance(orc["fmax"][bq], rep["rms"], rel, abs_frac)
+        ok, lo, hi = conditioned(bq, F[bq], I[bq], d64, box, radii, orc["hrms"], correction, tol, u)
         for j, q in enumerate(bq):
             print("  conditioned q=%d: gpu F=%.7g idx=%d, oracle F=%.7g idx=%d, range [%.7g, %.7g] %s"
                   % (q, F[q], I[q], orc["fmax"][q], orc["idx"][q], lo[:, j].max(), hi[:, j].max(),

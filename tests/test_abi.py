@@ -106,8 +106,14 @@ def test_more_validation_and_footprint_without_gpu():
     d.velocities = 2
     assert fp(d) == 0
     d = pin.make_desc(64, 100.0, [1.0])
-    d.precision = 1
+    d.precision = 2
     assert fp(d) == 0
+    # PIN_FP64 adds its FP64 workspace: half-spectrum 16 B, complex cube 16 B,
+    # tensor 48 B and F_max 8 B per mode / particle; batch 1 only
+    d = pin.make_desc(64, 100.0, [1.0], precision=pin.PIN_FP64)
+    extra = fp(d) - fp(pin.make_desc(64, 100.0, [1.0]))
+    assert extra == 64 * 64 * 33 * 16 + 64 ** 3 * (16 + 48 + 8)
+    assert fp(pin.make_desc(64, 100.0, [1.0], precision=pin.PIN_FP64, batch=2)) == 0
     d = pin.make_desc(64, 100.0, [1.0])
     d.radii = None
     assert fp(d) == 0

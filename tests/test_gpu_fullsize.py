@@ -2,7 +2,9 @@
 configuration, and the 384^3 grid with the same 4 Mpc/h cells (the other
 three-level transform size), checked where the oracle can follow them:
  - the deformation tensor at sampled grid points against the oracle's direct
-   sum over every mode (one radius), and the trace rule over the whole grid;
+   sum over every mode (one radius), and the trace rule over the whole grid
+   (phi_xx + phi_yy + phi_zz against the smoothed density IDFT(W delta) from
+   cuFFT in FP64, the checker only);
  - F_max and the scale index at 1e5 sampled particles against the oracle's
    eigenvalues and collapse times computed from the GPU's FP32 Hessians of
    those particles at all 40 radii."""
@@ -45,6 +47,20 @@ def test_hessian_points_against_direct_sum(run):
     assert np.abs(got - ref).max() < 2e-5 * rms
     tr = (h[0] + h[1] + h[2]).double()
     assert abs(float(tr.mean())) < 1e-6 * float(tr.std())  # zero mode removed
+    # trace rule at every grid point: the trace of the filtered tensor is the
+    # smoothed density (k_i k_i / k^2 = 1 for k != 0; diagonal components keep
+    # their Nyquist modes), here from cuFFT in FP64
+    import torch
+    from tests.test_gpu_cufft import _wavenumbers
+    del h
+    d = torch.from_numpy(d32).cuda().to(torch.complex128)
+    ks, _ = _wavenumbers((N, N, N), BOX)
+    k2 = ks[0] ** 2 + ks[1] ** 2 + ks[2] ** 2
+    w = torch.where(k2 == 0, torch.zeros_like(k2), torch.exp(-0.5 * k2 * radii[s] ** 2))
+    ref_tr = torch.fft.irfftn(w * d, s=(N, N, N)).reshape(-1)
+    del d, w, k2
+    err = float((tr - ref_tr).abs().max())
+    assert err < 1e-5 * float(ref_tr.std()), err
 
 
 def test_collapse_sampled_particles(run):

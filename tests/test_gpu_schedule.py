@@ -45,3 +45,36 @@ def test_overlapped_schedule_needs_a_fused_z_pass():
     assert e.value.status == pin.PIN_EINVAL
     assert pin.pin_get_schedule(plan.handle) == 0
     plan.close()
+
+
+def test_set_radii_matches_fresh_plans():
+    """pin_set_radii: one plan serves radius lists of other lengths and values
+    (its graphs are kept per radius count) with the results of a plan made for
+    each list, bit for bit."""
+    import torch
+    from paper_1305_1505_gb300 import pin
+    n, box = 64, 128.0
+    d32, _ = parity.inputs(n, box, 17)
+    lists = [ic.log_radii(2.0, 30.0, 6), ic.log_radii(3.0, 20.0, 9), ic.log_radii(2.5, 25.0, 6)]
+    fresh = []
+    for radii in lists:
+        p = pin.Plan(n, box, radii)
+        p.set_ic(torch.from_numpy(d32).cuda())
+        F, I = p.collapse_times()
+        fresh.append((F.clone(), I.clone()))
+        p.close()
+    plan = pin.Plan(n, box, lists[0])
+    plan.set_ic(torch.from_numpy(d32).cuda())
+    for k in (0, 1, 2, 1, 0):
+        plan.set_radii(lists[k])
+        F, I = plan.collapse_times()
+        assert torch.equal(F, fresh[k][0]) and torch.equal(I, fresh[k][1]), k
+        h = plan.hessian(len(lists[k]) - 1)  # the scale index refers to the new list
+        assert h.shape[0] == 6
+    with pytest.raises(pin.PinError) as e:
+        plan.set_radii(np.full(65, 2.0))
+    assert e.value.status == pin.PIN_EINVAL
+    with pytest.raises(pin.PinError) as e:
+        plan.set_radii([2.0, -1.0])
+    assert e.value.status == pin.PIN_EINVAL
+    plan.close()
