@@ -281,7 +281,7 @@ def measure_config(c, steps, warmup, tune=True):
                        % (n, c["box"], c["seed"], S, c["r_max"], c["r_min"]),
            "value": n ** 3 * S / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
            "best_ms_per_step": min(evs[i].elapsed_time(evs[i + 1]) for i in range(steps)),
-           "tiles": {"x": tiles[0], "y": tiles[1]},
+           "tiles": {"x": tiles[0], "y": tiles[1], "radix_x": plan.radix()[0], "radix_y": plan.radix()[1]},
            "step_alg_bytes_per_update": step_bytes / (n ** 3 * S),
            "step_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak, "hbm_peak_kind": peak_kind,
            "gpu_launches": int(steps * pin.pin_kernels_per_call(plan.handle))}
@@ -489,6 +489,7 @@ def run_ours(args):
     stats = plan.stats()
     kernels_per_call = pin.pin_kernels_per_call(plan.handle)
     pin_schedule = pin.pin_get_schedule(plan.handle)
+    radix = plan.radix()
 
     # roofline of the dominant pass (algorithmic bytes per launch, one launch per radius)
     fused = kernels_per_call == 4 * S
@@ -528,7 +529,10 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(_config(w), velocities=bool(args.velocities),
-                           tiles={"x": tiles[0], "y": tiles[1], "tuned": not (args.no_tune or args.tiles)},
+                           tiles={"x": tiles[0], "y": tiles[1], "radix_x": radix[0], "radix_y": radix[1],
+                                  "radix_shapes": {"x": pin.pin_radix_shape(n, radix[0]),
+                                                   "y": pin.pin_radix_shape(n, radix[1])},
+                                  "tuned": not (args.no_tune or args.tiles)},
                            schedule=pin_schedule),
             "roofline": dict(roofline(names[dom], per_launch_ms[dom], n, bool(args.velocities), fused,
                                       achieved, peak, peak_kind, clocks, passes), step=whole_step),

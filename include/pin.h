@@ -107,9 +107,11 @@ size_t pin_footprint_bytes(const pin_plan_desc* d);
 /* Loads the linear density field delta(k) (Sec. 2.1.1, Eq. "deltal"), a
  * half-spectrum as described above (B of them back to back for a batch), dtype PIN_C64 (interleaved float) or
  * PIN_C128 (interleaved double, rounded to FP32 on the device), from host
- * memory (on_device = 0) or device memory (on_device = 1).  The data are
- * copied; the caller may reuse its buffer when the call returns (host input)
- * or once the plan's stream has passed this point (device input). */
+ * memory (on_device = 0) or device memory (on_device = 1).  Page-locked host
+ * input is read in place by the device (no staging copy); other host memory
+ * is copied in first.  The data are copied; the caller may reuse its buffer
+ * when the call returns (host input) or once the plan's stream has passed
+ * this point (device input). */
 pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_device);
 
 /* Generates delta(k) on the device from a seed instead of loading it: the
@@ -131,7 +133,8 @@ pin_status pin_set_ic_seed(pin_plan_t p, uint64_t seed, const pin_spectrum* ps);
  *                index on exact ties), -1 if never collapses.
  * on_device = 1: both are device pointers; the call only enqueues work and
  * returns (use pin_sync or the stream).  on_device = 0: host pointers; the
- * call returns when the results are in host memory. */
+ * call returns when the results are in host memory (page-locked host memory
+ * is written by the device through its mapping, other host memory by a copy). */
 pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, int on_device);
 
 /* pin_collapse_times of a PIN_FP64 plan with F_max in double precision
@@ -217,31 +220,48 @@ int pin_kernels_per_call(pin_plan_t p);
 pin_status pin_profile(pin_plan_t p, int enable);
 pin_status pin_pass_times(pin_plan_t p, double* ms4);
 
-/* Tile schedule of the x and y passes (the paper has no counterpart: its FFTs
- * are FFTW's).  Each of those passes transforms blocks of tc columns of the
- * spectrum at a time; every width computes each column's line transform with
- * the same arithmetic, so the choice changes timings, never results.
+/* Tile and radix schedules of the x and y passes (the paper has no
+ * counterpart: its FFTs are FFTW's).  Each of those passes transforms blocks
+ * of tc columns of the spectrum at a time, every line by a decomposition of
+ * its length n = E x P (E values per thread, P threads per line; P = P1 x P2,
+ * a second shared-memory exchange when P2 > 1).  Each length has
+ * pin_radix_schedules() such decompositions ("radix schedules"); schedule 0
+ * is the default and the z pass's.  Every tile width computes each column's
+ * line transform with the same arithmetic, so the tile width changes timings,
+ * never results; the radix schedule changes the order of the arithmetic, so
+ * results differ in the last bits (both are checked against the oracle).
  *
- * pin_tile_options: the widths a pass over lines of n points can run, the
- * default first, into opts[0 .. *count - 1] (*count <= 2); PIN_EINVAL for an
- * unsupported n.
+ * pin_tile_options: the widths a pass over lines of n points can run with
+ * radix schedule 0, the default first, into opts[0 .. *count - 1]
+ * (*count <= 2); pin_tile_options_radix: the same for schedule `radix`.
+ * PIN_EINVAL for an unsupported n or schedule.
+ * pin_radix_shape: E, P1, P2 of schedule `radix` for lines of n points.
  * pin_get_tiles / pin_set_tiles: the widths the plan runs for its x pass
- * (lines of nx points) and y pass (ny points); 0 selects the default, any
- * other value must be one of pin_tile_options (else PIN_EINVAL, plan
- * unchanged).  Setting waits for the plan's stream.
- * pin_autotune: times every candidate width of the x pass and of the y pass
- * on the plan's own buffers (reps launches each, 1..1000, after one untimed
- * launch; the first radius, the plan's mode) and keeps the fastest of each.
- * Only the plan's workspaces are written (Phi0 is zeroed first if no field
- * is set); F_max, the scale index and v_max are untouched.  Choices are kept
- * per (device, nx, ny, nz, batch, velocities) for the process: a later call
- * for the same shape applies the kept choice without timing unless flags has
- * PIN_TUNE_FORCE.  The chosen widths go to *tc_x and *tc_y (either may be
- * NULL).  PIN_ESTATE while the plan's stream is being captured. */
+ * (lines of nx points) and y pass (ny points); 0 selects the default of the
+ * plan's radix schedule, any other value must be one of its options (else
+ * PIN_EINVAL, plan unchanged).  Setting waits for the plan's stream.
+ * pin_get_radix / pin_set_radix: the radix schedules of the plan's x and y
+ * passes (set: waits for the plan's stream, keeps the tile widths where the
+ * new schedules run them, else their defaults).
+ * pin_autotune: times every (radix schedule, tile width) candidate of the x
+ * pass and of the y pass on the plan's own buffers (reps launches each,
+ * 1..1000, after one untimed launch; the first radius, the plan's mode) and
+ * keeps the fastest of each.  Only the plan's workspaces are written (Phi0 is
+ * zeroed first if no field is set); F_max, the scale index and v_max are
+ * untouched.  Choices are kept per (device, nx, ny, nz, batch, velocities)
+ * for the process: a later call for the same shape applies the kept choice
+ * without timing unless flags has PIN_TUNE_FORCE.  The chosen widths go to
+ * *tc_x and *tc_y (either may be NULL; pin_get_radix gives the schedules).
+ * PIN_ESTATE while the plan's stream is being captured. */
 #define PIN_TUNE_FORCE 1
 pin_status pin_tile_options(int n, int* opts, int* count);
+pin_status pin_tile_options_radix(int n, int radix, int* opts, int* count);
+int pin_radix_schedules(void);
+pin_status pin_radix_shape(int n, int radix, int* E, int* P1, int* P2);
 pin_status pin_get_tiles(pin_plan_t p, int* tc_x, int* tc_y);
 pin_status pin_set_tiles(pin_plan_t p, int tc_x, int tc_y);
+pin_status pin_get_radix(pin_plan_t p, int* vx, int* vy);
+pin_status pin_set_radix(pin_plan_t p, int vx, int vy);
 pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y);
 
 /* Replaces the plan's radius list (1..64 radii, as in pin_plan_desc) without

@@ -38,16 +38,31 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // exp(+2 pi i j / n) for the register-DFT sizes, filled once per device from
-// double precision host values (pin.cu).  Indices are compile-time constants
-// after unrolling, so every read is a constant-bank operand.
+// double precision host values.  Indices are compile-time constants after
+// unrolling, so every read is a constant-bank operand.
 constexpr int kTwSizes[] = {4, 8, 12, 16, 24, 32, 48, 64};
 constexpr int kTwTotal = 4 + 8 + 12 + 16 + 24 + 32 + 48 + 64;
 __host__ __device__ constexpr int tw_offset(int n) {
   return n == 4 ? 0 : n == 8 ? 4 : n == 12 ? 12 : n == 16 ? 24 : n == 24 ? 40
        : n == 32 ? 64 : n == 48 ? 96 : n == 64 ? 144 : -1;
 }
-// Defined here (one translation unit includes this header).
+// Defined here: every translation unit that includes this header has a copy
+// of its own (separate device code), which that unit fills with
+// upload_tw_table_here (kernels.cu and kernels_v1.cu, through
+// upload_constant_twiddles).
 __constant__ float2 c_tw[kTwTotal];
+
+static inline cudaError_t upload_tw_table_here() {
+  float2 h[kTwTotal];
+  for (int n : kTwSizes) {
+    const int off = tw_offset(n);
+    for (int j = 0; j < n; ++j) {
+      const double ang = 2.0 * 3.14159265358979323846 * (double)j / (double)n;
+      h[off + j] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+  }
+  return cudaMemcpyToSymbol(c_tw, h, sizeof(h));
+}
 
 template <int N>
 __device__ __forceinline__ float2 twc(int j) {
@@ -142,29 +157,45 @@ template <int N> struct DFT {
 // P = P1 * P2): the length-P transforms are themselves split into a length-P2
 // stage and a length-P1 stage with a second exchange, so that E, and with it
 // the registers a thread holds, stays small (P1 and P2 divide E).
-template <int N> struct ShapeBase;
-template <> struct ShapeBase<8>    { static constexpr int E = 8,  P1 = 1, P2 = 1; };
-template <> struct ShapeBase<16>   { static constexpr int E = 16, P1 = 1, P2 = 1; };
-template <> struct ShapeBase<32>   { static constexpr int E = 8,  P1 = 4, P2 = 1; };
-template <> struct ShapeBase<48>   { static constexpr int E = 12, P1 = 4, P2 = 1; };
-template <> struct ShapeBase<64>   { static constexpr int E = 8,  P1 = 8, P2 = 1; };
-template <> struct ShapeBase<96>   { static constexpr int E = 24, P1 = 4, P2 = 1; };
-template <> struct ShapeBase<128>  { static constexpr int E = 16, P1 = 8, P2 = 1; };
-template <> struct ShapeBase<192>  { static constexpr int E = 24, P1 = 8, P2 = 1; };
-template <> struct ShapeBase<256>  { static constexpr int E = 16, P1 = 16, P2 = 1; };
+// Each size has two radix schedules: V = 0 (the default of every pass) and
+// V = 1, another split of the same length that the x and y passes can run
+// (pin_autotune times both); the z pass always runs V = 0.
+template <int N, int V = 0> struct ShapeBase;
+template <> struct ShapeBase<8, 0>    { static constexpr int E = 8,  P1 = 1, P2 = 1; };
+template <> struct ShapeBase<16, 0>   { static constexpr int E = 16, P1 = 1, P2 = 1; };
+template <> struct ShapeBase<32, 0>   { static constexpr int E = 8,  P1 = 4, P2 = 1; };
+template <> struct ShapeBase<48, 0>   { static constexpr int E = 12, P1 = 4, P2 = 1; };
+template <> struct ShapeBase<64, 0>   { static constexpr int E = 8,  P1 = 8, P2 = 1; };
+template <> struct ShapeBase<96, 0>   { static constexpr int E = 24, P1 = 4, P2 = 1; };
+template <> struct ShapeBase<128, 0>  { static constexpr int E = 16, P1 = 8, P2 = 1; };
+template <> struct ShapeBase<192, 0>  { static constexpr int E = 24, P1 = 8, P2 = 1; };
+template <> struct ShapeBase<256, 0>  { static constexpr int E = 16, P1 = 16, P2 = 1; };
 #ifndef PIN_384_TWO_LEVEL
-template <> struct ShapeBase<384>  { static constexpr int E = 24, P1 = 4, P2 = 4; };
+template <> struct ShapeBase<384, 0>  { static constexpr int E = 24, P1 = 4, P2 = 4; };
 #else
-template <> struct ShapeBase<384>  { static constexpr int E = 48, P1 = 8, P2 = 1; };
+template <> struct ShapeBase<384, 0>  { static constexpr int E = 48, P1 = 8, P2 = 1; };
 #endif
-template <> struct ShapeBase<512>  { static constexpr int E = 32, P1 = 16, P2 = 1; };
+template <> struct ShapeBase<512, 0>  { static constexpr int E = 32, P1 = 16, P2 = 1; };
 #ifndef PIN_768_TWO_LEVEL
-template <> struct ShapeBase<768>  { static constexpr int E = 24, P1 = 4, P2 = 8; };
+template <> struct ShapeBase<768, 0>  { static constexpr int E = 24, P1 = 4, P2 = 8; };
 #else
-template <> struct ShapeBase<768>  { static constexpr int E = 48, P1 = 16, P2 = 1; };
+template <> struct ShapeBase<768, 0>  { static constexpr int E = 48, P1 = 16, P2 = 1; };
 #endif
-template <int N> struct Shape : ShapeBase<N> {
-  static constexpr int E = ShapeBase<N>::E, P1 = ShapeBase<N>::P1, P2 = ShapeBase<N>::P2;
+// the alternative schedules
+template <> struct ShapeBase<8, 1>    { static constexpr int E = 4,  P1 = 2, P2 = 1; };
+template <> struct ShapeBase<16, 1>   { static constexpr int E = 4,  P1 = 4, P2 = 1; };
+template <> struct ShapeBase<32, 1>   { static constexpr int E = 16, P1 = 2, P2 = 1; };
+template <> struct ShapeBase<48, 1>   { static constexpr int E = 24, P1 = 2, P2 = 1; };
+template <> struct ShapeBase<64, 1>   { static constexpr int E = 16, P1 = 4, P2 = 1; };
+template <> struct ShapeBase<96, 1>   { static constexpr int E = 12, P1 = 4, P2 = 2; };
+template <> struct ShapeBase<128, 1>  { static constexpr int E = 8,  P1 = 4, P2 = 4; };
+template <> struct ShapeBase<192, 1>  { static constexpr int E = 12, P1 = 4, P2 = 4; };
+template <> struct ShapeBase<256, 1>  { static constexpr int E = 16, P1 = 4, P2 = 4; };
+template <> struct ShapeBase<384, 1>  { static constexpr int E = 24, P1 = 8, P2 = 2; };
+template <> struct ShapeBase<512, 1>  { static constexpr int E = 32, P1 = 4, P2 = 4; };
+template <> struct ShapeBase<768, 1>  { static constexpr int E = 24, P1 = 8, P2 = 4; };
+template <int N, int V = 0> struct Shape : ShapeBase<N, V> {
+  static constexpr int E = ShapeBase<N, V>::E, P1 = ShapeBase<N, V>::P1, P2 = ShapeBase<N, V>::P2;
   static constexpr int P = P1 * P2;
   // twiddles: w_N^{p k1} ([k1][p], E*P = N entries), then for three levels
   // w_P^{p1 k2a} ([k2a][p1], P entries)
@@ -238,10 +269,11 @@ __device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { retur
 // s_x again).  WARP: every transform is held within one warp (P divides 32,
 // transform c on threads [c P, c P + P)) with an exchange region of its own,
 // so those synchronisations are warp-level.
-template <int N, class Layout, bool WARP = false>
-__device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c, float2* s_x,
+template <int N, class Layout, bool WARP = false, int V = 0>
+__device__ __forceinline__ void fft_line(float2 (&v)[Shape<N, V>::E], int p, int c, float2* s_x,
                                          const float2* s_tw) {
-  constexpr int E = Shape<N>::E, P = Shape<N>::P, P1 = Shape<N>::P1, P2 = Shape<N>::P2;
+  using S = Shape<N, V>;
+  constexpr int E = S::E, P = S::P, P1 = S::P1, P2 = S::P2;
   static_assert(!WARP || 32 % P == 0, "warp-level exchanges need whole transforms per warp");
   auto sync = [] {
     if constexpr (WARP) __syncwarp();
@@ -311,9 +343,10 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N>::E], int p, int c,
 }
 
 // Output frequency of register slot j after fft_line.
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ int fft_out_index(int p, int j) {
-  constexpr int E = Shape<N>::E, P = Shape<N>::P, P1 = Shape<N>::P1, P2 = Shape<N>::P2;
+  using S = Shape<N, V>;
+  constexpr int E = S::E, P = S::P, P1 = S::P1, P2 = S::P2;
   if constexpr (P2 > 1) {
     const int m = j / P1, k2b = j % P1;
     const int pi = p + P * m;

@@ -127,16 +127,29 @@ struct PassShape {
 cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int nhp, int batch, int tc);
 cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int nx, int ny, int nhp, size_t spec_elems,
                         int batch, int tc);
-// Tile widths the x/y pass over lines of n points can run (opts[0] is the
-// default); returns their number (0 for an unsupported size).
-int xy_tile_options(int n, int* opts);
+// Radix schedules of the x/y line transforms (fft.cuh ShapeBase<N, V>):
+// 0, the default and the z pass's, and 1.
+constexpr int kRadixVariants = 2;
+// Tile widths the x/y pass over lines of n points can run with radix
+// schedule v (opts[0] is the default); returns their number (0 for an
+// unsupported size or schedule).
+int xy_tile_options(int n, int v, int* opts);
 
 bool size_supported(int n);
-PassShape pass_shape(int n);
+PassShape pass_shape(int n);          // schedule 0: z pass, and the x/y defaults
+PassShape pass_shape_xy(int n, int v);  // the x/y line transform of schedule v
 cudaError_t prepare_kernels(int n);  // sets shared-memory attributes (once per device)
-// tc: tile width, one of xy_tile_options(n) (anything else runs the default)
-cudaError_t launch_x(int n, int tc, const ArgsX& a, cudaStream_t st);
-cudaError_t launch_y(int n, int tc, const ArgsY& a, cudaStream_t st);
+// tc: tile width, one of xy_tile_options(n, v) (anything else runs the
+// default of schedule v); v: radix schedule
+cudaError_t launch_x(int n, int tc, int v, const ArgsX& a, cudaStream_t st);
+cudaError_t launch_y(int n, int tc, int v, const ArgsY& a, cudaStream_t st);
+// schedule 1 (kernels_v1.cu)
+cudaError_t upload_constant_twiddles_v1();  // that unit's copy of the register-DFT twiddles
+cudaError_t prepare_xy_v1(int n);
+int xy_tile_options_v1(int n, int* opts);
+PassShape pass_shape_xy_v1(int n);
+cudaError_t launch_x_v1(int n, int tc, const ArgsX& a, cudaStream_t st);
+cudaError_t launch_y_v1(int n, int tc, const ArgsY& a, cudaStream_t st);
 cudaError_t launch_z(int n, const ArgsZ& a, bool dump, cudaStream_t st);
 // Second-order LPT pieces: the z pass writing the source S of every particle
 // (from the six fields in src[0..5]) to out[0]; the inverse-sign transform

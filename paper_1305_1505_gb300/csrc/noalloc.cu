@@ -211,7 +211,7 @@ extern "C" pin_status pin_collapse_times_noalloc(const void* delta_k, int dtype,
     az.redo_list = redo_list;
     az.redo_count = redo_count;
     az.redo_cap = (unsigned)kRedoCap;
-    if (pin::launch_x(n, tc, ax, cs) != cudaSuccess || pin::launch_y(n, tc, ay, cs) != cudaSuccess ||
+    if (pin::launch_x(n, tc, 0, ax, cs) != cudaSuccess || pin::launch_y(n, tc, 0, ay, cs) != cudaSuccess ||
         cudaMemsetAsync(redo_count, 0, sizeof(unsigned), cs) != cudaSuccess ||
         pin::launch_z(n, az, false, cs) != cudaSuccess ||
         (!pin::z_fuses_roots(n) && pin::launch_roots(az, cs) != cudaSuccess) ||

@@ -58,6 +58,7 @@ struct pin_plan_s {
   long long wait_cycles = 0;               // TMA wait budget of the x/y passes (0: default)
   CUtensorMap tm_x{}, tm_y{};              // Phi0 -> x pass, U[3] -> y pass
   int tc_x = 0, tc_y = 0;                  // tile widths (columns per block) of the x and y passes
+  int vx = 0, vy = 0;                      // radix schedules of the x and y line transforms
   bool ic_set = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -189,6 +190,38 @@ __global__ void k_load_phi0(const void* src, int dtype, int nx, int ny, int nz, 
     }
     phi0[i] = out;
   }
+}
+
+// Plain copy by a kernel (16-byte words when both ends and the size allow,
+// else 4-byte ones): used to write results into page-locked host memory
+// through its device mapping.
+__global__ void k_copy_out(const void* src, void* dst, size_t bytes) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if ((((uintptr_t)src | (uintptr_t)dst | bytes) & 15) == 0) {
+    const uint4* s = static_cast<const uint4*>(src);
+    uint4* d = static_cast<uint4*>(dst);
+    for (size_t i = i0; i < bytes / 16; i += stride) d[i] = s[i];
+  } else {
+    const uint32_t* s = static_cast<const uint32_t*>(src);
+    uint32_t* d = static_cast<uint32_t*>(dst);
+    for (size_t i = i0; i < bytes / 4; i += stride) d[i] = s[i];
+  }
+}
+
+// Device-to-host copy of `bytes` (a multiple of 4) on stream st: page-locked
+// host memory mapped for the device is written by k_copy_out (no copy
+// engine), any other host memory by cudaMemcpyAsync.
+cudaError_t copy_to_host(void* host_dst, const void* dev_src, size_t bytes, cudaStream_t st) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host_dst) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer != nullptr) {
+    const unsigned blocks = (unsigned)std::min<size_t>((bytes / 16 + 255) / 256 + 1, 152 * 16);
+    k_copy_out<<<blocks, 256, 0, st>>>(dev_src, at.devicePointer, bytes);
+    return cudaGetLastError();
+  }
+  cudaGetLastError();  // a pageable pointer is not an error here
+  return cudaMemcpyAsync(host_dst, dev_src, bytes, cudaMemcpyDeviceToHost, st);
 }
 
 cudaError_t launch_load_phi0(const void* src, int dtype, int nx, int ny, int nz, int nhp, double box, int batch,
@@ -480,13 +513,13 @@ pin_status enqueue_radius(pin_plan_t p, int ms, int scale, float* const* dump, f
   };
   PIN_CK(p, mark(0, rs.xs));
   const ArgsX ax = radius_args_x(p, ms);
-  PIN_CK(p, launch_x(p->nx, p->tc_x, ax, rs.xs));
+  PIN_CK(p, launch_x(p->nx, p->tc_x, p->vx, ax, rs.xs));
   PIN_CK(p, mark(1, rs.xs));
   if (rs.y_wait) PIN_CK(p, cudaStreamWaitEvent(rs.xs, rs.y_wait, 0));
 
   PIN_CK(p, mark(2, rs.xs));
   const ArgsY ay = radius_args_y(p, ms, collapse, rs.vbuf);
-  PIN_CK(p, launch_y(p->ny, p->tc_y, ay, rs.xs));
+  PIN_CK(p, launch_y(p->ny, p->tc_y, p->vy, ay, rs.xs));
   PIN_CK(p, mark(3, rs.xs));
   if (rs.y_done) {
     PIN_CK(p, cudaEventRecord(rs.y_done, rs.xs));
@@ -623,22 +656,52 @@ pin_status finish_host(pin_plan_t p) {
 }
 
 // ------------------------------------------------------------ tile tuner --
-// Tile widths chosen by pin_autotune, per device, grid shape, batch and mode,
-// shared by every plan of the process.
+// Radix schedules and tile widths chosen by pin_autotune, per device, grid
+// shape, batch and mode, shared by every plan of the process.
 using TuneKey = std::tuple<int, int, int, int, int, int>;
+struct TuneChoice {
+  int vx, tc_x, vy, tc_y;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::map<TuneKey, TuneChoice> g_tune_cache;
 
 TuneKey tune_key(pin_plan_t p) {
   return std::make_tuple(p->device, p->nx, p->ny, p->nz, p->batch, p->velocities ? 1 : 0);
 }
 
-bool tile_allowed(int n, int tc) {
+bool tile_allowed(int n, int v, int tc) {
   int opts[2];
-  const int k = xy_tile_options(n, opts);
+  const int k = xy_tile_options(n, v, opts);
   for (int i = 0; i < k; ++i)
     if (opts[i] == tc) return true;
   return false;
+}
+
+// Twiddle table of the x (axis 0) or y (axis 1) line transform for radix
+// schedule v into its slot of the plan's table (the plan's stream must be
+// idle).
+pin_status upload_axis_twiddles(pin_plan_t p, int axis, int v) {
+  const int n = axis == 0 ? p->nx : p->ny;
+  const PassShape sh = pass_shape_xy(n, v);
+  std::vector<float2> t((size_t)n + (sh.P2 > 1 ? sh.P : 0));
+  fill_twiddles(t.data(), n, sh);
+  PIN_CK(p, cudaMemcpy(p->tw + p->tw_off[axis], t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  return PIN_OK;
+}
+
+// Switches the radix schedules of the x and y passes (twiddles, shapes).
+pin_status apply_radix(pin_plan_t p, int vx, int vy) {
+  if (vx == p->vx && vy == p->vy) return PIN_OK;
+  PIN_CK(p, cudaStreamSynchronize(p->stream));
+  drop_graph(p);
+  pin_status st = upload_axis_twiddles(p, 0, vx);
+  if (st == PIN_OK) st = upload_axis_twiddles(p, 1, vy);
+  if (st != PIN_OK) return st;
+  p->vx = vx;
+  p->vy = vy;
+  p->shape_x = pass_shape_xy(p->nx, vx);
+  p->shape_y = pass_shape_xy(p->ny, vy);
+  return PIN_OK;
 }
 
 // Re-encode the plan's tensor maps for new tile widths; the captured graph
@@ -659,7 +722,8 @@ pin_status apply_tiles(pin_plan_t p, int tc_x, int tc_y) {
 }
 
 // Mean device time (ms) of `reps` launches of the first radius's x or y pass
-// at tile width tc, after one untimed launch, on the plan's stream.
+// at tile width tc with the plan's current radix schedules, after one
+// untimed launch, on the plan's stream.
 pin_status time_pass(pin_plan_t p, bool y_pass, int tc, int reps, float* ms) {
   ArgsX ax = radius_args_x(p, 0);
   ArgsY ay = radius_args_y(p, 0, true);
@@ -671,7 +735,8 @@ pin_status time_pass(pin_plan_t p, bool y_pass, int tc, int reps, float* ms) {
   e = cudaEventCreate(&e1);
   for (int r = 0; e == cudaSuccess && r <= reps; ++r) {
     if (r == 1) e = cudaEventRecord(e0, p->stream);
-    if (e == cudaSuccess) e = y_pass ? launch_y(p->ny, tc, ay, p->stream) : launch_x(p->nx, tc, ax, p->stream);
+    if (e == cudaSuccess)
+      e = y_pass ? launch_y(p->ny, tc, p->vy, ay, p->stream) : launch_x(p->nx, tc, p->vx, ax, p->stream);
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -713,8 +778,8 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   p->precision = d->precision;
   p->batch = batch_of(d);
   p->velocities = d->velocities != 0;
-  p->shape_x = pass_shape(p->nx);
-  p->shape_y = pass_shape(p->ny);
+  p->shape_x = pass_shape_xy(p->nx, 0);
+  p->shape_y = pass_shape_xy(p->ny, 0);
   p->shape_z = pass_shape(p->nz);
   p->spec_elems = (size_t)p->nx * p->ny * p->nhp;
   p->field_elems = p->spec_elems * p->batch;
@@ -741,7 +806,9 @@ pin_status pin_plan(pin_plan_t* out, const pin_plan_desc* d) {
   size_t tw_elems = 0;
   for (int a = 0; a < 3; ++a) {
     p->tw_off[a] = tw_elems;
-    tw_elems += (size_t)ns[a] + (shapes[a]->P2 > 1 ? shapes[a]->P : 0);
+    // the x and y slots hold the table of either radix schedule (at most
+    // n + 64 entries: a three-level line has P <= 64 threads)
+    tw_elems += (size_t)ns[a] + (a < 2 ? 64 : (shapes[a]->P2 > 1 ? shapes[a]->P : 0));
   }
   auto A = [](auto** ptr, size_t bytes) { return plan_alloc(reinterpret_cast<void**>(ptr), bytes); };
   if (A(&p->phi0, p->field_elems * 8) != cudaSuccess || A(&p->U, 3 * p->field_elems * 8) != cudaSuccess ||
@@ -784,11 +851,25 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
   const size_t nh = (size_t)p->nz / 2 + 1;
   const size_t bytes = (size_t)p->nx * p->ny * nh * (dtype == PIN_C64 ? 8 : 16) * p->batch;
   const void* src = delta_k;
+  bool staged = false;
   if (!on_device) {
-    // stage through the V workspace (6 spectra >= one C128 half-spectrum)
-    PIN_CK(p, cudaMemcpyAsync(p->V, delta_k, bytes, cudaMemcpyHostToDevice, p->stream));
-    src = p->V;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, delta_k) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer != nullptr) {
+      // page-locked host memory, mapped for the device: the Phi0 kernel reads
+      // it in place (one pass over the host data, no staging copy; its many
+      // loads in flight keep the host link busy where a copy engine waits
+      // on address translation)
+      src = at.devicePointer;
+    } else {
+      cudaGetLastError();  // a pageable pointer is not an error here
+      // stage through the V workspace (6 spectra >= one C128 half-spectrum)
+      PIN_CK(p, cudaMemcpyAsync(p->V, delta_k, bytes, cudaMemcpyHostToDevice, p->stream));
+      src = p->V;
+      staged = true;
+    }
   }
+  (void)staged;
   PIN_CK(p, launch_load_phi0(src, dtype, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch, p->phi0, p->stream));
   if (p->d64) PIN_CK(p, fp64_load(src, dtype, p->nx, p->ny, p->nz, p->d64, p->stream));
   if (!on_device) PIN_CK(p, cudaStreamSynchronize(p->stream));
@@ -843,9 +924,13 @@ pin_status pin_collapse_times(pin_plan_t p, float* F_max, int32_t* scale_idx, in
   }
   if (st != PIN_OK) return st;
   const size_t n3 = p->n3() * p->batch;
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  PIN_CK(p, cudaMemcpyAsync(F_max, p->fmax, n3 * 4, kind, p->stream));
-  PIN_CK(p, cudaMemcpyAsync(scale_idx, p->idx, n3 * 4, kind, p->stream));
+  if (on_device) {
+    PIN_CK(p, cudaMemcpyAsync(F_max, p->fmax, n3 * 4, cudaMemcpyDeviceToDevice, p->stream));
+    PIN_CK(p, cudaMemcpyAsync(scale_idx, p->idx, n3 * 4, cudaMemcpyDeviceToDevice, p->stream));
+  } else {
+    PIN_CK(p, copy_to_host(F_max, p->fmax, n3 * 4, p->stream));
+    PIN_CK(p, copy_to_host(scale_idx, p->idx, n3 * 4, p->stream));
+  }
   p->calls++;
   if (!on_device) return finish_host(p);
   return PIN_OK;
@@ -959,7 +1044,7 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
   ax.batch = 1;
   ax.err = p->err;
   ax.wait_cycles = p->wait_cycles;
-  e = launch_x(p->nx, p->tc_x, ax, p->stream);
+  e = launch_x(p->nx, p->tc_x, p->vx, ax, p->stream);
   if (e != cudaSuccess) return e;
   // psi_x <- a1 (k_x), psi_y <- a0 (k_y), psi_z <- a0 (z: k_z); all times i
   ArgsY ay{};
@@ -986,7 +1071,7 @@ static cudaError_t enqueue_gradient(pin_plan_t p, float2* phi, float2* a0, float
   ay.batch = 1;
   ay.err = p->err;
   ay.wait_cycles = p->wait_cycles;
-  e = launch_y(p->ny, p->tc_y, ay, p->stream);
+  e = launch_y(p->ny, p->tc_y, p->vy, ay, p->stream);
   if (e != cudaSuccess) return e;
   ArgsZ az{};
   for (int f = 0; f < 3; ++f) {
@@ -1060,7 +1145,7 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
     ay.batch = 1;
     ay.err = p->err;
     ay.wait_cycles = p->wait_cycles;
-    if (e == cudaSuccess) e = launch_y(ny, p->tc_y, ay, p->stream);
+    if (e == cudaSuccess) e = launch_y(ny, p->tc_y, p->vy, ay, p->stream);
     ArgsX ax{};
     if (e == cudaSuccess) e = make_tmap_x(&ax.tm, spec(p, p->V, 1), nx, ny, p->nhp, 1, p->tc_x);
     ax.src = spec(p, p->V, 1);
@@ -1073,7 +1158,7 @@ pin_status pin_displacements_2lpt(pin_plan_t p, float* psi2, int on_device) {
     ax.batch = 1;
     ax.err = p->err;
     ax.wait_cycles = p->wait_cycles;
-    if (e == cudaSuccess) e = launch_x(nx, p->tc_x, ax, p->stream);
+    if (e == cudaSuccess) e = launch_x(nx, p->tc_x, p->vx, ax, p->stream);
     // 3) Phi2 = (3/7) S(k) / k^2 with S(k) = conj(T) (forward transform of real S), into U0
     if (e == cudaSuccess)
       e = launch_phi2(spec(p, p->V, 2), U0, nx, ny, nz, p->nhp, p->box, (float)(3.0 / 7.0 * (double)n3),
@@ -1145,11 +1230,50 @@ pin_status pin_profile(pin_plan_t p, int enable) {
 }
 
 pin_status pin_tile_options(int n, int* opts, int* count) {
+  return pin_tile_options_radix(n, 0, opts, count);
+}
+
+pin_status pin_tile_options_radix(int n, int radix, int* opts, int* count) {
   if (!opts || !count) return PIN_EINVAL;
-  const int k = xy_tile_options(n, opts);
+  const int k = xy_tile_options(n, radix, opts);
   if (k == 0) return PIN_EINVAL;
   *count = k;
   return PIN_OK;
+}
+
+int pin_radix_schedules(void) { return kRadixVariants; }
+
+pin_status pin_radix_shape(int n, int radix, int* E, int* P1, int* P2) {
+  if (!E || !P1 || !P2) return PIN_EINVAL;
+  if (!size_supported(n) || radix < 0 || radix >= kRadixVariants) return PIN_EINVAL;
+  const PassShape sh = pass_shape_xy(n, radix);
+  *E = sh.E;
+  *P1 = sh.P1;
+  *P2 = sh.P2;
+  return PIN_OK;
+}
+
+pin_status pin_get_radix(pin_plan_t p, int* vx, int* vy) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (!vx || !vy) return fail(p, PIN_EINVAL, "null output");
+  *vx = p->vx;
+  *vy = p->vy;
+  return PIN_OK;
+}
+
+pin_status pin_set_radix(pin_plan_t p, int vx, int vy) {
+  pin_status st = check_plan(p);
+  if (st != PIN_OK) return st;
+  if (vx < 0 || vx >= kRadixVariants || vy < 0 || vy >= kRadixVariants)
+    return fail(p, PIN_EINVAL, "radix schedule must be in 0..pin_radix_schedules()-1");
+  st = apply_radix(p, vx, vy);
+  if (st != PIN_OK) return st;
+  // keep the tile widths if the new schedules run them, else their defaults
+  const int tx = tile_allowed(p->nx, vx, p->tc_x) ? p->tc_x : p->shape_x.tc;
+  const int ty = tile_allowed(p->ny, vy, p->tc_y) ? p->tc_y : p->shape_y.tc;
+  if (tx == p->tc_x && ty == p->tc_y) return PIN_OK;
+  return apply_tiles(p, tx, ty);
 }
 
 pin_status pin_get_tiles(pin_plan_t p, int* tc_x, int* tc_y) {
@@ -1166,8 +1290,8 @@ pin_status pin_set_tiles(pin_plan_t p, int tc_x, int tc_y) {
   if (st != PIN_OK) return st;
   if (tc_x == 0) tc_x = p->shape_x.tc;
   if (tc_y == 0) tc_y = p->shape_y.tc;
-  if (!tile_allowed(p->nx, tc_x) || !tile_allowed(p->ny, tc_y))
-    return fail(p, PIN_EINVAL, "tile width is not one of pin_tile_options");
+  if (!tile_allowed(p->nx, p->vx, tc_x) || !tile_allowed(p->ny, p->vy, tc_y))
+    return fail(p, PIN_EINVAL, "tile width is not one of the plan's radix schedule's options");
   if (tc_x == p->tc_x && tc_y == p->tc_y) return PIN_OK;
   return apply_tiles(p, tc_x, tc_y);
 }
@@ -1181,7 +1305,7 @@ pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y)
   PIN_CK(p, cudaStreamIsCapturing(p->stream, &cap));
   if (cap != cudaStreamCaptureStatusNone) return fail(p, PIN_ESTATE, "the plan's stream is being captured");
   const auto key = tune_key(p);
-  std::pair<int, int> best{0, 0};
+  TuneChoice best{0, 0, 0, 0};
   bool cached = false;
   if (!(flags & PIN_TUNE_FORCE)) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1193,27 +1317,40 @@ pin_status pin_autotune(pin_plan_t p, int reps, int flags, int* tc_x, int* tc_y)
   }
   if (!cached) {
     // the passes only read Phi0 (zeros until a field is set) and write the
-    // U and V workspaces; F_max, the index and v_max are untouched
+    // U and V workspaces; F_max, the index and v_max are untouched.  Every
+    // (radix schedule, tile width) candidate of each pass is timed.
     if (!p->ic_set) PIN_CK(p, cudaMemsetAsync(p->phi0, 0, p->field_elems * sizeof(float2), p->stream));
-    for (int pass = 0; pass < 2; ++pass) {
-      int opts[2];
-      const int k = xy_tile_options(pass ? p->ny : p->nx, opts);
-      float best_ms = 0.f;
-      for (int i = 0; i < k; ++i) {
-        float ms = 0.f;
-        st = time_pass(p, pass == 1, opts[i], reps, &ms);
-        if (st != PIN_OK) return st;
-        if (i == 0 || ms < best_ms) {
-          best_ms = ms;
-          (pass ? best.second : best.first) = opts[i];
+    const int vx0 = p->vx, vy0 = p->vy;
+    float best_ms[2] = {0.f, 0.f};
+    bool have[2] = {false, false};
+    for (int v = 0; v < kRadixVariants; ++v) {
+      st = apply_radix(p, v, v);
+      if (st != PIN_OK) return st;
+      for (int pass = 0; pass < 2; ++pass) {
+        int opts[2];
+        const int k = xy_tile_options(pass ? p->ny : p->nx, v, opts);
+        for (int i = 0; i < k; ++i) {
+          float ms = 0.f;
+          st = time_pass(p, pass == 1, opts[i], reps, &ms);
+          if (st != PIN_OK) return st;
+          if (!have[pass] || ms < best_ms[pass]) {
+            have[pass] = true;
+            best_ms[pass] = ms;
+            if (pass) { best.vy = v; best.tc_y = opts[i]; }
+            else { best.vx = v; best.tc_x = opts[i]; }
+          }
         }
       }
     }
+    st = apply_radix(p, vx0, vy0);
+    if (st != PIN_OK) return st;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
   }
-  if (best.first != p->tc_x || best.second != p->tc_y) {
-    st = apply_tiles(p, best.first, best.second);
+  st = apply_radix(p, best.vx, best.vy);
+  if (st != PIN_OK) return st;
+  if (best.tc_x != p->tc_x || best.tc_y != p->tc_y) {
+    st = apply_tiles(p, best.tc_x, best.tc_y);
     if (st != PIN_OK) return st;
   }
   if (tc_x) *tc_x = p->tc_x;

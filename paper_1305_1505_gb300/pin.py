@@ -58,6 +58,7 @@ EXPORTS = ("pin_plan", "pin_footprint_bytes", "pin_set_ic", "pin_collapse_times"
            "pin_displacements", "pin_sync", "pin_get_stats", "pin_kernels_per_call",
            "pin_profile", "pin_pass_times", "pin_collapse_times_noalloc", "pin_velocities",
            "pin_fragment_order", "pin_displacements_2lpt", "pin_set_ic_seed", "pin_tile_options",
+           "pin_tile_options_radix", "pin_radix_schedules", "pin_radix_shape", "pin_get_radix", "pin_set_radix",
            "pin_get_tiles", "pin_set_tiles", "pin_autotune", "pin_noalloc_status", "pin_set_radii", "pin_set_schedule",
            "pin_get_schedule", "pin_set_wait_budget",
            "pin_debug_fail_alloc", "pin_strerror", "pin_last_error", "pin_destroy")
@@ -111,6 +112,16 @@ def load(path=None):
     IP = ctypes.POINTER(ctypes.c_int)
     L.pin_tile_options.argtypes = [ctypes.c_int, IP, IP]
     L.pin_tile_options.restype = ctypes.c_int
+    L.pin_tile_options_radix.argtypes = [ctypes.c_int, ctypes.c_int, IP, IP]
+    L.pin_tile_options_radix.restype = ctypes.c_int
+    L.pin_radix_schedules.argtypes = []
+    L.pin_radix_schedules.restype = ctypes.c_int
+    L.pin_radix_shape.argtypes = [ctypes.c_int, ctypes.c_int, IP, IP, IP]
+    L.pin_radix_shape.restype = ctypes.c_int
+    L.pin_get_radix.argtypes = [P, IP, IP]
+    L.pin_get_radix.restype = ctypes.c_int
+    L.pin_set_radix.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    L.pin_set_radix.restype = ctypes.c_int
     L.pin_get_tiles.argtypes = [P, IP, IP]
     L.pin_get_tiles.restype = ctypes.c_int
     L.pin_set_tiles.argtypes = [P, ctypes.c_int, ctypes.c_int]
@@ -267,6 +278,34 @@ def pin_tile_options(n):
     k = ctypes.c_int(0)
     _check(load().pin_tile_options(int(n), opts, ctypes.byref(k)))
     return list(opts[:k.value])
+
+
+def pin_tile_options_radix(n, radix):
+    opts = (ctypes.c_int * 2)()
+    k = ctypes.c_int(0)
+    _check(load().pin_tile_options_radix(int(n), int(radix), opts, ctypes.byref(k)))
+    return list(opts[:k.value])
+
+
+def pin_radix_schedules():
+    return load().pin_radix_schedules()
+
+
+def pin_radix_shape(n, radix):
+    """(E, P1, P2) of radix schedule `radix` for lines of n points."""
+    e, p1, p2 = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().pin_radix_shape(int(n), int(radix), ctypes.byref(e), ctypes.byref(p1), ctypes.byref(p2)))
+    return e.value, p1.value, p2.value
+
+
+def pin_get_radix(plan):
+    x, y = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().pin_get_radix(plan, ctypes.byref(x), ctypes.byref(y)), plan)
+    return x.value, y.value
+
+
+def pin_set_radix(plan, vx, vy):
+    _check(load().pin_set_radix(plan, int(vx), int(vy)), plan)
 
 
 def pin_get_tiles(plan):
@@ -501,6 +540,13 @@ class Plan:
     def tiles(self):
         """(x-pass, y-pass) tile widths in use."""
         return pin_get_tiles(self.handle)
+
+    def radix(self):
+        """(x-pass, y-pass) radix schedules in use."""
+        return pin_get_radix(self.handle)
+
+    def set_radix(self, vx=0, vy=0):
+        pin_set_radix(self.handle, vx, vy)
 
     def set_tiles(self, tc_x=0, tc_y=0):
         """Forces tile widths (0: the default); each must be one of

@@ -119,13 +119,13 @@ class PinEngine:
         return s
 
     def warm(self, sizes, box_per_cell=2.0, per_size=1):
-        """Loads the library, tunes the tile widths of each grid size on an
-        idle device and fills the pool with per_size plans of each size.
-        Returns the tile widths per size."""
+        """Loads the library, tunes the tile widths and radix schedules of
+        each grid size on an idle device and fills the pool with per_size plans
+        of each size.  Returns, per size, ((tc_x, tc_y), (radix_x, radix_y))."""
         out = {}
         for n in sizes:
             slots = [self._make(n, box_per_cell * n) for _ in range(per_size)]
-            out[int(n)] = slots[0].plan.tiles()
+            out[int(n)] = (slots[0].plan.tiles(), slots[0].plan.radix())
             for s in slots:
                 self._release(s)
         return out
@@ -184,14 +184,21 @@ class PinEngine:
 
 class Server:
     """FIFO admission by memory footprint and slot count; one worker thread
-    per admitted request."""
+    per admitted request.  Large requests (N >= big_n) are admitted at most
+    max_big at a time: two of them sharing the device would both take about
+    twice as long, which sets the latency tail, while small requests cost the
+    device little and overlap freely (and do not wait behind a large one)."""
 
-    def __init__(self, engine, budget_bytes, max_slots=4, keep_results=True):
+    def __init__(self, engine, budget_bytes, max_slots=4, keep_results=True, big_n=512, max_big=1):
         """keep_results: copy each result into arrays of the request (False:
         drop it; latency is measured to the result's arrival in host memory
-        either way)."""
+        either way).  big_n / max_big: the large-request limit (max_big 0:
+        none)."""
         self.engine = engine
         self.keep_results = bool(keep_results)
+        self.big_n = int(big_n)
+        self.max_big = int(max_big)
+        self.running_big = 0
         self.budget = int(budget_bytes)
         self.max_slots = int(max_slots)
         self.queue = collections.deque()
@@ -204,6 +211,9 @@ class Server:
         self._stop = False
         self._sched = threading.Thread(target=self._schedule, daemon=True)
         self._sched.start()
+
+    def _is_big(self, req):
+        return self.max_big > 0 and req.n >= self.big_n
 
     def submit(self, req, now=None):
         req.arrival = time.perf_counter() if now is None else now
@@ -234,16 +244,28 @@ class Server:
                     while self.queue and self.queue[0].deadline is not None and \
                             now - self.queue[0].arrival > self.queue[0].deadline:
                         self._finish(self.queue.popleft(), "timeout", error="deadline passed in the queue")
-                    if self.queue:
-                        head = self.queue[0]
-                        if self.running < self.max_slots and self.in_use + head.footprint <= self.budget:
+                    # FIFO, except that a large request held by the large-request
+                    # limit lets the requests behind it pass; the first one not
+                    # so held is admitted when its memory fits, else everyone
+                    # waits (no overtaking on memory, so none starves)
+                    pick = None
+                    if self.running < self.max_slots:
+                        for i, r in enumerate(self.queue):
+                            if self._is_big(r) and self.running_big >= self.max_big:
+                                continue
+                            if self.in_use + r.footprint <= self.budget:
+                                pick = i
                             break
+                    if pick is not None:
+                        break
                     self.lock.wait(0.01)
                 if self._stop:
                     return
-                req = self.queue.popleft()
+                req = self.queue[pick]
+                del self.queue[pick]
                 self.in_use += req.footprint
                 self.running += 1
+                self.running_big += 1 if self._is_big(req) else 0
                 self.peak_in_use = max(self.peak_in_use, self.in_use)
                 self.peak_running = max(self.peak_running, self.running)
                 req.t_admit = time.perf_counter()
@@ -273,6 +295,7 @@ class Server:
         with self.lock:
             self.in_use -= req.footprint
             self.running -= 1
+            self.running_big -= 1 if self._is_big(req) else 0
             self._finish(req, status, res, err)
             if t_done is not None:
                 req.t_done = t_done
@@ -370,7 +393,7 @@ def measure_serving(requests=600, rate=2.0, seed=5, slots=4, budget_bytes=0, pri
     out = {"metric": "served collapse-time requests: latency p50/p99 and throughput",
            "workload": "%d requests, Poisson arrivals (mean %g/s), N in {64,128,256,512} (.4/.3/.2/.1), "
                        "box 2 Mpc/h per cell, 20-40 radii 40->2 Mpc/h, seed %d" % (requests, rate, seed),
-           "tiles": {str(k): list(v) for k, v in tiles.items()},
+           "tiles": {str(k): {"tiles": list(v[0]), "radix": list(v[1])} for k, v in tiles.items()},
            "priority_from_n": priority_from_n,
            "nominal": one(rate)}
     if stress_rate > 0:

@@ -1,13 +1,16 @@
-"""The x/y tile schedule (pin_tile_options, pin_set_tiles, pin_autotune):
-every candidate width gives bit-identical results (each column's line
-transform is the same arithmetic whatever the tile), the tuner picks among
-the candidates and keeps its choice per grid shape, and a bad width is
-rejected without changing the plan."""
+"""The x/y tile and radix schedules (pin_tile_options, pin_set_tiles,
+pin_set_radix, pin_autotune): every tile width gives bit-identical results
+(each column's line transform is the same arithmetic whatever the tile), each
+radix schedule matches the oracle (and the other schedule to FP32 rounding),
+the tuner picks among the (schedule, width) candidates and keeps its choice
+per grid shape, and a bad width or schedule is rejected without changing the
+plan."""
 import itertools
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1305_1505_gb300 import ic, pin
 from tests import parity
 
@@ -50,8 +53,11 @@ def test_every_tile_width_gives_identical_results(shape, vel):
             for a, b in zip(ref, got):
                 assert torch.equal(a, b), (shape, tx, ty)
         tuned = plan.autotune(reps=2, force=True)
+        vx, vy = plan.radix()
         assert tuned == plan.tiles()
-        assert tuned[0] in pin.pin_tile_options(nx) and tuned[1] in pin.pin_tile_options(ny)
+        assert tuned[0] in pin.pin_tile_options_radix(nx, vx) and tuned[1] in pin.pin_tile_options_radix(ny, vy)
+        plan.set_radix(0, 0)
+        plan.set_tiles(0, 0)
         for a, b in zip(ref, _run(plan, vel)):
             assert torch.equal(a, b)
     finally:
@@ -75,7 +81,11 @@ def test_tuner_keeps_its_choice_and_rejects_bad_widths():
             b.set_tiles(7, 0)
         assert e.value.status == pin.PIN_EINVAL and b.tiles() == before
         b.set_tiles(0, 0)
-        assert b.tiles() == (pin.pin_tile_options(n)[0],) * 2
+        vx, vy = b.radix()
+        assert b.tiles() == (pin.pin_tile_options_radix(n, vx)[0], pin.pin_tile_options_radix(n, vy)[0])
+        with pytest.raises(pin.PinError) as e:
+            b.set_radix(2, 0)
+        assert e.value.status == pin.PIN_EINVAL and b.radix() == (vx, vy)
         # results after tuning equal the default schedule's
         for p in (a, b):
             p.set_ic(torch.from_numpy(d32).cuda())
@@ -105,5 +115,54 @@ def test_tuner_refuses_inside_stream_capture():
         torch.cuda.synchronize()
         assert float(x.sum()) == 8.0
         assert plan.autotune(reps=2, force=True) == plan.tiles()
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("n,box,S", [(16, 64.0, 5), (48, 96.0, 6), (64, 100.0, 8), (96, 192.0, 6), (128, 512.0, 8),
+                                     (384, 1536.0, 3)])
+def test_radix_schedules_match_the_oracle(n, box, S):
+    """Radix schedule 1 of the x and y passes, at every tile width, against
+    the oracle (collapse times under the parity rule, the deformation tensor
+    within 2e-5 of its rms) and against schedule 0 to FP32 rounding."""
+    import torch
+    assert pin.pin_radix_schedules() == 2
+    e0, e1 = pin.pin_radix_shape(n, 0), pin.pin_radix_shape(n, 1)
+    assert e0 != e1 and e0[0] * e0[1] * e0[2] == n == e1[0] * e1[1] * e1[2]
+    radii = ic.log_radii(box / n, box / 6, S)
+    d32, d64 = parity.inputs(n, box, 31)
+    plan = pin.Plan(n, box, radii)
+    try:
+        plan.set_ic(torch.from_numpy(d32).cuda())
+        F0, I0 = (t.clone() for t in plan.collapse_times())
+        orc = oracle.collapse_times(d64, box, radii, keep_all=n <= 64) if n <= 128 else None
+        href, _ = oracle.hessian(d64, box, radii[-1]) if n <= 128 else (None, None)
+        for vx, vy in ((1, 1), (1, 0), (0, 1)):
+            plan.set_radix(vx, vy)
+            assert plan.radix() == (vx, vy)
+            got = None
+            for tx in pin.pin_tile_options_radix(n, vx):
+                for ty in pin.pin_tile_options_radix(n, vy):
+                    plan.set_tiles(tx, ty)
+                    F, I = plan.collapse_times()
+                    if got is None:
+                        got = (F.clone(), I.clone())
+                    else:
+                        assert torch.equal(F, got[0]) and torch.equal(I, got[1]), (vx, vy, tx, ty)
+            F, I = got
+            # the schedules round differently: equal to FP32 rounding except at
+            # the rare ill-conditioned particles (C10a), at most 1e-5 of them
+            rel = (F - F0).abs() / (F0.abs() + F0.pow(2).mean().sqrt())
+            outliers = int((rel > 1e-4).sum())
+            print("radix %d,%d %d^3: max rel diff to schedule 0 %.2e, %d particles above 1e-4"
+                  % (vx, vy, n, rel.max().item(), outliers))
+            assert outliers <= max(1, 1e-5 * n ** 3), outliers
+            if orc is not None:
+                parity.assert_parity(F.cpu().numpy(), I.cpu().numpy(), orc, d64, box, radii,
+                                     label="radix %d,%d %d^3" % (vx, vy, n))
+                h = plan.hessian(S - 1).double().cpu().numpy()
+                assert np.abs(h - href).max() < 2e-5 * np.sqrt(np.mean(href ** 2))
+            else:
+                assert (I != I0).float().mean().item() < 1e-4
     finally:
         plan.close()

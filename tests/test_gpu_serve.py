@@ -16,8 +16,8 @@ def test_results_same_alone_and_in_the_mix():
     tiles = eng.warm([16, 32, 48, 64], per_size=2)
     assert sorted(tiles) == [16, 32, 48, 64]
     from paper_1305_1505_gb300 import pin
-    for n, (tx, ty) in tiles.items():
-        assert tx in pin.pin_tile_options(n) and ty in pin.pin_tile_options(n)
+    for n, ((tx, ty), (vx, vy)) in tiles.items():
+        assert tx in pin.pin_tile_options_radix(n, vx) and ty in pin.pin_tile_options_radix(n, vy)
     specs = [(16, 3), (32, 5), (48, 4), (64, 6), (32, 7), (16, 2), (64, 3), (48, 8)]
     reqs = [serve.Request(i, n, 2.0 * n, 500 + i, ic.log_radii(2.0, 20.0, s))
             for i, (n, s) in enumerate(specs)]

@@ -110,3 +110,35 @@ def test_close_cancels_queued_requests_and_lets_running_ones_finish():
         assert r.wait(timeout=2.0) == "cancelled"
     assert reqs[0].wait(timeout=2.0) == "done"
     assert reqs[0].result == (64, 100)
+
+
+def test_large_requests_do_not_share_the_device_and_do_not_block_small_ones():
+    """At most max_big large requests (N >= big_n) run at once; a small
+    request queued behind a held large one is admitted meanwhile."""
+    eng = FakeEngine(dur=0.1)
+    running_big, peak_big = [0], [0]
+    lock = threading.Lock()
+    orig = eng.run
+
+    def run(req, timeout_s=None):
+        big = req.n >= 512
+        with lock:
+            running_big[0] += big
+            peak_big[0] = max(peak_big[0], running_big[0])
+        try:
+            return orig(req, timeout_s)
+        finally:
+            with lock:
+                running_big[0] -= big
+
+    eng.run = run
+    srv = serve.Server(eng, budget_bytes=10 ** 9, max_slots=4, big_n=512, max_big=1)
+    reqs = [srv.submit(_req(0, 512)), srv.submit(_req(1, 512)), srv.submit(_req(2, 64))]
+    time.sleep(0.05)
+    # the second large request waits; the small one behind it already runs
+    assert reqs[1].status == "queued" and reqs[2].status in ("running", "done")
+    assert srv.drain(timeout=5)
+    srv.close()
+    assert all(r.status == "done" for r in reqs)
+    assert peak_big[0] == 1
+    assert reqs[2].t_done < reqs[1].t_done
