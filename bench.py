@@ -119,15 +119,20 @@ def algorithmic_bytes(n, fused, velocities):
     return alg
 
 
-# DRAM traffic of the dominant kernel per launch (dram__bytes_read.sum +
-# dram__bytes_write.sum), from an ncu capture of bench.py, valid only while
-# the kernel sources hash to the recorded value; otherwise reported as null.
-TRAFFIC_SOURCES = ["kernels.cu", "kernels.cuh", "fft.cuh", "collapse.cuh", "pin.cu"]
+# Counters of the dominant kernel, valid only while the kernel sources hash to
+# the recorded value (otherwise reported as null): DRAM read + write bytes and
+# warp instructions per particle and launch, averaged over the 40 launches of
+# one step of the 384^3 x 40 workload (the same 4 Mpc/h cells and radii; a
+# small case of 2.7 GB on the device, one ncu pass), scaled to a launch of the
+# benchmark by its particle count.  The 768-point line transform has one more
+# radix-2 level than the 384-point one, so the instruction count is a slight
+# underestimate at 768^3.
+TRAFFIC_SOURCES = ["kernels.cu", "kernels_v1.cu", "passes_xy.cuh", "kernels.cuh", "fft.cuh", "packed.cuh",
+                   "collapse.cuh", "collapse_x2.cuh", "pin.cu"]
 MEASURED_TRAFFIC = {
-    # profiles/launch_list_768x40.md: dram bytes and warp instructions of the
-    # fused z pass per launch, 768^3 x 40
-    ("k_pass_z", 768, False): {"sources": "e00300e503102fbe", "bytes_per_launch": 16.761e9,
-                               "warp_inst_per_launch": 6.945e9},
+    # profiles/z_pass_instruction_mix_384.md
+    ("k_pass_z", 768, False): {"sources": "ef4da1240a98a4f2", "bytes_per_particle": 30.197, "warp_inst_per_particle": 10.2851,
+                               "measured_at": "384^3 x 40, the 40 launches of one step, scaled by particles"},
 }
 
 
@@ -164,7 +169,7 @@ def measured_record(kernel, n, velocities):
 
 def measured_traffic(kernel, n, nscales, velocities):
     rec = measured_record(kernel, n, velocities)
-    return None if rec is None else rec["bytes_per_launch"]
+    return None if rec is None else rec["bytes_per_particle"] * n ** 3
 
 
 # Issue roof of the SMs: 152 SMs x 4 warp schedulers x 1 warp instruction per
@@ -181,19 +186,20 @@ def roofline(pass_name, ms_per_launch, n, velocities, fused, hbm_achieved, hbm_p
     the sampled maximum SM clock), with its HBM fraction alongside."""
     kname = ("k_pass_" if pass_name in "xyz" else "k_") + pass_name
     rec = measured_record(kname, n, velocities)
-    traffic = None if rec is None else rec["bytes_per_launch"]
+    traffic = None if rec is None else rec["bytes_per_particle"] * n ** 3
     hbm = {"bound": "hbm", "kernel": kname, "achieved": hbm_achieved, "peak": hbm_peak,
            "peak_kind": peak_kind, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
            "traffic": traffic, "passes": passes}
-    if rec is None or not fused or kname != "k_pass_z" or not rec.get("warp_inst_per_launch"):
+    if rec is None or not fused or kname != "k_pass_z" or not rec.get("warp_inst_per_particle"):
         return hbm
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = SMS * SCHEDULERS * mhz * 1e6 / 1e9
-    achieved = rec["warp_inst_per_launch"] / (ms_per_launch / 1e3) / 1e9
+    achieved = rec["warp_inst_per_particle"] * n ** 3 / (ms_per_launch / 1e3) / 1e9
     return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
             "peak_kind": "derived: %d SMs x %d schedulers x 1 warp instruction/cycle x %.0f MHz"
                          % (SMS, SCHEDULERS, mhz),
             "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": traffic,
+            "counters_measured_at": rec.get("measured_at"),
             "hbm_frac": hbm_achieved / hbm_peak, "hbm_peak_kind": peak_kind, "passes": passes}
 
 
@@ -401,12 +407,13 @@ def run_ours(args):
     # x/y tile widths timed on this plan, outside the timed region
     if args.schedule:
         pin.pin_set_schedule(plan.handle, args.schedule)
+    if args.radix:
+        rx, ry = (int(v) for v in args.radix.split(","))
+        plan.set_radix(rx, ry)
     if args.tiles:
         tx, ty = (int(v) for v in args.tiles.split(","))
         plan.set_tiles(tx, ty)
-        tiles = plan.tiles()
-    else:
-        tiles = plan.tiles() if args.no_tune else plan.autotune(reps=5)
+    tiles = plan.tiles() if (args.no_tune or args.tiles or args.radix) else plan.autotune(reps=5)
     F = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
     I = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
     pin.pin_profile(plan.handle, 1)
@@ -532,7 +539,7 @@ def run_ours(args):
                            tiles={"x": tiles[0], "y": tiles[1], "radix_x": radix[0], "radix_y": radix[1],
                                   "radix_shapes": {"x": pin.pin_radix_shape(n, radix[0]),
                                                    "y": pin.pin_radix_shape(n, radix[1])},
-                                  "tuned": not (args.no_tune or args.tiles)},
+                                  "tuned": not (args.no_tune or args.tiles or args.radix)},
                            schedule=pin_schedule),
             "roofline": dict(roofline(names[dom], per_launch_ms[dom], n, bool(args.velocities), fused,
                                       achieved, peak, peak_kind, clocks, passes), step=whole_step),
@@ -825,6 +832,7 @@ def main():
                     help="radius schedule (pin_set_schedule): 0 serial, 1 z(s) beside x(s+1), "
                          "2 z(s) beside x and y of s+1")
     ap.add_argument("--tiles", default="", help="force the x,y tile widths (e.g. 8,8) instead of tuning")
+    ap.add_argument("--radix", default="", help="force the x,y radix schedules (e.g. 1,1) instead of tuning")
     ap.add_argument("--requests", type=int, default=600, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=2.0, help="serve: mean arrivals per second")
     ap.add_argument("--no-configs", action="store_true",

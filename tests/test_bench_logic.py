@@ -24,12 +24,14 @@ def test_digest_follows_code_not_comments():
 
 def test_roofline_uses_the_record_only_for_matching_sources(monkeypatch):
     passes = {"z": {"ms_per_launch": 6.8}}
-    rec = {"sources": bench.sources_digest(), "bytes_per_launch": 16.7e9, "warp_inst_per_launch": 6.9e9}
+    n3 = 768 ** 3
+    rec = {"sources": bench.sources_digest(), "bytes_per_particle": 16.7e9 / n3,
+           "warp_inst_per_particle": 6.9e9 / n3, "measured_at": "test"}
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("k_pass_z", 768, False), rec)
     r = bench.roofline("z", 6.8, 768, False, True, 2400.0, 6669.0, "measured",
                        {"sm_max_mhz": 2070.0}, passes)
     assert r["bound"] == "alu" and abs(r["frac"] - 6.9e9 / 6.8e-3 / (152 * 4 * 2.07e9)) < 1e-9
-    assert r["traffic"] == 16.7e9
+    assert abs(r["traffic"] - 16.7e9) < 1.0
     stale = dict(rec, sources="0000000000000000")
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("k_pass_z", 768, False), stale)
     r = bench.roofline("z", 6.8, 768, False, True, 2400.0, 6669.0, "measured",
