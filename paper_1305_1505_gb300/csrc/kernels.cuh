@@ -87,6 +87,7 @@ struct ArgsZ {
   int nfields;
   int nlines;    // batch * N^2 lines along z
   int npart;     // batch * N^3 particles
+  int prefetch_blocks;  // z pass: prefetch the lines of block + this many into L2 (0: none)
   const float2* tw;
   int nhp;
   // eigenvalue mode (nfields 6), plus the displacement components (nfields 9)
