@@ -253,9 +253,16 @@ struct XLayoutLines {
   }
 };
 
-// Level-2 twiddles w_N^{p k1}, laid out [k1][p] in shared memory.
-template <int E, int P>
-__device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { return s_tw[k1 * P + p]; }
+// A twiddle: from shared memory, or (TWG) from the global table through the
+// read-only cache.
+template <bool TWG>
+__device__ __forceinline__ float2 ld_tw(const float2* tw) {
+  if constexpr (TWG) return __ldg(tw);
+  else return *tw;
+}
+// Level-2 twiddles w_N^{p k1}, laid out [k1][p].
+template <int E, int P, bool TWG = false>
+__device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { return ld_tw<TWG>(s_tw + k1 * P + p); }
 
 // Inverse FFT of one line held as v[t] = x[p + P t] by thread p of the line.
 // Two levels: on return v[i * P + k2] = X[(p + P i) + E k2] for i in [0, E/P),
@@ -268,8 +275,9 @@ __device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { retur
 // the exchange buffer in use (callers synchronise the block before writing
 // s_x again).  WARP: every transform is held within one warp (P divides 32,
 // transform c on threads [c P, c P + P)) with an exchange region of its own,
-// so those synchronisations are warp-level.
-template <int N, class Layout, bool WARP = false, int V = 0>
+// so those synchronisations are warp-level.  TWG: s_tw is the global twiddle
+// table (same layout), read through the read-only cache.
+template <int N, class Layout, bool WARP = false, int V = 0, bool TWG = false>
 __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N, V>::E], int p, int c, float2* s_x,
                                          const float2* s_tw) {
   using S = Shape<N, V>;
@@ -284,7 +292,7 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N, V>::E], int p, int
     // level 1 done; twiddle w_N^{p k1} and first exchange
 #pragma unroll
     for (int k1 = 0; k1 < E; ++k1) {
-      float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P>(s_tw, k1, p));
+      float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P, TWG>(s_tw, k1, p));
       s_x[Layout::at(k1, p, c)] = z;
     }
     sync();
@@ -293,7 +301,7 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N, V>::E], int p, int
     const int p1 = p % P1, q = p / P1;
     float2 twb[P2];  // w_P^{p1 k2a}: the same for every k1 of this thread
 #pragma unroll
-    for (int k2a = 1; k2a < P2; ++k2a) twb[k2a] = s_tw[E * P + k2a * P1 + p1];
+    for (int k2a = 1; k2a < P2; ++k2a) twb[k2a] = ld_tw<TWG>(s_tw + E * P + k2a * P1 + p1);
 #pragma unroll
     for (int i = 0; i < E / P2; ++i) {
       float2 t[P2];
@@ -324,7 +332,7 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N, V>::E], int p, int
   } else if constexpr (P > 1) {
 #pragma unroll
     for (int k1 = 0; k1 < E; ++k1) {
-      float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P>(s_tw, k1, p));
+      float2 z = (k1 == 0) ? v[k1] : cmul(v[k1], tw2<E, P, TWG>(s_tw, k1, p));
       s_x[Layout::at(k1, p, c)] = z;
     }
     sync();
