@@ -32,6 +32,12 @@ template <int N> __host__ __device__ constexpr int field_stride() {
   return Shape<N>::P2 > 1 ? N + 2 : N + (Shape<N>::P >= 2 ? Shape<N>::P / 2 : 1);
 }
 
+// Compaction of the root solve in the fused z pass (1: queue the particles
+// that cannot be skipped and solve them after the main loop).
+#ifndef PIN_Z_COMPACT
+#define PIN_Z_COMPACT 1
+#endif
+
 // ---------------------------------------------------------------- z pass --
 // Lines along z: line index l = x*N + y, the half line src[f][l*nhp + kz],
 // kz in [0, N/2], is contiguous.  Fields are paired (A + iB) into one complex
@@ -53,6 +59,7 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
   float2* s_x = reinterpret_cast<float2*>(smem_raw);
   constexpr int kFS = field_stride<N>();
   float* s_f = reinterpret_cast<float*>(smem_raw);
+  __shared__ int s_nq;  // queued particles (compaction of the root solve)
   const int nthreads = NC * P;
   const int tid = threadIdx.x;
   // the lines of the block that starts about one wave of resident blocks
@@ -123,6 +130,7 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
     return;
   } else {
     constexpr int kPts = LINES * N;
+    if (tid == 0) s_nq = 0;
     __syncthreads();  // exchange buffer becomes the field buffer
     if (pair < npairs) {
 #pragma unroll
@@ -152,6 +160,51 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
       // interleave)
       constexpr int NPR = PIN_Z_ILP / 2;
       const CollapseConsts<float> ccf{a.dcorr_f, a.correction};
+      // Compaction: particles that cannot be skipped are queued and solved
+      // after the main loop, two per thread, so that a warp's root solve runs
+      // on full lanes
+      constexpr bool kCompact = PIN_Z_COMPACT != 0;
+      unsigned short* s_q = reinterpret_cast<unsigned short*>(s_f + LINES * NF * kFS);
+      // The end of a pair's computation: the rare minor-axis solve, the FP64
+      // redo of an ill-conditioned root, and the running maximum.
+      auto finish = [&](CollapseStateX2& cx, unsigned dn, const float2 (&lm)[3], const int (&qv)[2],
+                        const int (&lzv)[2], const float (&fmv)[2]) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if ((dn >> u) & 1u) continue;
+          CollapseState<float> cs = lane_state(cx, u);
+          if (cs.need[0] || cs.need[1]) collapse_rare<float>(cs);
+          const int qq = qv[u];
+          const float F = cs.best + cs.corr;
+          if (cs.kappa < a.tau_root) {
+            atomicAdd(a.counters + 1, 1ull);
+            const unsigned slot = atomicAdd(a.redo_count, 1u);
+            if (slot < a.redo_cap) {
+              RedoEntry e;
+              e.q = qq;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) e.h[k] = u ? lm[k].y : lm[k].x;
+              e.h[3] = e.h[4] = e.h[5] = 0.f;
+              e.kind = 1;
+              a.redo_list[slot] = e;
+              if constexpr (NP == 5) {
+#pragma unroll
+                for (int cpt = 0; cpt < 3; ++cpt) a.psi_out[cpt * total + qq] = s_f[lzv[u] + (6 + cpt) * kFS];
+              }
+              continue;
+            }
+            atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
+          }
+          if (F > fmv[u] || (F == fmv[u] && F > 0.f && a.scale < a.idx[qq])) {
+            a.fmax[qq] = F;
+            a.idx[qq] = a.scale;
+            if constexpr (NP == 5) {
+#pragma unroll
+              for (int cpt = 0; cpt < 3; ++cpt) a.vstate[cpt * total + qq] = s_f[lzv[u] + (6 + cpt) * kFS];
+            }
+          }
+        }
+      };
       for (int pt0 = tid; pt0 < kPts; pt0 += 2 * NPR * nthreads) {
         int q[NPR][2], lz[NPR][2];
         bool valid[NPR][2];
@@ -208,8 +261,7 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
         }
         // lanes that cannot beat their running maximum (the radii run
         // smallest first, so most particles reach F_max early) or that the
-        // FP64 redo finishes skip the root solve; a pair solves only if one of
-        // its lanes needs it
+        // FP64 redo finishes skip the root solve
         CollapseStateX2 csx[NPR];
         unsigned done[NPR];
 #pragma unroll
@@ -218,45 +270,61 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_p
           collapse_prep_x2(lam[r], ccf, csx[r], c0);
           done[r] = cannot_beat_x2(c0, csx[r], make_float2(fm[r][0], fm[r][1])) | (valid[r][0] ? 0u : 1u) |
                     (valid[r][1] ? 0u : 2u);
-          if (done[r] != 3u) collapse_root_x2(c0, csx[r]);
-        }
+          if constexpr (kCompact) {
+            // the rest wait in a queue: eigenvalues and F_max in the
+            // particle's own (already read) field slots 0-3
 #pragma unroll
-        for (int r = 0; r < NPR; ++r)
+            for (int u = 0; u < 2; ++u) {
+              if ((done[r] >> u) & 1u) continue;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) s_f[lz[r][u] + k * kFS] = u ? lam[r][k].y : lam[r][k].x;
+              s_f[lz[r][u] + 3 * kFS] = fm[r][u];
+              s_q[atomicAdd(&s_nq, 1)] = (unsigned short)(pt0 + (2 * r + u) * nthreads);
+            }
+          } else {
+            // a pair solves if one of its lanes needs it
+            if (done[r] != 3u) collapse_root_x2(c0, csx[r]);
+          }
+        }
+        if constexpr (!kCompact) {
+#pragma unroll
+          for (int r = 0; r < NPR; ++r) finish(csx[r], done[r], lam[r], q[r], lz[r], fm[r]);
+        }
+      }
+      if constexpr (kCompact) {
+        // the queued particles, two per thread: the lanes of a warp all need
+        // the root (in the main loop a warp solved whenever one of its 64
+        // particles did: about 40 % of warps for 7 % of pairs at 768^3; z
+        // pass 5.52 -> 5.21 ms per radius)
+        __syncthreads();
+        const int nq = s_nq;
+        for (int k0 = 2 * tid; k0 < nq; k0 += 2 * nthreads) {
+          int q2[2], lz2[2];
+          float fm2[2];
+          float2 lam2[3];
+          unsigned dn = 0;
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            if ((done[r] >> u) & 1u) continue;
-            CollapseState<float> cs = lane_state(csx[r], u);
-            if (cs.need[0] || cs.need[1]) collapse_rare<float>(cs);
-            const int qq = q[r][u];
-            const float F = cs.best + cs.corr;
-            if (cs.kappa < a.tau_root) {
-              atomicAdd(a.counters + 1, 1ull);
-              const unsigned slot = atomicAdd(a.redo_count, 1u);
-              if (slot < a.redo_cap) {
-                RedoEntry e;
-                e.q = qq;
+            const bool ok = k0 + u < nq;
+            const int pt = s_q[ok ? k0 + u : k0];
+            const int l = pt / N, z = pt % N;
+            q2[u] = (blockIdx.x * LINES + l) * N + z;
+            lz2[u] = (l * NF) * kFS + z;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) e.h[k] = u ? lam[r][k].y : lam[r][k].x;
-                e.h[3] = e.h[4] = e.h[5] = 0.f;
-                e.kind = 1;
-                a.redo_list[slot] = e;
-                if constexpr (NP == 5) {
-#pragma unroll
-                  for (int cpt = 0; cpt < 3; ++cpt) a.psi_out[cpt * total + qq] = s_f[lz[r][u] + (6 + cpt) * kFS];
-                }
-                continue;
-              }
-              atomicAdd(a.counters + 2, 1ull);  // queue full: keep the FP32 value
+            for (int k = 0; k < 3; ++k) {
+              const float x = s_f[lz2[u] + k * kFS];
+              if (u) lam2[k].y = x;
+              else lam2[k].x = x;
             }
-            if (F > fm[r][u] || (F == fm[r][u] && F > 0.f && a.scale < a.idx[qq])) {
-              a.fmax[qq] = F;
-              a.idx[qq] = a.scale;
-              if constexpr (NP == 5) {
-#pragma unroll
-                for (int cpt = 0; cpt < 3; ++cpt) a.vstate[cpt * total + qq] = s_f[lz[r][u] + (6 + cpt) * kFS];
-              }
-            }
+            fm2[u] = s_f[lz2[u] + 3 * kFS];
+            dn |= ok ? 0u : (1u << u);
           }
+          CollapseStateX2 cs2;
+          float2 c0[3];
+          collapse_prep_x2(lam2, ccf, cs2, c0);
+          collapse_root_x2(c0, cs2);
+          finish(cs2, dn, lam2, q2, lz2, fm2);
+        }
       }
     } else if constexpr (FUSE) {
       // eigenvalues, collapse time and running maximum, PIN_Z_ILP particles
@@ -663,13 +731,17 @@ template <int N> struct Cfg {
 #endif
   static constexpr size_t xz = (size_t)XLayoutLines<E, P, 3 * LINES, P1>::kSize * 8;
   static constexpr size_t fz = (size_t)LINES * 6 * field_stride<N>() * 4;
-  static constexpr size_t smem_z = xz > fz ? xz : fz;  // twiddles come through the read-only cache
+  // the field buffer is followed by the queue of the root solve (one 16-bit
+  // index per particle); twiddles come through the read-only cache
+  static constexpr size_t fzq = fz + (size_t)LINES * N * 2;
+  static constexpr size_t smem_z = xz > fzq ? xz : fzq;
   static constexpr int threads_z = 3 * LINES * P;
   // with the displacement fields: five pairs per line, half as many lines
   static constexpr int LINES_V = LINES >= 2 ? LINES / 2 : 1;
   static constexpr size_t xzv = (size_t)XLayoutLines<E, P, 5 * LINES_V, P1>::kSize * 8;
   static constexpr size_t fzv = (size_t)LINES_V * 10 * field_stride<N>() * 4;
-  static constexpr size_t smem_zv = xzv > fzv ? xzv : fzv;
+  static constexpr size_t fzvq = fzv + (size_t)LINES_V * N * 2;
+  static constexpr size_t smem_zv = xzv > fzvq ? xzv : fzvq;
   static constexpr int threads_zv = 5 * LINES_V * P;
   // forward z: NCF complex transforms (two real lines each) per block
   static constexpr int NCF = P >= 64 ? 3 : 3 * (64 / P);
