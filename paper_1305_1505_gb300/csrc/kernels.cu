@@ -50,7 +50,8 @@ template <int N> __host__ __device__ constexpr int field_stride() {
 // second-order LPT source S = sum_{i<j} (phi_ii phi_jj - phi_ij^2) of every
 // particle goes to out[0] (a real field).
 template <int N, int LINES, bool DUMP, int NP, bool FUSE, bool SRC = false>
-__global__ void __launch_bounds__(NP * LINES * Shape<N>::P, MinBlocks<N>::z) k_pass_z(ArgsZ a) {
+__global__ void __launch_bounds__(NP * LINES * Shape<N>::P, NP == 5 ? MinBlocks<N>::zv : MinBlocks<N>::z)
+    k_pass_z(ArgsZ a) {
   constexpr int E = Shape<N>::E, P = Shape<N>::P;
   constexpr int NC = NP * LINES;  // pair-columns of the block
   constexpr int NF = 2 * NP;      // field slots per line
@@ -721,7 +722,12 @@ template <int N> struct Cfg {
 #define PIN_TC_LONG 16
 #endif
   static constexpr int TC = P >= 16 ? PIN_TC_LONG : (P >= 8 ? 16 : (P == 4 ? 32 : 64));
-  static constexpr int LINES = P >= 64 ? 1 : 64 / P;
+  // z-pass lines per block: 64 threads' worth of line per pair (at the
+  // three-level sizes one 32-thread line: 768 -> 1, 384 -> 2)
+#ifndef PIN_Z_LW3
+#define PIN_Z_LW3 32
+#endif
+  static constexpr int LINES = P >= 64 ? 1 : (Shape<N>::P2 > 1 ? PIN_Z_LW3 : 64) / P;
   // the root solve runs inside the z pass where its transform leaves the
   // registers for it (three-level lines)
 #ifndef PIN_Z_FUSE
@@ -737,7 +743,7 @@ template <int N> struct Cfg {
   static constexpr size_t smem_z = xz > fzq ? xz : fzq;
   static constexpr int threads_z = 3 * LINES * P;
   // with the displacement fields: five pairs per line, half as many lines
-  static constexpr int LINES_V = LINES >= 2 ? LINES / 2 : 1;
+  static constexpr int LINES_V = P >= 64 ? 1 : (64 / P >= 2 ? 64 / P / 2 : 1);
   static constexpr size_t xzv = (size_t)XLayoutLines<E, P, 5 * LINES_V, P1>::kSize * 8;
   static constexpr size_t fzv = (size_t)LINES_V * 10 * field_stride<N>() * 4;
   static constexpr size_t fzvq = fzv + (size_t)LINES_V * N * 2;

@@ -116,17 +116,24 @@ template <int N> struct Stage {
 #ifndef PIN_Z_ILP
 #define PIN_Z_ILP 2
 #endif
-#ifndef PIN_Z_MINB3
-#define PIN_Z_MINB3 4
-#endif
 // Three-level lines hold half the registers per thread: the z pass is sized
-// for more resident blocks.
+// for more resident blocks (one line per block, 96 threads, nine blocks per
+// SM at 72 registers: measured against four 192-thread blocks at 80
+// registers, 768^3 z pass 5.21 -> 4.90 ms per radius); with the velocity
+// fields (five transforms per line, 160 threads) four blocks.
+#ifndef PIN_Z_MINB3
+#define PIN_Z_MINB3 9
+#endif
+#ifndef PIN_Z_MINB3V
+#define PIN_Z_MINB3V 4
+#endif
 template <int N, int TC = 16, int V = 0> struct MinBlocks {
   // three-level x/y blocks (TC columns x P threads) are sized for 512
   // resident threads per SM
   static constexpr int xy =
       Shape<N, V>::P2 > 1 ? 512 / (TC * Shape<N, V>::P) : (N >= 384 ? PIN_XY_MINB : 1);
   static constexpr int z = Shape<N>::P2 > 1 ? PIN_Z_MINB3 : (N >= 384 ? PIN_Z_MINB : 1);
+  static constexpr int zv = Shape<N>::P2 > 1 ? PIN_Z_MINB3V : (N >= 384 ? PIN_Z_MINB : 1);
 };
 
 // ---------------------------------------------------------------- x pass --
