@@ -111,11 +111,22 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, NP == 5 ? MinBlocks<
       v[t] = make_float2(xa.x - xb.y, xa.y + xb.x);  // A + iB
     }
   }
-  // twiddles from the global table through the read-only cache: the table
-  // is a few KB and stays cached for every block on the SM, so a block starts
-  // with its spectrum loads instead of a copy and a barrier (z pass 5.87 ->
-  // 5.52 ms per radius at 768^3)
-  fft_line<N, L, 32 % Shape<N>::P == 0, 0, true>(v, p, c, s_x, a.tw);
+  if constexpr (Shape<N>::P2 > 1) {
+    // three-level lines: twiddles from the global table through the
+    // read-only cache (a few KB, cached for every block on the SM), so that a
+    // block starts with its spectrum loads instead of a copy and a barrier
+    // (z pass 5.87 -> 5.52 ms per radius at 768^3)
+    fft_line<N, L, 32 % Shape<N>::P == 0, 0, true>(v, p, c, s_x, a.tw);
+  } else {
+    // two-level lines: a shared-memory copy behind the field buffer, made
+    // after the spectrum loads are issued (256^3: 0.18 -> 0.16 ms per radius
+    // against the read-only cache)
+    constexpr int kXB = L::kSize * 8, kFB = LINES * NF * kFS * 4 + LINES * N * 2;
+    float2* s_tw = reinterpret_cast<float2*>(smem_raw + (kXB > kFB ? kXB : kFB));
+    for (int i = tid; i < Shape<N>::kTw; i += nthreads) s_tw[i] = a.tw[i];
+    __syncthreads();
+    fft_line<N, L, 32 % Shape<N>::P == 0>(v, p, c, s_x, s_tw);
+  }
 
   if constexpr (DUMP) {
     if (active) {
@@ -740,14 +751,15 @@ template <int N> struct Cfg {
   // the field buffer is followed by the queue of the root solve (one 16-bit
   // index per particle); twiddles come through the read-only cache
   static constexpr size_t fzq = fz + (size_t)LINES * N * 2;
-  static constexpr size_t smem_z = xz > fzq ? xz : fzq;
+  static constexpr size_t tw_z = Shape<N>::P2 > 1 ? 0 : (size_t)NTW * 8;  // two-level: twiddle copy
+  static constexpr size_t smem_z = (xz > fzq ? xz : fzq) + tw_z;
   static constexpr int threads_z = 3 * LINES * P;
   // with the displacement fields: five pairs per line, half as many lines
   static constexpr int LINES_V = P >= 64 ? 1 : (64 / P >= 2 ? 64 / P / 2 : 1);
   static constexpr size_t xzv = (size_t)XLayoutLines<E, P, 5 * LINES_V, P1>::kSize * 8;
   static constexpr size_t fzv = (size_t)LINES_V * 10 * field_stride<N>() * 4;
   static constexpr size_t fzvq = fzv + (size_t)LINES_V * N * 2;
-  static constexpr size_t smem_zv = xzv > fzvq ? xzv : fzvq;
+  static constexpr size_t smem_zv = (xzv > fzvq ? xzv : fzvq) + tw_z;
   static constexpr int threads_zv = 5 * LINES_V * P;
   // forward z: NCF complex transforms (two real lines each) per block
   static constexpr int NCF = P >= 64 ? 3 : 3 * (64 / P);
