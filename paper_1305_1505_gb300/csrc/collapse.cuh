@@ -296,6 +296,31 @@ struct CollapseConsts {
   int correction;
 };
 
+// Upper bound on the collapse time F of a particle from two invariants of its
+// deformation tensor h, without the eigenvalues.  With q = tr(h)/3 and
+// 6 p^2 = tr((h - qI)^2), every eigenvalue lies in [q - 2p, q + 2p] (the
+// deviations from q sum to zero and their squares to 6 p^2), so
+// |lambda_i| <= L = |q| + 2p.  Then for every axis |c1| <= L,
+// |c2| = (3/7)|e_i| <= (3/7) L^2 and |c3| <= (10/84)(2 L^3 + 2 L^3) + L^3/9
+// < 0.5874 L^3, so g(F) >= F^3 - L F^2 - (3/7) L^2 F - 0.5874 L^3, which is
+// increasing for F >= L and positive at F = 1.54 L (1.54^3 - 1.54^2 -
+// (3/7) 1.54 - 0.5874 > 0.03): every axis root lies below 1.54 L.  The
+// correction is at most max(mu1, 0) dcorr (mu1 = 3q, exp(-z^2) <= 1).
+// Used to clear particles queued for the FP64 redo that cannot beat their
+// running maximum.
+constexpr double kRootBound = 1.54;
+template <typename T>
+__host__ __device__ __forceinline__ T collapse_bound(const T h[6], const CollapseConsts<T>& cc) {
+  using F = M<T>;
+  const T q = (h[0] + h[1] + h[2]) * (T(1) / T(3));
+  const T b0 = h[0] - q, b1 = h[1] - q, b2 = h[2] - q;
+  const T p2 = b0 * b0 + b1 * b1 + b2 * b2 + T(2) * (h[3] * h[3] + h[4] * h[4] + h[5] * h[5]);
+  const T L = (q < T(0) ? -q : q) + T(2) * F::sqrt_approx(p2 * (T(1) / T(6)));
+  const T mu1 = T(3) * q;
+  const T corr = (cc.correction && mu1 > T(0) && cc.dcorr > T(0)) ? mu1 * cc.dcorr : T(0);
+  return T(kRootBound) * L + corr;
+}
+
 // True when g(F) = F^3 - c1 F^2 - c2 F - c3 has no real root at or above T:
 // g(T) > 0 and g stays positive beyond T, i.e. g' has no real root, or the
 // right critical point F* = (c1 + sqrt(c1^2 + 3 c2))/3 lies at or below T, or

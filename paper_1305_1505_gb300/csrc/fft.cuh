@@ -277,9 +277,13 @@ __device__ __forceinline__ float2 tw2(const float2* s_tw, int k1, int p) { retur
 // transform c on threads [c P, c P + P)) with an exchange region of its own,
 // so those synchronisations are warp-level.  TWG: s_tw is the global twiddle
 // table (same layout), read through the read-only cache.
-template <int N, class Layout, bool WARP = false, int V = 0, bool TWG = false>
+// No-op hook for fft_line.
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+template <int N, class Layout, bool WARP = false, int V = 0, bool TWG = false, class Hook = NoHook>
 __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N, V>::E], int p, int c, float2* s_x,
-                                         const float2* s_tw) {
+                                         const float2* s_tw, Hook before_exchange = Hook()) {
   using S = Shape<N, V>;
   constexpr int E = S::E, P = S::P, P1 = S::P1, P2 = S::P2;
   static_assert(!WARP || 32 % P == 0, "warp-level exchanges need whole transforms per warp");
@@ -288,6 +292,7 @@ __device__ __forceinline__ void fft_line(float2 (&v)[Shape<N, V>::E], int p, int
     else __syncthreads();
   };
   DFT<E>::run(v);
+  before_exchange();  // all threads of the block: nothing has touched s_x yet
   if constexpr (P2 > 1) {
     // level 1 done; twiddle w_N^{p k1} and first exchange
 #pragma unroll

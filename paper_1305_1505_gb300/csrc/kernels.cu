@@ -245,6 +245,17 @@ __global__ void __launch_bounds__(NP * LINES * Shape<N>::P, NP == 5 ? MinBlocks<
           for (int u = 0; u < 2; ++u) {
             fm[r][u] = valid[r][u] ? a.fmax[q[r][u]] : 0.f;
             if (valid[r][u] && (u ? rabs.y : rabs.x) > 1.f - a.tau_eig) {
+              // a near-degenerate pair: the FP32 eigenvalues are not trusted,
+              // but the invariant bound (no eigenvalues) may already show that
+              // the particle cannot beat F_max, by more than the FP32 error of
+              // the bound; then neither the redo nor anything else is needed
+              float hl[6];
+#pragma unroll
+              for (int f = 0; f < 6; ++f) hl[f] = u ? h[f].y : h[f].x;
+              if (fm[r][u] * (1.f - 1e-5f) > collapse_bound<float>(hl, ccf) * (1.f + 1e-5f)) {
+                valid[r][u] = false;
+                continue;
+              }
               atomicAdd(a.counters + 0, 1ull);
               const unsigned slot = atomicAdd(a.redo_count, 1u);
               if (slot < a.redo_cap) {
@@ -698,6 +709,11 @@ __global__ void __launch_bounds__(128) k_redo64(ArgsZ a) {
     double h[6], lam[3], kap;
 #pragma unroll
     for (int f = 0; f < 6; ++f) h[f] = (double)e.h[f];
+    // the invariant bound (the six components, or diag(lambda) for kind 1)
+    // first: below F_max by more than the FP32 rounding of F, the particle
+    // cannot be updated, and the FP64 eigenvalues and roots are skipped
+    const float fm0 = a.fmax[e.q];
+    if ((double)fm0 * (1.0 - 1e-6) > collapse_bound<double>(h, ccd)) continue;
     if (e.kind == 0) {
       eig3<double>(h, lam);
     } else {
@@ -1007,6 +1023,13 @@ cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int 
   const cuuint64_t strides[1] = {(cuuint64_t)ny * nhp * 8};
   const cuuint32_t box[2] = {(cuuint32_t)tc, (cuuint32_t)(nx / boxes)};
   return encode(tm, 2, src, dims, strides, box);
+}
+
+cudaError_t make_tmap_rows(CUtensorMap* tm, const float2* base, int cols, long long rows, int tc, int box_rows) {
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)tc, (cuuint32_t)box_rows};
+  return encode(tm, 2, base, dims, strides, box);
 }
 
 cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int nx, int ny, int nhp, size_t spec_elems,

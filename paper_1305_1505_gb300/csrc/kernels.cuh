@@ -36,6 +36,7 @@ struct ArgsX {
   int batch;          // realisations stacked back to back (same N, radii)
   int* err;           // set to 1 if a TMA wait gave up (bounded wait)
   long long wait_cycles;  // budget of a TMA wait in SM clocks; <= 0: the default (2^31)
+  CUtensorMap tm_out[3];  // maps of dst[f] (filled at launch when outputs go out by TMA stores)
 };
 
 // y pass (lines of length ny): dst[f] = zfac[f](kz) * IDFT_y(mult[ym[f]] *
@@ -65,6 +66,7 @@ struct ArgsY {
   int batch;
   int* err;
   long long wait_cycles;
+  CUtensorMap tm_out[kMaxFields];  // maps of dst[o] (filled at launch when outputs go out by TMA stores)
 };
 
 // A particle whose FP32 collapse is ill-conditioned, finished in FP64 by the
@@ -126,6 +128,8 @@ struct PassShape {
 // between the spectra the y map spans; tc is the tile width (columns) of the
 // pass that reads the map, one of xy_tile_options.
 cudaError_t make_tmap_x(CUtensorMap* tm, const float2* src, int nx, int ny, int nhp, int batch, int tc);
+// 2D map of rows of `cols` complex values (row pitch cols), box {tc, box_rows}
+cudaError_t make_tmap_rows(CUtensorMap* tm, const float2* base, int cols, long long rows, int tc, int box_rows);
 cudaError_t make_tmap_y(CUtensorMap* tm, const float2* src3, int nx, int ny, int nhp, size_t spec_elems,
                         int batch, int tc);
 // Radix schedules of the x/y line transforms (fft.cuh ShapeBase<N, V>):

@@ -89,6 +89,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, int c0, int c1, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
                                             int c3, uint32_t bar) {
   asm volatile(
@@ -108,6 +116,17 @@ template <int N> struct Stage {
 // already limits the long-line passes to one or two blocks per SM).
 #ifndef PIN_XY_MINB
 #define PIN_XY_MINB 1
+#endif
+// Outputs of the x pass, and of the y pass in single-store mode, go out by
+// TMA bulk tensor stores of the output tile (written into the exchange
+// buffer in tile order) instead of per-thread stores: the warps leave the
+// global store queue to the copy engine (x 1.80 -> 1.62 ms, y 3.58 -> 3.36
+// ms per radius at 768^3).  0 selects the per-thread stores.
+#ifndef PIN_X_TMASTORE
+#define PIN_X_TMASTORE 1
+#endif
+#ifndef PIN_Y_TMASTORE
+#define PIN_Y_TMASTORE 1
 #endif
 #ifndef PIN_Z_MINB
 #define PIN_Z_MINB 2
@@ -141,7 +160,8 @@ template <int N, int TC = 16, int V = 0> struct MinBlocks {
 // (kx, col) sits at kx*N*nhp + col, so a row of TC columns is contiguous.  A
 // persistent block walks column tiles; the staged Phi0 tile serves all
 // outputs, and the next tile is requested as soon as the last output has read
-// the current one into registers.
+// the current one into registers.  Each output tile leaves by TMA stores
+// (PIN_X_TMASTORE; columns past the last are clipped by the map).
 template <int N, int TC, int V>
 __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
     k_pass_x(const __grid_constant__ ArgsX a) {
@@ -182,8 +202,23 @@ __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
   };
   if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
   uint32_t parity = 0;
+  // TMA stores: an output tile is written into the exchange buffer in tile
+  // order and stored by the copy engine; the next transform's first
+  // exchange waits (in the hook) until the engine has read it
+  constexpr bool kStore = PIN_X_TMASTORE != 0;
+  bool pending = false;
+  auto wait_store = [&] {
+    if (kStore && pending) {
+      if (tid == 0) bulk_wait_read();
+      __syncthreads();
+      pending = false;
+    }
+  };
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (!stage_ready(bar, parity, a.err, a.wait_cycles)) return;
+    if (!stage_ready(bar, parity, a.err, a.wait_cycles)) {
+      if (kStore && tid == 0) bulk_wait_all();
+      return;
+    }
     parity ^= 1;
     const int col = (tile % tpr) * TC + c;
     const bool ok = col < ncols;
@@ -201,20 +236,40 @@ __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
           issue(tile + gridDim.x);
         }
       }
-      fft_line<N, L, false, V>(v, p, c, s_x, s_tw);
-      float2* d = s_dst[f] + rbase + (ok ? col : 0);
+      if constexpr (kStore) {
+        fft_line<N, L, false, V>(v, p, c, s_x, s_tw, wait_store);
+        __syncthreads();  // every thread has read its last exchange values
 #pragma unroll
-      for (int j = 0; j < E; ++j)
-        if (ok) d[(size_t)fft_out_index<N, V>(p, j) * ncols] = v[j];
-      __syncthreads();
+        for (int j = 0; j < E; ++j) s_x[fft_out_index<N, V>(p, j) * TC + c] = v[j];
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          const int r = tile / tpr, t = tile % tpr;
+#pragma unroll
+          for (int b = 0; b < G::kBoxes; ++b)
+            tma_store_2d(&a.tm_out[f], t * TC, r * N + b * G::kRows, smem_u32(s_x + b * G::kRows * TC));
+          bulk_commit();
+        }
+        pending = true;
+      } else {
+        fft_line<N, L, false, V>(v, p, c, s_x, s_tw);
+        float2* d = s_dst[f] + rbase + (ok ? col : 0);
+#pragma unroll
+        for (int j = 0; j < E; ++j)
+          if (ok) d[(size_t)fft_out_index<N, V>(p, j) * ncols] = v[j];
+        __syncthreads();
+      }
     }
   }
+  if (kStore && tid == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------- y pass --
 // Lines along y: a tile is TC consecutive kz of one x plane; element
 // (ky, kz) of plane x sits at (x*N + ky)*nhp + kz.  Columns past nhp are
-// zero-filled by the tensor map and not stored.
+// zero-filled by the tensor map and not stored.  Without second stores each
+// output tile leaves by TMA stores (PIN_Y_TMASTORE); with them (DUAL) by
+// per-thread stores.
 template <int N, int TC, bool DUAL, int V>
 __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
     k_pass_y(const __grid_constant__ ArgsY a) {
@@ -262,6 +317,16 @@ __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
   };
   if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, s_sel[0]);
   uint32_t parity = 0;
+  // TMA stores (single-store mode): as in the x pass
+  constexpr bool kStore = PIN_Y_TMASTORE != 0 && !DUAL;
+  bool pending = false;
+  auto wait_store = [&] {
+    if (kStore && pending) {
+      if (tid == 0) bulk_wait_read();
+      __syncthreads();
+      pending = false;
+    }
+  };
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int x = tile / ktiles, kz = (tile % ktiles) * TC + c;
     const bool ok = kz < nhp;
@@ -269,7 +334,10 @@ __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
 #pragma unroll 1
     for (int o = 0; o < nout; ++o) {
       if (o == 0 || s_sel[o] != s_sel[o - 1]) {
-        if (!stage_ready(bar, parity, a.err, a.wait_cycles)) return;
+        if (!stage_ready(bar, parity, a.err, a.wait_cycles)) {
+          if (kStore && tid == 0) bulk_wait_all();
+          return;
+        }
         parity ^= 1;
       }
       const float* mt = s_m + s_ym[o] * N + p;
@@ -296,7 +364,8 @@ __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
       float zf2 = 0.f;
       if constexpr (DUAL)
         zf2 = (ok && s_dst2[o] != nullptr && kz <= nz / 2) ? __ldg(a.mult_z + s_zm2[o] * nz + kz) : 0.f;
-      fft_line<N, L, false, V>(v, p, c, s_x, s_tw);
+      if constexpr (kStore) fft_line<N, L, false, V>(v, p, c, s_x, s_tw, wait_store);
+      else fft_line<N, L, false, V>(v, p, c, s_x, s_tw);
       const bool mi = s_mi[o] != 0;
       float2* d = s_dst[o] + base;
       if constexpr (DUAL) {
@@ -319,6 +388,25 @@ __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
             d2[off] = w2;
           }
         }
+      } else if constexpr (kStore) {
+        __syncthreads();  // every thread has read its last exchange values
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          float2 w = cscale(v[j], zf);
+          if (mi) w = cmuli(w);
+          s_x[fft_out_index<N, V>(p, j) * TC + c] = w;
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          const int kz0 = (tile % ktiles) * TC;
+#pragma unroll
+          for (int b = 0; b < G::kBoxes; ++b)
+            tma_store_2d(&a.tm_out[o], kz0, x * N + b * G::kRows, smem_u32(s_x + b * G::kRows * TC));
+          bulk_commit();
+        }
+        pending = true;
+        continue;
       } else {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
@@ -330,6 +418,7 @@ __global__ void __launch_bounds__(TC* Shape<N, V>::P, MinBlocks<N, TC, V>::xy)
       __syncthreads();
     }
   }
+  if (kStore && tid == 0) bulk_wait_all();
 }
 
 // One x/y tile width: staged tile + exchange + twiddles + multipliers +
@@ -387,8 +476,16 @@ static unsigned persistent_grid(K kernel, int threads, size_t smem, long ntiles)
 }
 
 template <int N, int TC, int V>
-static cudaError_t run_x(const ArgsX& a, cudaStream_t st) {
+static cudaError_t run_x(const ArgsX& a_in, cudaStream_t st) {
   using C = CfgXY<N, TC, V>;
+  ArgsX a = a_in;
+  if (PIN_X_TMASTORE) {
+    // output maps: the same geometry as the source map, one per output
+    for (int f = 0; f < a.nout; ++f) {
+      const cudaError_t e = make_tmap_x(&a.tm_out[f], a.dst[f], N, a.ny, a.nhp, a.batch, TC);
+      if (e != cudaSuccess) return e;
+    }
+  }
   const long ntiles = (((long)a.ny * a.nhp + TC - 1) / TC) * a.batch;
   const unsigned grid = persistent_grid(k_pass_x<N, TC, V>, C::threads, C::smem, ntiles);
   k_pass_x<N, TC, V><<<grid, C::threads, C::smem, st>>>(a);
@@ -401,6 +498,18 @@ static cudaError_t run_y(const ArgsY& a, cudaStream_t st) {
   const long ntiles = (long)a.nx * a.batch * ((a.nhp + TC - 1) / TC);
   bool dual = false;
   for (int o = 0; o < a.nout; ++o) dual = dual || a.dst2[o] != nullptr;
+  if (PIN_Y_TMASTORE && !dual) {
+    // output maps: rows (x, ky) of nhp values, boxes of the staged tile's rows
+    ArgsY b = a;
+    for (int o = 0; o < b.nout; ++o) {
+      const cudaError_t e = make_tmap_rows(&b.tm_out[o], b.dst[o], b.nhp, (long long)b.nx * b.batch * N, TC,
+                                           Stage<N>::kRows);
+      if (e != cudaSuccess) return e;
+    }
+    const unsigned grid = persistent_grid(k_pass_y<N, TC, false, V>, C::threads, C::smem, ntiles);
+    k_pass_y<N, TC, false, V><<<grid, C::threads, C::smem, st>>>(b);
+    return cudaGetLastError();
+  }
   if (dual) {
     const unsigned grid = persistent_grid(k_pass_y<N, TC, true, V>, C::threads, C::smem, ntiles);
     k_pass_y<N, TC, true, V><<<grid, C::threads, C::smem, st>>>(a);

@@ -16,3 +16,13 @@ extern "C" double host_eig(const double* h, double* lam, int use_float) {
   if (use_float) { float hf[6], lf[3]; for (int i=0;i<6;++i) hf[i]=(float)h[i]; float r = pin::eig3<float>(hf, lf); for(int i=0;i<3;++i) lam[i]=lf[i]; return r; }
   return pin::eig3<double>(h, lam);
 }
+extern "C" double host_bound(const double* h, int corr, int use_float, double dcorr) {
+  if (use_float) {
+    float hf[6];
+    for (int i = 0; i < 6; ++i) hf[i] = (float)h[i];
+    pin::CollapseConsts<float> cc{(float)dcorr, corr};
+    return pin::collapse_bound<float>(hf, cc);
+  }
+  pin::CollapseConsts<double> cc{dcorr, corr};
+  return pin::collapse_bound<double>(h, cc);
+}

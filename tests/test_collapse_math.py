@@ -31,6 +31,8 @@ def lib():
     L.host_collapse.restype = ctypes.c_double
     L.host_eig.argtypes = [DP, DP, ctypes.c_int]
     L.host_eig.restype = ctypes.c_double
+    L.host_bound.argtypes = [DP, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    L.host_bound.restype = ctypes.c_double
     return L
 
 
@@ -140,3 +142,44 @@ def test_fp32_eigenvalue_absolute_error_bound(lib):
             continue  # near-degenerate: redone in FP64
         worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
     assert worst < 4e-6, worst
+
+
+def _rotated(lam, rng):
+    """h = R diag(lam) R^T for a random rotation R, as (xx, yy, zz, xy, xz, yz)."""
+    R, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    A = R @ np.diag(lam) @ R.T
+    return np.array([A[0, 0], A[1, 1], A[2, 2], A[0, 1], A[0, 2], A[1, 2]])
+
+
+def test_invariant_bound_above_F(lib):
+    """collapse_bound (which clears FP64-redo candidates that cannot beat
+    their running maximum) is an upper bound on F: over spheres, one- and
+    two-axis triples, ties, sign mixes and six decades of amplitude, in random
+    orientations, the oracle's F never exceeds it (FP64 bound, and the FP32
+    bound within its rounding)."""
+    k = 1.54
+    assert k ** 3 - k ** 2 - 3 / 7 * k - (40 / 84 + 1 / 9) > 0.03  # the root bound's margin
+    dcorr = 1 / oracle.delta_c() - 1 / oracle.x3()
+    assert dcorr > 0
+    rng = np.random.default_rng(13)
+    worst = 0.0
+    for lam in _structured(rng):
+        h = _rotated(lam, rng)
+        hc = np.ascontiguousarray(h)
+        scale = np.abs(lam).max()
+        for corr in (0, 1):
+            F, _ = oracle.collapse_point(h, corr)
+            b64 = lib.host_bound(hc.ctypes.data_as(DP), corr, 0, dcorr)
+            b32 = lib.host_bound(hc.ctypes.data_as(DP), corr, 1, dcorr)
+            assert F <= b64 * (1 + 1e-12), (lam, corr, F, b64)
+            assert F <= b32 * (1 + 1e-6) + 1e-7 * scale, (lam, corr, F, b32)
+            if b64 > 0:
+                worst = max(worst, F / b64)
+        # the diagonal form (the redo's entries that carry eigenvalues)
+        d = np.ascontiguousarray([lam[0], lam[1], lam[2], 0.0, 0.0, 0.0])
+        F, _ = oracle.collapse_point(d, 1)
+        assert F <= lib.host_bound(d.ctypes.data_as(DP), 1, 0, dcorr) * (1 + 1e-12)
+    print("largest F / bound: %.3f" % worst)
+    assert worst < 1.0
+    z = np.zeros(6)
+    assert lib.host_bound(z.ctypes.data_as(DP), 1, 0, dcorr) == 0.0
