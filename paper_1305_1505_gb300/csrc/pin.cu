@@ -851,7 +851,6 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
   const size_t nh = (size_t)p->nz / 2 + 1;
   const size_t bytes = (size_t)p->nx * p->ny * nh * (dtype == PIN_C64 ? 8 : 16) * p->batch;
   const void* src = delta_k;
-  bool staged = false;
   if (!on_device) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, delta_k) == cudaSuccess && at.type == cudaMemoryTypeHost &&
@@ -866,10 +865,8 @@ pin_status pin_set_ic(pin_plan_t p, const void* delta_k, int dtype, int on_devic
       // stage through the V workspace (6 spectra >= one C128 half-spectrum)
       PIN_CK(p, cudaMemcpyAsync(p->V, delta_k, bytes, cudaMemcpyHostToDevice, p->stream));
       src = p->V;
-      staged = true;
     }
   }
-  (void)staged;
   PIN_CK(p, launch_load_phi0(src, dtype, p->nx, p->ny, p->nz, p->nhp, p->box, p->batch, p->phi0, p->stream));
   if (p->d64) PIN_CK(p, fp64_load(src, dtype, p->nx, p->ny, p->nz, p->d64, p->stream));
   if (!on_device) PIN_CK(p, cudaStreamSynchronize(p->stream));
