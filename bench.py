@@ -131,7 +131,7 @@ TRAFFIC_SOURCES = ["kernels.cu", "kernels_v1.cu", "passes_xy.cuh", "kernels.cuh"
                    "collapse.cuh", "collapse_x2.cuh", "pin.cu"]
 MEASURED_TRAFFIC = {
     # profiles/z_pass_instruction_mix_384.md
-    ("k_pass_z", 768, False): {"sources": "ad06de88d60b604d", "bytes_per_particle": 30.239, "warp_inst_per_particle": 9.6018,
+    ("k_pass_z", 768, False): {"sources": "3f2b757b0f7242b0", "bytes_per_particle": 30.239, "warp_inst_per_particle": 9.6018,
                                "measured_at": "384^3 x 40, the 40 launches of one step, scaled by particles"},
 }
 
